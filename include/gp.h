@@ -1,0 +1,157 @@
+/* gp.h -- C ABI of the GB300 exact-GP prediction library (libgp.so).
+ *
+ * What it computes (arxiv 2602.19683, Sec. 3.1-3.2):
+ *   K      = K_{X,X}   with K_ij = v*exp(-|x_i-x_j|^2/(2 l^2)) + [i==j]*s2        (Eq. 1)
+ *   K      = L L^T     by the tiled right-looking Cholesky of Sec. 3.2 (Fig. 1): POTRF on the
+ *                      diagonal tile, TRSM on the tiles below it, SYRK/GEMM on the trailing tiles
+ *   mean   = K_{Xs,X} K^{-1} y, via L beta = y, L^T alpha = beta, mean = K_{Xs,X} alpha  (Eq. 2)
+ *   cov    = K_{Xs,Xs} - K_{Xs,X} K^{-1} K_{X,Xs}, via L V = K_{X,Xs}, cov = K_{Xs,Xs} - V^T V (Eq. 3)
+ *   nlml   = 1/2 y^T alpha + sum_i log L_ii + n/2 log(2 pi) and its gradient w.r.t. (l, v, s2)
+ *            (Rasmussen & Williams 2006, Eqs. 2.30 and 5.9; the paper cites them for the kernel and
+ *            says hyperparameters are normally optimised, Sec. 3.1)
+ *
+ * Lengthscale convention: the paper prints the exponent as -(1/(2 l)) sum_d (x_id - x_jd)^2. This
+ * library uses the textbook -|x_i - x_j|^2 / (2 l^2); pass l = sqrt(paper's l). At the paper's l = 1
+ * both are the same kernel.
+ *
+ * Conventions for every entry point:
+ *   - Returns gp_status (0 = GP_OK). Argument errors are detected synchronously on the host.
+ *   - Work is enqueued on the context's CUDA stream and is ASYNCHRONOUS unless the entry point says
+ *     otherwise. Device-side failures (not positive definite, time-out of a bounded device wait)
+ *     are written to a device status word; gp_sync() waits for the stream and returns them.
+ *   - All numeric arrays are caller-owned DEVICE pointers to contiguous row-major FP64 data:
+ *     X is n x D, Xs is m x D, y is n, mean is m, cov is m x m. The library never frees them.
+ *   - Host pointers appear only for scalar outputs (documented as "host").
+ *   - The library owns its workspace (tile storage, packed panels, task lists, counters) inside the
+ *     context and the factor objects, allocated with cudaMalloc when they are created or grown.
+ *   - Nothing traps: every device-side wait is bounded by cfg.timeout_ns and ends with
+ *     GP_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef GP_H_
+#define GP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gp_status;
+enum {
+  GP_OK = 0,
+  GP_ERR_INVALID_ARG = 1,     /* bad size, null pointer, unsupported option                     */
+  GP_ERR_NOT_PD = 2,          /* a Cholesky pivot was not positive; info = 1-based column       */
+  GP_ERR_NONFINITE = 3,       /* NaN/Inf in an input or a pivot                                 */
+  GP_ERR_OOM = 4,             /* cudaMalloc failed                                               */
+  GP_ERR_CUDA = 5,            /* another CUDA runtime error (launch, copy)                      */
+  GP_ERR_TIMEOUT = 6,         /* a bounded device wait expired (scheduler dependency not met)   */
+  GP_ERR_NO_CONVERGENCE = 7,  /* iterative refinement stopped above its tolerance; result kept  */
+  GP_ERR_NO_DEVICE = 8        /* no usable sm_103 GPU                                            */
+};
+
+/* Precision of the trailing SYRK/GEMM updates and of the panel TRSMs after the first block column
+ * (the diagonal POTRFs, the first block column's TRSMs and every residual stay FP64). */
+enum {
+  GP_FP64 = 0,      /* everything FP64                                                          */
+  GP_FP32 = 1       /* FP32 trailing updates with FP32 accumulation; FP64 POTRF, first-column TRSM,
+                       FP64 iterative refinement of K^{-1} y                                     */
+};
+
+typedef struct {
+  double l;   /* lengthscale (textbook form, see above) */
+  double v;   /* vertical scale                          */
+  double s2;  /* noise variance                          */
+} gp_hyper;
+
+typedef struct {
+  int32_t tile;           /* tile edge T (multiple of 32, 32..1024); 0 = choose automatically        */
+  int32_t precision;      /* GP_FP64 or GP_FP32                                                       */
+  double ir_tol;          /* refinement stops when ||y - K alpha||_2 / ||y||_2 <= ir_tol (0 = 1e-14)  */
+  int32_t ir_maxit;       /* refinement iteration limit (0 = 10)                                      */
+  int32_t noisy_prior;    /* 1: K_{Xs,Xs} includes s2 on its diagonal (noisy-target covariance)       */
+  int64_t timeout_ns;     /* bound on any single device-side wait (0 = 60 s)                          */
+  int32_t grid;           /* persistent-kernel CTAs (0 = as many as fit, up to two per SM)            */
+  int32_t withhold_task;  /* TEST HOOK, read only when withhold_enable != 0: the persistent-kernel
+                             task with this index (in dispatch order) is skipped and never publishes
+                             its completion, so the bounded waits of the tasks that depend on it expire
+                             and the call ends with GP_ERR_TIMEOUT. Leave both fields 0.              */
+  int32_t withhold_enable;
+  int32_t reserved[5];
+} gp_config;
+
+typedef struct gp_ctx gp_ctx;
+typedef struct gp_factor gp_factor;
+
+/* Creates a context on `device` that enqueues on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream). `cfg` may be NULL (all defaults). */
+gp_status gp_create(gp_ctx** ctx, int32_t device, void* cuda_stream, const gp_config* cfg);
+gp_status gp_destroy(gp_ctx* ctx);
+/* Replaces the stream used by later calls. */
+gp_status gp_set_stream(gp_ctx* ctx, void* cuda_stream);
+
+/* Eq. (1) on the lower tiles of K (Sec. 3.2 stores only tiles on or below the diagonal). X is a
+ * device n x D row-major FP64 array and must stay valid for gp_predict_* and gp_nlml* calls on the
+ * factor. *K_out: if NULL a factor is allocated; if it already holds a factor of the same n, D and
+ * configuration it is reused without allocating. Tiles are T x T row-major, packed tile (I, J) at
+ * index I(I+1)/2 + J; n is padded to a multiple of T with an identity block, which leaves L, alpha
+ * and the log-determinant of the leading n x n part unchanged. */
+gp_status gp_assemble(gp_ctx* ctx, const double* X, int64_t n, int32_t D, gp_hyper h, gp_factor** K_out);
+
+/* Tiled right-looking Cholesky (Sec. 3.2, Fig. 1) in place: K -> L, as one persistent kernel that
+ * walks the task DAG of POTRF/TRSM/SYRK/GEMM tile operations. A non-positive pivot ends it with
+ * GP_ERR_NOT_PD (reported by gp_sync, info = 1-based column of the n x n matrix). */
+gp_status gp_cholesky(gp_ctx* ctx, gp_factor* K);
+
+/* Eq. (2): mean[0..m) = K_{Xs,X} K^{-1} y, using the factor L from gp_cholesky. y and Xs are device
+ * arrays (n and m x D). With GP_FP32 precision the solve is refined in FP64 against the stored FP64
+ * K; *ir_iters_out (host, may be NULL) receives the iteration count, which makes this call wait for
+ * the stream. alpha = K^{-1} y stays in the factor for gp_nlml. */
+gp_status gp_predict_mean(gp_ctx* ctx, gp_factor* L, const double* y, const double* Xs, int64_t m,
+                          double* mean_out, int32_t* ir_iters_out);
+
+/* Eq. (3): cov (m x m, both triangles written) = K_{Xs,Xs} - V^T V with L V = K_{X,Xs}. */
+gp_status gp_predict_full_cov(gp_ctx* ctx, gp_factor* L, const double* Xs, int64_t m, double* cov_out);
+
+/* log det K = 2 sum log L_ii of the factor (host output; waits for the stream). */
+gp_status gp_logdet(gp_ctx* ctx, gp_factor* L, double* out);
+
+/* Negative log marginal likelihood and its gradient w.r.t. (l, v, s2) at h, for device X (n x D) and
+ * y (n): assembles K, factors it, solves for alpha, then runs the blocked Cholesky adjoint to obtain
+ * Kbar = 1/2 (K^{-1} - alpha alpha^T) tile by tile and contracts it with dK/dtheta recomputed from X
+ * (dK is never stored). Host outputs; waits for the stream. */
+gp_status gp_nlml_grad(gp_ctx* ctx, const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
+                       double* nlml_out, double grad_out[3]);
+
+/* Copies rows [row0, row0 + nrows) of the n x n lower-triangular matrix held by the factor (K after
+ * gp_assemble, L after gp_cholesky) to out (device, nrows x n row-major; entries above the diagonal
+ * are written as 0). Asynchronous. */
+gp_status gp_factor_rows(gp_ctx* ctx, const gp_factor* f, int64_t row0, int64_t nrows, double* out);
+
+/* Copies alpha = K^{-1} y from the last gp_predict_mean on the factor to out (device, n). */
+gp_status gp_alpha(gp_ctx* ctx, const gp_factor* f, double* out);
+
+gp_status gp_factor_free(gp_ctx* ctx, gp_factor* f);
+
+/* Waits for the context's stream, then returns and clears the first device-side error
+ * (GP_OK if none). *info (host, may be NULL) receives its detail (failing column for NOT_PD). */
+gp_status gp_sync(gp_ctx* ctx, int64_t* info);
+
+/* Host-only introspection of the persistent kernel's dispatch order: writes the task list of graph
+ * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve) for Mt tile rows, Mc covariance
+ * tile columns, tile edge T and `workers` CTAs as int32 quadruples {kind, p, q, r} (kinds as in the
+ * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
+ * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch)) into out (host, room
+ * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
+int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t* out,
+                          int64_t cap);
+
+/* Human-readable name of a status code (static string). */
+const char* gp_status_string(gp_status s);
+
+/* Number of kernel launches the library has enqueued on this context so far. */
+int64_t gp_launch_count(const gp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H_ */

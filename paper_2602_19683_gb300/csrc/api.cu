@@ -1,0 +1,436 @@
+// C ABI of libgp (declared in include/gp.h): contexts, factor objects, workspace and the entry
+// points of the hot path (assembly, tiled Cholesky, mean and covariance prediction).
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gp.h"
+#include "kernels.h"
+#include "schedule.h"
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+gp_status grow(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return GP_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return GP_OK;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GP_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return GP_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+gp_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return GP_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA;
+}
+
+#define GP_TRY(x)                 \
+  do {                            \
+    gp_status s_ = (x);           \
+    if (s_ != GP_OK) return s_;   \
+  } while (0)
+#define GP_CUDA(x) GP_TRY(cuda_status(x))
+
+using TaskKey = std::tuple<int, int, int, int, int>;  // graph kind, Mt, Mc, T, workers
+
+struct TaskBuf {
+  DevBuf buf;
+  int ntasks = 0;
+};
+
+}  // namespace
+
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gp_config cfg{};
+  int sms = 0;
+  int ctas_per_sm = 1;
+  int grid = 0;
+  gpk::DevStatus* d_status = nullptr;
+  double* d_scalar = nullptr;  // small device scratch for scalar results
+  long long launches = 0;
+  std::map<TaskKey, TaskBuf> tasks;
+};
+
+struct gp_factor {
+  long long n = 0;
+  int D = 0, T = 0, Mt = 0, precision = GP_FP64;
+  gp_hyper h{};
+  const double* X = nullptr;  // caller's device array (not owned)
+  DevBuf Kt, cK;              // packed lower tiles and their counters
+  DevBuf bvec, cMean;         // y -> beta -> alpha, and the solve counters
+  DevBuf V, S, cCov;          // covariance workspace
+  bool factored = false, alpha_valid = false;
+};
+
+namespace {
+
+void count_launch(gp_ctx* c, int k = 1) { c->launches += k; }
+
+int auto_tile(long long n) {
+  if (n >= 16384) return 256;
+  if (n >= 2048) return 128;
+  if (n >= 256) return 64;
+  return 32;
+}
+
+gpk::CostModel cost_model(const gp_ctx* c) {
+  gpk::CostModel cm;
+  // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it.
+  cm.sec_per_flop = (double)c->ctas_per_sm / 7.8e9;
+  return cm;
+}
+
+// Returns the device task list of graph `kind` (0 Cholesky, 1 covariance, 2 mean), building and
+// uploading it on first use.
+gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, const TaskBuf** out) {
+  const int workers = c->grid;
+  TaskKey key{kind, Mt, Mc, T, workers};
+  auto it = c->tasks.find(key);
+  if (it == c->tasks.end()) {
+    std::vector<gpk::Task4> v;
+    const gpk::CostModel cm = cost_model(c);
+    if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
+    if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
+    if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
+    TaskBuf tb;
+    GP_TRY(grow(tb.buf, v.size() * sizeof(gpk::Task4)));
+    if (!v.empty())
+      GP_CUDA(cudaMemcpy(tb.buf.p, v.data(), v.size() * sizeof(gpk::Task4), cudaMemcpyHostToDevice));
+    tb.ntasks = (int)v.size();
+    it = c->tasks.emplace(key, tb).first;
+  }
+  *out = &it->second;
+  return GP_OK;
+}
+
+gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
+  gpk::DagArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.Kt = (double*)f->Kt.p;
+  a.T = f->T;
+  a.Mt = f->Mt;
+  a.nch = f->T / 32;
+  a.cK = (int*)f->cK.p;
+  a.st = c->d_status;
+  a.timeout_ns = c->cfg.timeout_ns;
+  a.withhold_task = c->cfg.withhold_enable ? c->cfg.withhold_task : -1;
+  return a;
+}
+
+gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb) {
+  if (tb->ntasks == 0) return GP_OK;
+  GP_CUDA(cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), c->stream));
+  a.tasks = (const int4*)tb->buf.p;
+  a.ntasks = tb->ntasks;
+  const int grid = c->grid < tb->ntasks ? c->grid : tb->ntasks;
+  GP_CUDA(gpk::launch_dag(a, grid, c->stream));
+  count_launch(c);
+  return GP_OK;
+}
+
+bool valid_hyper(const gp_hyper& h) {
+  return std::isfinite(h.l) && std::isfinite(h.v) && std::isfinite(h.s2) && h.l > 0 && h.v > 0 && h.s2 >= 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gp_status_string(gp_status s) {
+  switch (s) {
+    case GP_OK: return "ok";
+    case GP_ERR_INVALID_ARG: return "invalid argument";
+    case GP_ERR_NOT_PD: return "matrix not positive definite";
+    case GP_ERR_NONFINITE: return "non-finite value";
+    case GP_ERR_OOM: return "out of device memory";
+    case GP_ERR_CUDA: return "CUDA error";
+    case GP_ERR_TIMEOUT: return "device wait timed out";
+    case GP_ERR_NO_CONVERGENCE: return "iterative refinement did not converge";
+    case GP_ERR_NO_DEVICE: return "no usable sm_103 device";
+  }
+  return "unknown status";
+}
+
+gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config* cfg) {
+  if (!out) return GP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GP_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp prop;
+  GP_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) return GP_ERR_NO_DEVICE;
+  gp_config c{};
+  if (cfg) c = *cfg;
+  if (c.tile != 0 && (c.tile < 32 || c.tile > 1024 || c.tile % 32)) return GP_ERR_INVALID_ARG;
+  if (c.precision != GP_FP64 && c.precision != GP_FP32) return GP_ERR_INVALID_ARG;
+  if (c.ir_tol <= 0) c.ir_tol = 1e-14;
+  if (c.ir_maxit <= 0) c.ir_maxit = 10;
+  if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
+  GP_CUDA(cudaSetDevice(device));
+  gp_ctx* ctx = new (std::nothrow) gp_ctx();
+  if (!ctx) return GP_ERR_OOM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->cfg = c;
+  ctx->sms = prop.multiProcessorCount;
+  int occ = gpk::dag_max_ctas_per_sm();
+  ctx->ctas_per_sm = occ >= 2 ? 2 : 1;
+  ctx->grid = c.grid > 0 ? c.grid : ctx->sms * ctx->ctas_per_sm;
+  if (c.grid > 0) ctx->ctas_per_sm = (c.grid + ctx->sms - 1) / ctx->sms;
+  if (cudaMalloc(&ctx->d_status, sizeof(gpk::DevStatus)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_scalar, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return GP_ERR_OOM;
+  }
+  gpk::DevStatus st;
+  std::memset(&st, 0, sizeof(st));
+  st.info = LLONG_MAX;
+  if (cudaMemcpy(ctx->d_status, &st, sizeof(st), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    gp_destroy(ctx);
+    return GP_ERR_CUDA;
+  }
+  *out = ctx;
+  return GP_OK;
+}
+
+gp_status gp_destroy(gp_ctx* c) {
+  if (!c) return GP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->tasks) release(kv.second.buf);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->d_scalar) cudaFree(c->d_scalar);
+  delete c;
+  return GP_OK;
+}
+
+gp_status gp_set_stream(gp_ctx* c, void* stream) {
+  if (!c) return GP_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return GP_OK;
+}
+
+int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
+
+int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t* out,
+                          int64_t cap) {
+  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 2) return -1;
+  gpk::CostModel cm;
+  std::vector<gpk::Task4> v;
+  if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
+  if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
+  if (graph == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
+  if (out) {
+    const int64_t k = (int64_t)v.size() < cap ? (int64_t)v.size() : cap;
+    std::memcpy(out, v.data(), (size_t)k * sizeof(gpk::Task4));
+  }
+  return (int64_t)v.size();
+}
+
+gp_status gp_sync(gp_ctx* c, int64_t* info) {
+  if (!c) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  gpk::DevStatus st;
+  GP_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (info) *info = (st.code != 0 && st.info != LLONG_MAX) ? st.info : 0;
+  if (st.code != 0) {
+    gpk::DevStatus z;
+    std::memset(&z, 0, sizeof(z));
+    z.info = LLONG_MAX;
+    GP_CUDA(cudaMemcpy(c->d_status, &z, sizeof(z), cudaMemcpyHostToDevice));
+  }
+  return st.code;
+}
+
+gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
+  if (!c || !f) return GP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  release(f->Kt);
+  release(f->cK);
+  release(f->bvec);
+  release(f->cMean);
+  release(f->V);
+  release(f->S);
+  release(f->cCov);
+  delete f;
+  return GP_OK;
+}
+
+gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper h, gp_factor** K_out) {
+  if (!c || !K_out || !X || n < 1 || D < 1 || D > 4096 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const int T = c->cfg.tile ? c->cfg.tile : auto_tile(n);
+  const long long Mt = (n + T - 1) / T;
+  if (Mt > 46340) return GP_ERR_INVALID_ARG;  // packed tile index must fit int arithmetic
+  gp_factor* f = *K_out;
+  const bool fresh = (f == nullptr);
+  if (fresh) {
+    f = new (std::nothrow) gp_factor();
+    if (!f) return GP_ERR_OOM;
+  }
+  const size_t ntiles = (size_t)Mt * (Mt + 1) / 2;
+  gp_status s = grow(f->Kt, ntiles * T * T * sizeof(double));
+  if (s == GP_OK) s = grow(f->cK, ntiles * sizeof(int));
+  if (s != GP_OK) {
+    if (fresh) gp_factor_free(c, f);
+    return s;
+  }
+  f->n = n;
+  f->D = D;
+  f->T = T;
+  f->Mt = (int)Mt;
+  f->h = h;
+  f->precision = c->cfg.precision;
+  f->X = X;
+  f->factored = false;
+  f->alpha_valid = false;
+  GP_CUDA(gpk::launch_assemble_tiles(X, n, D, h.l, h.v, h.s2, (double*)f->Kt.p, T, (int)Mt, c->stream));
+  count_launch(c);
+  *K_out = f;
+  return GP_OK;
+}
+
+gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
+  if (!c || !f || !f->Kt.p) return GP_ERR_INVALID_ARG;
+  if (f->factored) return GP_ERR_INVALID_ARG;  // already holds L
+  GP_CUDA(cudaSetDevice(c->device));
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, &tb));
+  const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
+  GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
+  GP_TRY(run_dag(c, base_args(c, f), tb));
+  f->factored = true;
+  return GP_OK;
+}
+
+gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double* Xs, int64_t m, double* mean_out,
+                          int32_t* ir_iters_out) {
+  if (!c || !f || !y || m < 0 || (m > 0 && (!Xs || !mean_out)) || !f->factored) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const int T = f->T, Mt = f->Mt, nch = T / 32;
+  const size_t npad = (size_t)Mt * T;
+  GP_TRY(grow(f->bvec, npad * sizeof(double)));
+  const size_t ncnt = (size_t)Mt * nch * 2 + (size_t)Mt * 2;
+  GP_TRY(grow(f->cMean, ncnt * sizeof(int)));
+  GP_CUDA(cudaMemsetAsync(f->bvec.p, 0, npad * sizeof(double), c->stream));
+  GP_CUDA(cudaMemcpyAsync(f->bvec.p, y, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 2, Mt, 0, T, &tb));
+  gpk::DagArgs a = base_args(c, f);
+  a.bvec = (double*)f->bvec.p;
+  int* cm = (int*)f->cMean.p;
+  a.cF = cm;
+  a.cB = cm + (size_t)Mt * nch;
+  a.dF = cm + (size_t)Mt * nch * 2;
+  a.dB = a.dF + Mt;
+  GP_TRY(run_dag(c, a, tb));
+  f->alpha_valid = true;
+  if (m > 0) {
+    GP_CUDA(gpk::launch_mean_gemv(Xs, m, f->X, f->n, f->D, f->h.l, f->h.v, (const double*)f->bvec.p, mean_out,
+                                  c->stream));
+    count_launch(c);
+  }
+  if (ir_iters_out) *ir_iters_out = 0;
+  return GP_OK;
+}
+
+gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, double* cov_out) {
+  if (!c || !f || m < 0 || (m > 0 && (!Xs || !cov_out)) || !f->factored) return GP_ERR_INVALID_ARG;
+  if (m == 0) return GP_OK;
+  if (m > 8 * 65535LL || f->Mt * (long long)f->T > 8 * 65535LL) return GP_ERR_INVALID_ARG;  // dense-assembly grid
+  GP_CUDA(cudaSetDevice(c->device));
+  const int T = f->T, Mt = f->Mt;
+  const long long Mc = (m + T - 1) / T;
+  const size_t ldv = (size_t)Mc * T, npad = (size_t)Mt * T;
+  GP_TRY(grow(f->V, npad * ldv * sizeof(double)));
+  GP_TRY(grow(f->S, ldv * ldv * sizeof(double)));
+  const size_t ncnt = (size_t)Mt * Mc + (size_t)Mc * (Mc + 1) / 2;
+  GP_TRY(grow(f->cCov, ncnt * sizeof(int)));
+  // Right-hand side K_{X,Xs} (n x m, zero padded) and the prior K_{Xs,Xs} (Eq. 3).
+  GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
+                                     (long long)npad, (long long)ldv, c->stream));
+  GP_CUDA(gpk::launch_assemble_dense(Xs, m, Xs, m, f->D, f->h.l, f->h.v, c->cfg.noisy_prior ? f->h.s2 : 0.0,
+                                     (double*)f->S.p, (long long)ldv, (long long)ldv, (long long)ldv, c->stream));
+  count_launch(c, 2);
+  GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 1, Mt, (int)Mc, T, &tb));
+  gpk::DagArgs a = base_args(c, f);
+  a.V = (double*)f->V.p;
+  a.ldv = (long long)ldv;
+  a.Mc = (int)Mc;
+  a.S = (double*)f->S.p;
+  a.lds = (long long)ldv;
+  a.cV = (int*)f->cCov.p;
+  a.cS = a.cV + (size_t)Mt * Mc;
+  GP_TRY(run_dag(c, a, tb));
+  GP_CUDA(gpk::launch_cov_copy((const double*)f->S.p, (long long)ldv, cov_out, m, c->stream));
+  count_launch(c);
+  return GP_OK;
+}
+
+gp_status gp_factor_rows(gp_ctx* c, const gp_factor* f, int64_t row0, int64_t nrows, double* out) {
+  if (!c || !f || !out || row0 < 0 || nrows < 0 || row0 + nrows > f->n) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(gpk::launch_factor_rows((const double*)f->Kt.p, f->T, f->n, row0, nrows, out, c->stream));
+  count_launch(c);
+  return GP_OK;
+}
+
+gp_status gp_alpha(gp_ctx* c, const gp_factor* f, double* out) {
+  if (!c || !f || !out || !f->alpha_valid) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(cudaMemcpyAsync(out, f->bvec.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return GP_OK;
+}
+
+gp_status gp_logdet(gp_ctx* c, gp_factor* f, double* out) {
+  if (!c || !f || !out || !f->factored) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(gpk::launch_logdet((const double*)f->Kt.p, f->T, f->n, c->d_scalar, c->stream));
+  count_launch(c);
+  GP_CUDA(cudaMemcpyAsync(out, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  return GP_OK;
+}
+
+gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
+                       double* nlml_out, double grad_out[3]) {
+  (void)c; (void)X; (void)y; (void)n; (void)D; (void)h; (void)nlml_out; (void)grad_out;
+  return GP_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

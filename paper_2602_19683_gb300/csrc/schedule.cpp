@@ -1,0 +1,171 @@
+// Task graphs of the tiled algorithms (Sec. 3.2, Fig. 1; Eqs. 2-3) and a list scheduler that orders
+// them for the persistent kernel. The paper's runtime fires a task when the futures of its input
+// tiles resolve (HPX dataflow, Sec. 2.1); here the same dependencies are resolved on the device by
+// per-tile counters, and the host only chooses the order in which CTAs pick tasks up.
+#include "schedule.h"
+
+#include <algorithm>
+#include <queue>
+#include <utility>
+
+#include "kernels.h"
+
+namespace gpk {
+
+std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
+                               int workers) {
+  const int n = (int)cost.size();
+  std::vector<std::vector<int>> succ(n);
+  std::vector<int> indeg(n, 0);
+  for (int t = 0; t < n; ++t) {
+    indeg[t] = (int)preds[t].size();
+    for (int p : preds[t]) succ[p].push_back(t);
+  }
+  // Bottom level: longest cost path from a task to the end. Tasks are created in a topological
+  // order (every predecessor has a smaller index), so one backward sweep suffices.
+  std::vector<double> bl(n, 0.0);
+  for (int t = n - 1; t >= 0; --t) {
+    double m = 0.0;
+    for (int s : succ[t]) m = std::max(m, bl[s]);
+    bl[t] = cost[t] + m;
+  }
+  auto cmp = [&](int a, int b) { return bl[a] < bl[b] || (bl[a] == bl[b] && a > b); };
+  std::priority_queue<int, std::vector<int>, decltype(cmp)> ready(cmp);
+  for (int t = 0; t < n; ++t)
+    if (indeg[t] == 0) ready.push(t);
+  using Ev = std::pair<double, int>;  // (finish time, task)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
+  std::vector<int> order;
+  order.reserve(n);
+  double now = 0.0;
+  int free_workers = std::max(1, workers);
+  while ((int)order.size() < n) {
+    while (free_workers > 0 && !ready.empty()) {
+      const int t = ready.top();
+      ready.pop();
+      order.push_back(t);
+      running.push({now + cost[t], t});
+      --free_workers;
+    }
+    if (running.empty()) break;  // cannot happen for a DAG
+    const Ev e = running.top();
+    running.pop();
+    now = e.first;
+    ++free_workers;
+    for (int s : succ[e.second])
+      if (--indeg[s] == 0) ready.push(s);
+  }
+  return order;
+}
+
+namespace {
+
+struct Builder {
+  std::vector<Task4> tasks;
+  std::vector<double> cost;
+  std::vector<std::vector<int>> preds;
+  int add(int kind, int p, int q, int r, double c, std::initializer_list<int> deps) {
+    tasks.push_back({kind, p, q, r});
+    cost.push_back(c);
+    std::vector<int> d;
+    for (int x : deps)
+      if (x >= 0) d.push_back(x);
+    preds.push_back(std::move(d));
+    return (int)tasks.size() - 1;
+  }
+  std::vector<Task4> ordered(int workers) const {
+    std::vector<int> ord = list_schedule(cost, preds, workers);
+    std::vector<Task4> out;
+    out.reserve(ord.size());
+    for (int t : ord) out.push_back(tasks[t]);
+    return out;
+  }
+};
+
+inline size_t tri(int I, int J) { return (size_t)I * (I + 1) / 2 + J; }
+
+}  // namespace
+
+std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& cm) {
+  Builder b;
+  const double t3 = (double)T * T * T;
+  const double c_potrf = cm.task_overhead + cm.sec_per_flop * t3 / 3.0 / cm.potrf_eff;
+  const double c_trsm = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
+  const double c_gemm = cm.task_overhead + cm.sec_per_flop * 2.0 * t3 / cm.gemm_eff;
+  const double c_syrk = cm.task_overhead + cm.sec_per_flop * (t3 + 64.0 * T * T) / cm.gemm_eff;
+  std::vector<int> last(tri(Mt, 0), -1);  // last task that wrote each lower tile
+  for (int J = 0; J < Mt; ++J) {
+    const int po = b.add(TASK_POTRF, J, 0, 0, c_potrf, {last[tri(J, J)]});
+    last[tri(J, J)] = po;
+    for (int I = J + 1; I < Mt; ++I) last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, c_trsm, {po, last[tri(I, J)]});
+    for (int I = J + 1; I < Mt; ++I)
+      for (int K = J + 1; K <= I; ++K)
+        last[tri(I, K)] =
+            b.add(TASK_UPD, I, K, J, I == K ? c_syrk : c_gemm, {last[tri(I, J)], last[tri(K, J)], last[tri(I, K)]});
+  }
+  return b.ordered(workers);
+}
+
+std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm) {
+  Builder b;
+  const double t3 = (double)T * T * T;
+  const double c_trsm = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
+  const double c_gemm = cm.task_overhead + cm.sec_per_flop * 2.0 * t3 / cm.gemm_eff;
+  std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1);
+  for (int J = 0; J < Mt; ++J) {
+    for (int c = 0; c < Mc; ++c)
+      lastV[(size_t)J * Mc + c] = b.add(TASK_VTRSM, J, c, 0, c_trsm, {lastV[(size_t)J * Mc + c]});
+    for (int I = J + 1; I < Mt; ++I)
+      for (int c = 0; c < Mc; ++c)
+        lastV[(size_t)I * Mc + c] =
+            b.add(TASK_VGEMM, I, J, c, c_gemm, {lastV[(size_t)J * Mc + c], lastV[(size_t)I * Mc + c]});
+    for (int a = 0; a < Mc; ++a)
+      for (int bb = 0; bb <= a; ++bb)
+        lastS[tri(a, bb)] = b.add(TASK_WSYRK, a, bb, J, c_gemm,
+                                  {lastV[(size_t)J * Mc + a], lastV[(size_t)J * Mc + bb], lastS[tri(a, bb)]});
+  }
+  return b.ordered(workers);
+}
+
+std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm) {
+  Builder b;
+  const int nch = T / 32;
+  const double c_solve = cm.task_overhead + cm.sec_per_flop * (double)T * T / cm.vec_eff;
+  const double c_gemv = cm.task_overhead + cm.sec_per_flop * 2.0 * 32.0 * T / cm.vec_eff;
+  std::vector<int> lastF((size_t)Mt * nch, -1), lastB((size_t)Mt * nch, -1), fsolve(Mt, -1);
+  for (int J = 0; J < Mt; ++J) {
+    std::vector<int> d;
+    int fs;
+    {
+      b.tasks.push_back({TASK_FSOLVE, J, 0, 0});
+      b.cost.push_back(c_solve);
+      std::vector<int> pr;
+      for (int ch = 0; ch < nch; ++ch)
+        if (lastF[(size_t)J * nch + ch] >= 0) pr.push_back(lastF[(size_t)J * nch + ch]);
+      b.preds.push_back(pr);
+      fs = (int)b.tasks.size() - 1;
+    }
+    fsolve[J] = fs;
+    for (int I = J + 1; I < Mt; ++I)
+      for (int ch = 0; ch < nch; ++ch)
+        lastF[(size_t)I * nch + ch] = b.add(TASK_FGEMV, I, J, ch, c_gemv, {fs, lastF[(size_t)I * nch + ch]});
+  }
+  for (int I = Mt - 1; I >= 0; --I) {
+    int bs;
+    {
+      b.tasks.push_back({TASK_BSOLVE, I, 0, 0});
+      b.cost.push_back(c_solve);
+      std::vector<int> pr{fsolve[I]};
+      for (int ch = 0; ch < nch; ++ch)
+        if (lastB[(size_t)I * nch + ch] >= 0) pr.push_back(lastB[(size_t)I * nch + ch]);
+      b.preds.push_back(pr);
+      bs = (int)b.tasks.size() - 1;
+    }
+    for (int J = 0; J < I; ++J)
+      for (int ch = 0; ch < nch; ++ch)
+        lastB[(size_t)J * nch + ch] = b.add(TASK_BGEMV, J, I, ch, c_gemv, {bs, fsolve[J], lastB[(size_t)J * nch + ch]});
+  }
+  return b.ordered(workers);
+}
+
+}  // namespace gpk

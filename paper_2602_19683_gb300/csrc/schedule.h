@@ -1,0 +1,33 @@
+// Host-side task graphs of the tiled algorithms and their dispatch order.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace gpk {
+
+struct Task4 {
+  int32_t kind, p, q, r;
+};
+
+// Relative speed model used to order tasks (seconds per flop of one CTA, plus a fixed overhead).
+struct CostModel {
+  double sec_per_flop = 1.0 / 3.9e9;   // one CTA on a shared SM, FP64 FFMA
+  double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
+  double task_overhead = 3e-6;
+};
+
+// Tasks of the tiled right-looking Cholesky (Fig. 1) on Mt x Mt tiles of edge T, in the order a
+// simulated list scheduler with `workers` CTAs would start them (priority: longest remaining
+// path). The order is a topological order of the dependency DAG.
+std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& cm);
+// Tasks of L V = B (B: Mt x Mc tiles) followed by S -= V^T V on the Mc x Mc lower tiles.
+std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm);
+// Tasks of L beta = y then L^T alpha = beta on Mt tiles, vector chunks of 32 rows.
+std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm);
+
+// Generic list scheduling: returns the start order of tasks with the given costs and
+// predecessor lists, simulated on `workers` identical workers.
+std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
+                               int workers);
+
+}  // namespace gpk

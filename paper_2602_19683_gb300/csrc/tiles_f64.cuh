@@ -1,0 +1,399 @@
+// CTA-level FP64 tile operations of the tiled Cholesky (Sec. 3.2: POTRF, TRSM, SYRK, GEMM) and of
+// the triangular solves of Eqs. (2)-(3). Every function is executed by all kThreads threads of one
+// CTA and reads operands that other CTAs may have written through L2-only loads.
+//
+// On GB300 the FP64 pipe issues about two FMAs per clock per SM (measured: 1.19 TFLOP/s FP64 FFMA,
+// 1.05 TFLOP/s for the FP64 mma.sync path), so these routines are FP64-issue bound at any sane
+// memory layout: the design goal is no wasted FMAs and enough independent FMA chains per warp, and
+// the FMA path is plain FFMA rather than DMMA.
+#pragma once
+#include "common.cuh"
+
+namespace gpk {
+
+// Operand layouts of C -= op(A) op(B), with op(A) M x K and op(B) K x N.
+enum { A_MK = 0, A_KM = 1 };  // A_MK: A[m*lda + k]; A_KM: A[k*lda + m]
+enum { B_NK = 0, B_KN = 1 };  // B_NK: B[n*ldb + k] (C -= A B^T); B_KN: B[k*ldb + n]
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GPAD = 4;
+
+struct GemmSmem {
+  double a[2][GBK][GBM + GPAD];
+  double b[2][GBK][GBN + GPAD];
+};
+
+template <int LA>
+__device__ __forceinline__ void gemm_load_a(double (&r)[4], const double* A, int lda, int m0, int k0, int M, int K) {
+  const int t = threadIdx.x;
+  if (LA == A_MK) {  // 64 rows x 16 k: thread -> (m = t/4, k = 4*(t%4) .. +3)
+    const int m = m0 + t / 4, k = k0 + 4 * (t % 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = (m < M && k + q < K) ? ldcg(A + (size_t)m * lda + k + q) : 0.0;
+  } else {  // 16 k x 64 m: thread -> (k = t/16, m = 4*(t%16) .. +3)
+    const int k = k0 + t / 16, m = m0 + 4 * (t % 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = (k < K && m + q < M) ? ldcg(A + (size_t)k * lda + m + q) : 0.0;
+  }
+}
+
+template <int LA>
+__device__ __forceinline__ void gemm_store_a(GemmSmem& s, int buf, const double (&r)[4]) {
+  const int t = threadIdx.x;
+  if (LA == A_MK) {
+    const int m = t / 4, k = 4 * (t % 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.a[buf][k + q][m] = r[q];
+  } else {
+    const int k = t / 16, m = 4 * (t % 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.a[buf][k][m + q] = r[q];
+  }
+}
+
+template <int LB>
+__device__ __forceinline__ void gemm_load_b(double (&r)[4], const double* B, int ldb, int n0, int k0, int N, int K) {
+  const int t = threadIdx.x;
+  if (LB == B_NK) {
+    const int n = n0 + t / 4, k = k0 + 4 * (t % 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = (n < N && k + q < K) ? ldcg(B + (size_t)n * ldb + k + q) : 0.0;
+  } else {
+    const int k = k0 + t / 16, n = n0 + 4 * (t % 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = (k < K && n + q < N) ? ldcg(B + (size_t)k * ldb + n + q) : 0.0;
+  }
+}
+
+template <int LB>
+__device__ __forceinline__ void gemm_store_b(GemmSmem& s, int buf, const double (&r)[4]) {
+  const int t = threadIdx.x;
+  if (LB == B_NK) {
+    const int n = t / 4, k = 4 * (t % 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.b[buf][k + q][n] = r[q];
+  } else {
+    const int k = t / 16, n = 4 * (t % 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s.b[buf][k][n + q] = r[q];
+  }
+}
+
+// C[M x N] -= op(A) op(B). lower: only entries with (row + diag_off) >= col are written (and output
+// blocks entirely above that line are skipped). Ends with __syncthreads().
+template <int LA, int LB>
+__device__ void cta_gemm_sub(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N,
+                             int K, bool lower, int diag_off, GemmSmem& s) {
+  const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+  const int nbm = (M + GBM - 1) / GBM, nbn = (N + GBN - 1) / GBN;
+  const int nk = (K + GBK - 1) / GBK;
+  for (int blk = 0; blk < nbm * nbn; ++blk) {
+    const int m0 = (blk / nbn) * GBM, n0 = (blk % nbn) * GBN;
+    if (lower && n0 > m0 + GBM - 1 + diag_off) continue;  // block strictly above the diagonal
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    double ra[4], rb[4];
+    gemm_load_a<LA>(ra, A, lda, m0, 0, M, K);
+    gemm_load_b<LB>(rb, B, ldb, n0, 0, N, K);
+    gemm_store_a<LA>(s, 0, ra);
+    gemm_store_b<LB>(s, 0, rb);
+    __syncthreads();
+    for (int kc = 0; kc < nk; ++kc) {
+      const int cur = kc & 1;
+      if (kc + 1 < nk) {
+        gemm_load_a<LA>(ra, A, lda, m0, (kc + 1) * GBK, M, K);
+        gemm_load_b<LB>(rb, B, ldb, n0, (kc + 1) * GBK, N, K);
+      }
+#pragma unroll
+      for (int k = 0; k < GBK; ++k) {
+        const double2 a01 = *reinterpret_cast<const double2*>(&s.a[cur][k][ty * 4]);
+        const double2 a23 = *reinterpret_cast<const double2*>(&s.a[cur][k][ty * 4 + 2]);
+        const double2 b01 = *reinterpret_cast<const double2*>(&s.b[cur][k][tx * 4]);
+        const double2 b23 = *reinterpret_cast<const double2*>(&s.b[cur][k][tx * 4 + 2]);
+        const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+        const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      if (kc + 1 < nk) {
+        gemm_store_a<LA>(s, cur ^ 1, ra);
+        gemm_store_b<LB>(s, cur ^ 1, rb);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty * 4 + i;
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx * 4 + j;
+        if (n >= N || (lower && n > m + diag_off)) continue;
+        double* c = C + (size_t)m * ldc + n;
+        *c = ldcg(c) - acc[i][j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- 32-wide triangular kernels
+
+// Smem copy of a 32 x 32 lower-triangular diagonal block with its reciprocal diagonal.
+struct Tri32 {
+  double l[32][33];
+  double inv[32];
+};
+
+// Loads the lower triangle of L[0..32) x [0..32) (already factored) into smem.
+__device__ __forceinline__ void tri32_load(Tri32& s, const double* L, int ldl) {
+  for (int e = threadIdx.x; e < 32 * 32; e += kThreads) {
+    const int i = e / 32, j = e % 32;
+    s.l[i][j] = (j <= i) ? ldcg(L + (size_t)i * ldl + j) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) s.inv[threadIdx.x] = 1.0 / s.l[threadIdx.x][threadIdx.x];
+  __syncthreads();
+}
+
+// Unblocked Cholesky of the 32 x 32 diagonal block at A (in place, lower; upper zeroed), by warp 0
+// with lane i owning row i: right-looking column by column. Leaves the factor in s. Returns 0 or
+// the 1-based failing column (same value in every thread).
+__device__ int cta_potrf32(double* A, int lda, Tri32& s, int* shared_flag) {
+  const int t = threadIdx.x;
+  for (int e = t; e < 32 * 32; e += kThreads) {
+    const int i = e / 32, j = e % 32;
+    s.l[i][j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
+  }
+  if (t == 0) *shared_flag = 0;
+  __syncthreads();
+  if (t < 32) {
+    const int i = t;
+    int fail = 0;
+    for (int j = 0; j < 32; ++j) {
+      const double d = s.l[j][j];
+      if (!(d > 0.0)) {  // also catches NaN
+        fail = j + 1;
+        break;
+      }
+      const double ljj = sqrt(d);
+      const double inv = 1.0 / ljj;
+      __syncwarp();
+      if (i == j) {
+        s.l[j][j] = ljj;
+        s.inv[j] = inv;
+      }
+      if (i > j) s.l[i][j] *= inv;
+      __syncwarp();
+      if (i > j) {
+        const double lij = s.l[i][j];
+        for (int k = j + 1; k <= i; ++k) s.l[i][k] = fma(-lij, s.l[k][j], s.l[i][k]);
+      }
+      __syncwarp();
+    }
+    if (i == 0) *shared_flag = fail;
+  }
+  __syncthreads();
+  const int fail = *shared_flag;
+  if (fail == 0) {
+    for (int e = t; e < 32 * 32; e += kThreads) {
+      const int i = e / 32, j = e % 32;
+      A[(size_t)i * lda + j] = (j <= i) ? s.l[i][j] : 0.0;
+    }
+  }
+  __syncthreads();
+  return fail;
+}
+
+// B[rows x 32] <- B L^{-T} with L the 32 x 32 lower block in s: each thread solves whole rows
+// (x_c = (b_c - sum_{k<c} x_k L_ck) / L_cc).
+__device__ void cta_trsm_rows32(const Tri32& s, double* B, int ldb, int rows) {
+  for (int r = threadIdx.x; r < rows; r += kThreads) {
+    double x[32];
+    double* row = B + (size_t)r * ldb;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = ldcg(row + c);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      double acc = x[c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) acc = fma(-x[k], s.l[c][k], acc);
+      x[c] = acc * s.inv[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) row[c] = x[c];
+  }
+  __syncthreads();
+}
+
+// B[32 x ncols] <- L^{-1} B with L the 32 x 32 lower block in s: each thread solves whole columns.
+__device__ void cta_trsm_cols32(const Tri32& s, double* B, int ldb, int ncols) {
+  for (int c = threadIdx.x; c < ncols; c += kThreads) {
+    double x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = ldcg(B + (size_t)i * ldb + c);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      double acc = x[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc = fma(-s.l[i][k], x[k], acc);
+      x[i] = acc * s.inv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) B[(size_t)i * ldb + c] = x[i];
+  }
+  __syncthreads();
+}
+
+struct TileSmem {
+  GemmSmem g;
+  Tri32 tri;
+  int flag;
+};
+
+// POTRF of the nb x nb diagonal tile A (nb a multiple of 32), blocked right-looking with 32-wide
+// strips: factor the strip's diagonal block, TRSM the rows below it, SYRK-update the trailing
+// lower triangle. Upper triangle zeroed. Returns 0 or the 1-based failing column within the tile.
+__device__ int cta_potrf(double* A, int lda, int nb, TileSmem& s) {
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    const int fail = cta_potrf32(A + (size_t)k0 * lda + k0, lda, s.tri, &s.flag);
+    if (fail) return k0 + fail;
+    const int rest = nb - k0 - 32;
+    if (rest > 0) {
+      cta_trsm_rows32(s.tri, A + (size_t)(k0 + 32) * lda + k0, lda, rest);
+      double* P = A + (size_t)(k0 + 32) * lda + k0;  // rest x 32 panel
+      cta_gemm_sub<A_MK, B_NK>(A + (size_t)(k0 + 32) * lda + k0 + 32, lda, P, lda, P, lda, rest, rest, 32, true, 0,
+                               s.g);
+    }
+    // zero the strip's part above the diagonal block (columns k0+32.. of rows k0..k0+32)
+    for (int e = threadIdx.x; e < 32 * rest; e += kThreads) {
+      const int i = e / rest, j = e % rest;
+      A[(size_t)(k0 + i) * lda + k0 + 32 + j] = 0.0;
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// TRSM from the right: B[rows x nb] <- B L^{-T}, L the nb x nb lower factor (Sec. 3.2 TRSM,
+// L_IJ = K_IJ L_JJ^{-T}). Right-looking over 32-wide column strips.
+__device__ void cta_trsm_right(const double* L, int ldl, double* B, int ldb, int rows, int nb, TileSmem& s) {
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    tri32_load(s.tri, L + (size_t)k0 * ldl + k0, ldl);
+    cta_trsm_rows32(s.tri, B + k0, ldb, rows);
+    const int rest = nb - k0 - 32;
+    if (rest > 0)
+      cta_gemm_sub<A_MK, B_NK>(B + k0 + 32, ldb, B + k0, ldb, L + (size_t)(k0 + 32) * ldl + k0, ldl, rows, rest, 32,
+                               false, 0, s.g);
+  }
+}
+
+// TRSM from the left: B[nb x ncols] <- L^{-1} B (Eq. 3's L V = K_{X,Xs}, one tile row at a time).
+__device__ void cta_trsm_left(const double* L, int ldl, double* B, int ldb, int nb, int ncols, TileSmem& s) {
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    tri32_load(s.tri, L + (size_t)k0 * ldl + k0, ldl);
+    cta_trsm_cols32(s.tri, B + (size_t)k0 * ldb, ldb, ncols);
+    const int rest = nb - k0 - 32;
+    if (rest > 0)
+      cta_gemm_sub<A_MK, B_KN>(B + (size_t)(k0 + 32) * ldb, ldb, L + (size_t)(k0 + 32) * ldl + k0, ldl,
+                               B + (size_t)k0 * ldb, ldb, rest, ncols, 32, false, 0, s.g);
+  }
+}
+
+// ---------------------------------------------------------------- vector solves (Eq. 2)
+
+// b[0..nb) <- L^{-1} b (forward substitution with one diagonal tile). Warp 0 solves each 32-row
+// strip (lane i owns row i), then all threads update the rows below with the strip's columns.
+__device__ void cta_trsv_lower(const double* L, int ldl, double* b, int nb, double* xs /*smem[32]*/) {
+  const int t = threadIdx.x;
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    if (t < 32) {
+      double bi = ldcg(b + k0 + t);
+      const double* Lr = L + (size_t)(k0 + t) * ldl + k0;
+      for (int j = 0; j < 32; ++j) {
+        double xj = 0.0;
+        if (t == j) xj = bi / ldcg(Lr + j);
+        xj = __shfl_sync(0xffffffffu, xj, j);
+        if (t == j) bi = xj;
+        if (t > j) bi = fma(-ldcg(Lr + j), xj, bi);
+      }
+      xs[t] = bi;
+      b[k0 + t] = bi;
+    }
+    __syncthreads();
+    for (int r = k0 + 32 + t; r < nb; r += kThreads) {
+      const double* Lr = L + (size_t)r * ldl + k0;
+      double acc = ldcg(b + r);
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc = fma(-ldcg(Lr + j), xs[j], acc);
+      b[r] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// b[0..nb) <- L^{-T} b (backward substitution with one diagonal tile), strips from the bottom.
+__device__ void cta_trsv_lower_T(const double* L, int ldl, double* b, int nb, double* xs) {
+  const int t = threadIdx.x;
+  for (int k0 = nb - 32; k0 >= 0; k0 -= 32) {
+    if (t < 32) {
+      double bi = ldcg(b + k0 + t);
+      for (int j = 31; j >= 0; --j) {
+        double xj = 0.0;
+        if (t == j) xj = bi / ldcg(L + (size_t)(k0 + j) * ldl + k0 + j);
+        xj = __shfl_sync(0xffffffffu, xj, j);
+        if (t == j) bi = xj;
+        if (t < j) bi = fma(-ldcg(L + (size_t)(k0 + j) * ldl + k0 + t), xj, bi);
+      }
+      xs[t] = bi;
+      b[k0 + t] = bi;
+    }
+    __syncthreads();
+    for (int r = t; r < k0; r += kThreads) {  // rows above: b_r -= sum_j L[k0+j][r] x_j
+      double acc = ldcg(b + r);
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc = fma(-ldcg(L + (size_t)(k0 + j) * ldl + r), xs[j], acc);
+      b[r] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// b[r] -= sum_c A[r][c] x[c] for r in [0, rows): one warp per row, lanes over columns.
+__device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* b, int rows, int cols) {
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int r = w; r < rows; r += kThreads / 32) {
+    const double* Ar = A + (size_t)r * lda;
+    double acc = 0.0;
+    for (int c = lane; c < cols; c += 32) acc = fma(ldcg(Ar + c), ldcg(x + c), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) b[r] = ldcg(b + r) - acc;
+  }
+  __syncthreads();
+}
+
+// b[c] -= sum_r A[r][c] x[r] for c in [0, cols) with cols <= 32: warps split the rows, lanes own
+// columns, partial sums reduced through smem (red[8][32]).
+__device__ void cta_gemv_T_sub(const double* A, int lda, const double* x, double* b, int rows, int cols,
+                               double (*red)[32]) {
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double acc = 0.0;
+  if (lane < cols)
+    for (int r = w; r < rows; r += kThreads / 32) acc = fma(ldcg(A + (size_t)r * lda + lane), ldcg(x + r), acc);
+  red[w][lane] = acc;
+  __syncthreads();
+  if (threadIdx.x < cols) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
+    b[threadIdx.x] = ldcg(b + threadIdx.x) - s;
+  }
+  __syncthreads();
+}
+
+}  // namespace gpk

@@ -1,0 +1,126 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every declared entry point,
+argument validation works without a GPU, and the persistent kernel's dispatch orders are
+topological orders of the tiled algorithms' dependency graphs (Sec. 3.2, Fig. 1; Eqs. 2-3)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_2602_19683_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return N.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:gp_status|const char\*|int64_t|void)\s+(gp_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in N.SIGNATURES, f"binding lacks {name}"
+
+
+def test_no_gpu_or_bad_args_are_rejected(lib):
+    h = ctypes.c_void_p()
+    s = lib.gp_create(ctypes.byref(h), 0, None, None)
+    import torch
+    if not torch.cuda.is_available():
+        assert s == N.GP_ERR_NO_DEVICE
+    else:
+        assert s == N.GP_OK
+        lib.gp_destroy(h)
+    assert lib.gp_create(None, 0, None, None) == N.GP_ERR_INVALID_ARG
+    assert lib.gp_cholesky(None, None) == N.GP_ERR_INVALID_ARG
+    assert lib.gp_status_string(N.GP_ERR_NOT_PD) == b"matrix not positive definite"
+
+
+def tasks(lib, graph, Mt, Mc, T, workers):
+    cnt = lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, None, 0)
+    out = np.zeros((cnt, 4), dtype=np.int32)
+    assert lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, out.ctypes.data, cnt) == cnt
+    return out
+
+
+@pytest.mark.parametrize("Mt,workers", [(1, 4), (2, 1), (5, 3), (9, 304), (16, 304)])
+def test_cholesky_schedule_is_topological(lib, Mt, workers):
+    """Every tile of the lower triangle receives POTRF/TRSM once and its updates J = 0..min-1 in order,
+    and each task appears after the tasks whose tiles it reads (Fig. 1's dependencies)."""
+    t = tasks(lib, 0, Mt, 0, 64, workers)
+    assert len(t) == Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
+    cnt = {}  # tile -> updates applied (+1 once final)
+    for kind, p, q, r in t:
+        if kind == 0:
+            assert cnt.get((p, p), 0) == p
+            cnt[(p, p)] = p + 1
+        elif kind == 1:
+            assert cnt.get((q, q), 0) == q + 1 and cnt.get((p, q), 0) == q and p > q
+            cnt[(p, q)] = q + 1
+        elif kind == 2:
+            assert p >= q > r
+            assert cnt.get((p, r), 0) == r + 1 and cnt.get((q, r), 0) == r + 1 and cnt.get((p, q), 0) == r
+            cnt[(p, q)] = r + 1
+        else:
+            raise AssertionError(kind)
+    assert all(cnt[(I, J)] == J + 1 for I in range(Mt) for J in range(I + 1))
+
+
+@pytest.mark.parametrize("Mt,Mc,workers", [(1, 1, 2), (4, 3, 5), (7, 2, 304)])
+def test_cov_schedule_is_topological(lib, Mt, Mc, workers):
+    t = tasks(lib, 1, Mt, Mc, 64, workers)
+    cv, cs = {}, {}
+    for kind, p, q, r in t:
+        if kind == 3:
+            assert cv.get((p, q), 0) == p
+            cv[(p, q)] = p + 1
+        elif kind == 4:
+            assert cv.get((q, r), 0) == q + 1 and cv.get((p, r), 0) == q and p > q
+            cv[(p, r)] = q + 1
+        elif kind == 5:
+            assert p >= q and cv.get((r, p), 0) == r + 1 and cv.get((r, q), 0) == r + 1 and cs.get((p, q), 0) == r
+            cs[(p, q)] = r + 1
+        else:
+            raise AssertionError(kind)
+    assert all(cs[(a, b)] == Mt for a in range(Mc) for b in range(a + 1))
+
+
+@pytest.mark.parametrize("Mt,T,workers", [(1, 32, 1), (3, 64, 2), (6, 96, 304)])
+def test_mean_schedule_is_topological(lib, Mt, T, workers):
+    t = tasks(lib, 2, Mt, 0, T, workers)
+    nch = T // 32
+    cf, cb, df, db = {}, {}, set(), set()
+    for kind, p, q, r in t:
+        if kind == 6:
+            assert all(cf.get((p, ch), 0) == p for ch in range(nch))
+            df.add(p)
+        elif kind == 7:
+            assert q in df and cf.get((p, r), 0) == q and p > q
+            cf[(p, r)] = q + 1
+        elif kind == 8:
+            assert p in df and all(cb.get((p, ch), 0) == Mt - 1 - p for ch in range(nch))
+            db.add(p)
+        elif kind == 9:
+            assert q in db and p in df and cb.get((p, r), 0) == Mt - 1 - q and q > p
+            cb[(p, r)] = Mt - q
+        else:
+            raise AssertionError(kind)
+    assert df == db == set(range(Mt))
+
+
+def test_schedule_rejects_bad_arguments(lib):
+    assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, None, 0) == -1
+    assert lib.gp_schedule_tasks(3, 4, 0, 64, 1, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, None, 0) == -1

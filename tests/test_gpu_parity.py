@@ -1,0 +1,198 @@
+"""GPU parity of the FP64 path against the FP64 oracle, through the C ABI.
+
+Bars (from the method's stated accuracy): the factor reconstructs K to ||LL^T - K||_F/||K||_F <= 1e-13;
+the predictive mean (Eq. 2) agrees to <= 1e-10 and the covariance (Eq. 3) to <= 1e-9, both as
+max-abs error relative to the oracle's max-abs value. Assembly (Eq. 1) agrees to 1e-14 relative:
+both sides evaluate the same expression, the only freedom being fused multiply-adds in |x_i-x_j|^2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import nfir
+import oracle
+from oracle import Hyper
+
+pytestmark = pytest.mark.gpu
+
+H0 = Hyper(1.0, 1.0, 0.1)
+
+
+@pytest.fixture(scope="module")
+def api():
+    __graft_entry__.build()
+    from paper_2602_19683_gb300 import api as A
+    return A
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    d = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (d if d > 0 else 1.0))
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to("cuda") for a in arrs]
+
+
+CASES = [
+    # n, m, D, T, h, seed
+    (1024, 1024, 8, 256, H0, 0),          # 4 x 4 tiles: the small workload
+    (1000, 333, 8, 64, H0, 1),            # ragged n and m
+    (777, 100, 4, 96, Hyper(0.8, 1.3, 0.05), 2),
+    (33, 65, 3, 32, Hyper(1.5, 0.7, 0.2), 3),  # D with no specialised kernel
+    (1, 1, 16, 32, H0, 4),                # n = 1, m = 1
+    (2048, 512, 16, 128, Hyper(2.0, 1.0, 0.1), 5),
+]
+
+
+@pytest.mark.parametrize("n,m,D,T,h,seed", CASES)
+def test_fp64_pipeline_matches_oracle(api, n, m, D, T, h, seed):
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, seed)
+    ref = oracle.gp_predict(X, y, Xs, h)
+    ctx = api.Context(0, tile=T)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*h))
+    K = api.gp_factor_rows(ctx, f).cpu().numpy()
+    api.gp_cholesky(ctx, f)
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+    alpha = api.gp_alpha(ctx, f)
+    cov = api.gp_predict_full_cov(ctx, f, Xsd)
+    logdet = api.gp_logdet(ctx, f)
+    api.gp_sync(ctx)
+    assert ctx.launch_count() > 0
+    Kref = np.tril(ref["K"])
+    assert rel(K, Kref) <= 1e-14
+    assert np.linalg.norm(L @ L.T - ref["K"]) / np.linalg.norm(ref["K"]) <= 1e-13
+    assert np.all(np.triu(L, 1) == 0)
+    assert rel(L, ref["L"]) <= 1e-12
+    assert rel(alpha.cpu().numpy(), ref["alpha"]) <= 1e-10
+    assert rel(mean.cpu().numpy(), ref["mean"]) <= 1e-10
+    c = cov.cpu().numpy()
+    assert rel(c, ref["cov"]) <= 1e-9
+    assert np.array_equal(c, c.T)
+    assert abs(logdet - ref["logdet"]) <= 1e-12 * max(1.0, abs(ref["logdet"]))
+    f.free()
+
+
+def test_noisy_prior_adds_s2(api):
+    X, y, Xs, _ = nfir.make_dataset(200, 50, 8, 7)
+    ref = oracle.gp_predict(X, y, Xs, H0, noisy_prior=True)
+    ctx = api.Context(0, tile=64, noisy_prior=True)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    mean, cov = api.predict(Xd, yd, Xsd, api.Hyper(*H0), ctx=ctx)
+    assert rel(cov.cpu().numpy(), ref["cov"]) <= 1e-9
+
+
+def test_tile_size_invariance(api):
+    """Same factor and predictions for every tile edge, up to rounding (Sec. 3.2's tiling is exact)."""
+    X, y, Xs, _ = nfir.make_dataset(600, 90, 8, 9)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    outs = []
+    for T in (32, 64, 160, 256, 640):
+        ctx = api.Context(0, tile=T)
+        outs.append([t.cpu().numpy() for t in api.predict(Xd, yd, Xsd, api.Hyper(*H0), ctx=ctx)])
+    for mean, cov in outs[1:]:
+        assert rel(mean, outs[0][0]) <= 1e-11
+        assert rel(cov, outs[0][1]) <= 1e-11
+
+
+def test_repeatable_bitwise(api):
+    """Updates into each tile are applied in increasing J order whatever the schedule, so two runs
+    (and two CTA counts) give bit-identical factors."""
+    X, y, Xs, _ = nfir.make_dataset(900, 10, 8, 11)
+    (Xd,) = to_dev(X)
+    Ls = []
+    for grid in (0, 37, 0):
+        ctx = api.Context(0, tile=64, grid=grid)
+        f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+        api.gp_cholesky(ctx, f)
+        Ls.append(api.gp_factor_rows(ctx, f).cpu().numpy())
+        api.gp_sync(ctx)
+    assert np.array_equal(Ls[0], Ls[1]) and np.array_equal(Ls[0], Ls[2])
+
+
+def test_not_positive_definite_reports_column(api):
+    """Duplicate points with s2 = 0: the second copy's pivot is exactly 0 (Q3 reading)."""
+    X = np.array([[0.0], [1.0], [0.0]])
+    ctx = api.Context(0, tile=32)
+    (Xd,) = to_dev(X)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(1.0, 1.0, 0.0))
+    api.gp_cholesky(ctx, f)
+    with pytest.raises(api.GPError) as e:
+        api.gp_sync(ctx)
+    assert e.value.status == 2 and e.value.info == 3
+    # the context stays usable after the error is collected
+    f2 = api.gp_assemble(ctx, Xd, api.Hyper(1.0, 1.0, 0.1))
+    api.gp_cholesky(ctx, f2)
+    api.gp_sync(ctx)
+
+
+def test_withheld_task_times_out_and_context_survives(api):
+    """A task whose completion is never published makes its dependants' bounded waits expire: the
+    persistent kernel returns GP_ERR_TIMEOUT instead of hanging, and the GPU stays usable."""
+    X, y, Xs, _ = nfir.make_dataset(512, 8, 8, 12)
+    (Xd,) = to_dev(X)
+    ctx = api.Context(0, tile=64, timeout_s=0.2, withhold_task=0)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    with pytest.raises(api.GPError) as e:
+        api.gp_sync(ctx)
+    assert e.value.status == 6
+    ctx2 = api.Context(0, tile=64)
+    f2 = api.gp_assemble(ctx2, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx2, f2)
+    L = api.gp_factor_rows(ctx2, f2).cpu().numpy()
+    api.gp_sync(ctx2)
+    assert rel(L, oracle.cholesky(oracle.assemble_K(X, H0))) <= 1e-12
+
+
+def test_invalid_arguments(api):
+    ctx = api.Context(0)
+    X = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(api.GPError):
+        api.gp_assemble(ctx, X, api.Hyper(-1.0, 1.0, 0.1))
+    with pytest.raises(TypeError):
+        api.gp_assemble(ctx, X.float(), api.Hyper())
+    with pytest.raises(api.GPError):
+        api.Context(0, tile=48)
+
+
+def test_full_size_sampled(api):
+    """The large workload (n = 32768 training, m = 4096 test, D = 8) with the benchmark's launch
+    configuration. Checked at sampled entries against the oracle: LL^T = K on sampled entries of K
+    (recomputed by the oracle), the residual y - K alpha on sampled rows, the mean from alpha, and
+    sampled covariance entries k(a,b) - v_a^T v_b with v_a = L^{-1} k_a by the oracle's forward
+    substitution on the GPU's factor."""
+    n, m, D = 32768, 4096, 8
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
+    ctx = api.Context(0)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+    alpha = api.gp_alpha(ctx, f).cpu().numpy()
+    cov = api.gp_predict_full_cov(ctx, f, Xsd)
+    api.gp_sync(ctx)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(n, 24, replace=False))
+    Lrows = np.concatenate([api.gp_factor_rows(ctx, f, int(r), 1).cpu().numpy() for r in rows])
+    # (L L^T)_ij = L_i . L_j for sampled i, j against K_ij from the oracle's kernel
+    ii, jj = np.meshgrid(np.arange(len(rows)), np.arange(len(rows)), indexing="ij")
+    LLt = Lrows @ Lrows.T
+    Kij = oracle.kernel_entries(X, X, rows[ii.ravel()], rows[jj.ravel()], rows[ii.ravel()] == rows[jj.ravel()], H0)
+    assert rel(LLt.ravel(), Kij) <= 1e-13
+    # residual of K alpha = y on sampled rows (backward-stable solve: ~ n eps ||K|| ||alpha||)
+    r = y[rows] - oracle.kernel_rows_matvec(X, rows, alpha, H0)
+    assert np.max(np.abs(r)) <= 1e-9 * np.max(np.abs(y))
+    cols = np.sort(rng.choice(m, 16, replace=False))
+    mref = oracle.assemble_cross(Xs[cols], X, H0) @ alpha
+    assert rel(mean.cpu().numpy()[cols], mref) <= 1e-10
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    ks = oracle.assemble_cross(Xs[cols], X, H0)  # 16 x n
+    V = oracle.forward(L, np.ascontiguousarray(ks.T))
+    cref = oracle.assemble_prior(Xs[cols], H0) - V.T @ V
+    c = cov.cpu().numpy()[np.ix_(cols, cols)]
+    assert rel(c, cref) <= 1e-9
