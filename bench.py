@@ -48,8 +48,10 @@ def parse():
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-n", type=int, default=6144, help="oracle sample size for the CPU baseline")
-    p.add_argument("--cpu-m", type=int, default=768)
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (GP_FP32) leg")
+    p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
+    p.add_argument("--cpu-n", type=int, default=8192, help="oracle sample size for the CPU baseline")
+    p.add_argument("--cpu-m", type=int, default=1024)
     p.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference-arm step")
     p.add_argument("--ref-m", type=int, default=512)
     return p.parse_args()
@@ -266,6 +268,48 @@ def run_ours(args):
             e2e_ms = s0.elapsed_time(s1) / args.steps
             e2e = {"ms": e2e_ms, "h2d": (X.nbytes + y.nbytes + Xs.nbytes), "d2h": (m + m * m) * 8}
 
+        # mixed-precision leg: same workload, GP_FP32 mode, errors against this run's FP64 results
+        mixed = None
+        if not args.no_mixed and args.precision == "fp64":
+            mean64, cov64 = mean.clone(), cov.clone()
+            logdet64 = api.gp_logdet(ctx, fac[0])
+            ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32")
+            fac32 = [None]
+            mean32 = torch.empty_like(mean)
+            cov32 = torch.empty_like(cov)
+            iters = [0]
+
+            def step32():
+                fac32[0] = api.gp_assemble(ctx32, Xd, h, fac32[0])
+                api.gp_cholesky(ctx32, fac32[0])
+                _, iters[0] = api.gp_predict_mean(ctx32, fac32[0], yd, Xsd, out=mean32, want_iters=True)
+                api.gp_predict_full_cov(ctx32, fac32[0], Xsd, out=cov32)
+
+            for _ in range(args.warmup):
+                step32()
+            api.gp_sync(ctx32)
+            barrier()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(args.steps):
+                step32()
+            m1.record(stream)
+            barrier()
+            api.gp_sync(ctx32)
+            ms32 = m0.elapsed_time(m1) / args.steps
+            logdet32 = api.gp_logdet(ctx32, fac32[0])
+
+            def relerr(a, b):
+                return float((a - b).abs().max() / b.abs().max())
+            mixed = {"precision": "fp32 trailing updates, FP64 POTRF/first-column TRSM/refinement",
+                     "s_per_solve": ms32 / 1e3, "tflops": algorithmic_flops(n, m) / (ms32 / 1e3) / 1e12,
+                     "speedup_vs_fp64": ms / ms32, "ir_iterations": iters[0],
+                     "mean_err_vs_fp64": relerr(mean32, mean64), "cov_err_vs_fp64": relerr(cov32, cov64),
+                     "logdet_err_vs_fp64": abs(logdet32 - logdet64) / abs(logdet64)}
+            fac32[0].free()
+            ctx32.close()
+
     t = torch.tensor([ms, chol_ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -291,6 +335,8 @@ def run_ours(args):
                          "peak_source": "FP64 FFMA pipe: 2 FMA/clk/SM x 152 SMs x max SM clock (derived)",
                          "traffic": None},
             "gpu_launches": launches, "clocks": clocks}
+    if mixed:
+        line["mixed"] = mixed
     if e2e:
         line["e2e"] = {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
@@ -302,6 +348,23 @@ def run_ours(args):
                                 "cores": cpu_cores(), "kind": "oracle",
                                 "sample": f"one oracle pipeline pass at n={args.cpu_n}, m={args.cpu_m}, D={D} "
                                           f"({secs:.1f} s), same FLOP/s metric"}
+    if rank == 0 and not args.no_vendor:
+        fac[0].free()
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        from paper_2602_19683_gb300 import baselines
+        try:
+            v = baselines.run(n)
+            dp = v.get("cusolver_dpotrf", {})
+            line["vendor"] = {"cusolver_dpotrf_s": dp.get("ms", float("nan")) / 1e3,
+                              "cusolver_spotrf_s": v.get("cusolver_spotrf", {}).get("ms", float("nan")) / 1e3,
+                              "cholesky_speedup_vs_cusolver_dpotrf": dp.get("ms", float("nan")) / chol_ms,
+                              "ffma64_tflops": v.get("ffma64", {}).get("tflops"),
+                              "dmma_tflops": v.get("dmma_m8n8k4", {}).get("tflops"),
+                              "ffma32_tflops": v.get("ffma32", {}).get("tflops"),
+                              "cublas_dgemm_tflops": v.get("cublas_dgemm", {}).get("tflops")}
+        except Exception as e:  # the baseline leg must not hide the measured line
+            line["vendor"] = {"error": str(e)[:200]}
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -142,8 +142,8 @@ gp_status gp_sync(gp_ctx* ctx, int64_t* info);
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch)) into out (host, room
  * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
-int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t* out,
-                          int64_t cap);
+int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
+                          int32_t* out, int64_t cap);
 
 /* Human-readable name of a status code (static string). */
 const char* gp_status_string(gp_status s);

@@ -45,7 +45,7 @@ SIGNATURES = {
     "gp_sync": ([_P, ctypes.POINTER(_I64)], _I32),
     "gp_status_string": ([_I32], ctypes.c_char_p),
     "gp_launch_count": ([_P], _I64),
-    "gp_schedule_tasks": ([_I32, _I32, _I32, _I32, _I32, _P, _I64], _I64),
+    "gp_schedule_tasks": ([_I32, _I32, _I32, _I32, _I32, _I32, _P, _I64], _I64),
 }
 
 _lock = threading.Lock()

@@ -1,0 +1,194 @@
+// Vendor baselines and pipe-throughput probes on the same GPU (never on libgp's product path):
+//   cuSOLVER Dpotrf / Spotrf on an n x n SPD matrix (the single-call factorisation the paper's
+//   tiled approach is compared with in Sec. 4.1), cuBLAS DGEMM, and register-only FP64 FFMA,
+//   FP64 mma.sync (DMMA) and FP32 FFMA loops that bound what FMA-issue-bound kernels can reach.
+// Prints one JSON object per measurement. Usage: vendor_baselines [n] [--no-potrf]
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#define CK(x)                                                                   \
+  do {                                                                          \
+    cudaError_t e = (x);                                                        \
+    if (e != cudaSuccess) {                                                     \
+      printf("{\"error\": \"%s\", \"line\": %d}\n", cudaGetErrorString(e), __LINE__); \
+      exit(1);                                                                  \
+    }                                                                           \
+  } while (0)
+
+__global__ void ffma64_loop(double* out, int iters, double a, double b) {
+  double x[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = threadIdx.x + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = fma(x[j], a, b);
+  double s = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void ffma32_loop(float* out, int iters, float a, float b) {
+  float x[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = threadIdx.x + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = fmaf(x[j], a, b);
+  float s = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void dmma_loop(double* out, int iters) {
+  double a = 1.0 + threadIdx.x * 1e-3, b = 1.0 - threadIdx.x * 1e-3;
+  double c[8][2];
+  for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = 0;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(c[j][0]), "+d"(c[j][1])
+                   : "d"(a), "d"(b));
+  double s = 0;
+  for (int j = 0; j < 8; ++j) s += c[j][0] + c[j][1];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// A = exp(-((i-j)/64)^2) + 0.1 I: symmetric positive definite.
+__global__ void fill_spd(double* A, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    const double d = (double)(i - j) / 64.0;
+    A[e] = exp(-d * d) + (i == j ? 0.1 : 0.0);
+  }
+}
+__global__ void to_float(const double* A, float* B, long long cnt) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    B[e] = (float)A[e];
+}
+
+template <class F>
+float best_ms(F f, int reps) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  f();
+  CK(cudaDeviceSynchronize());
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0);
+    f();
+    cudaEventRecord(e1);
+    CK(cudaEventSynchronize(e1));
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  return best;
+}
+
+int main(int argc, char** argv) {
+  long long n = 32768;
+  bool potrf = true;
+  for (int i = 1; i < argc; ++i) {
+    if (!strcmp(argv[i], "--no-potrf")) potrf = false;
+    else n = atoll(argv[i]);
+  }
+  cudaDeviceProp p;
+  CK(cudaGetDeviceProperties(&p, 0));
+  const int sms = p.multiProcessorCount;
+  double* out;
+  CK(cudaMalloc(&out, sizeof(double) * sms * 2048));
+  {
+    const int grid = sms * 8, iters = 4000;
+    float ms = best_ms([&] { ffma64_loop<<<grid, 256>>>(out, iters, 0.999, 1e-3); }, 3);
+    printf("{\"probe\": \"ffma64\", \"tflops\": %.4f}\n", 2.0 * 16 * iters * (double)grid * 256 / ms / 1e9);
+  }
+  {
+    const int grid = sms * 8, iters = 2000;
+    float ms = best_ms([&] { ffma32_loop<<<grid, 256>>>((float*)out, iters, 0.999f, 1e-3f); }, 3);
+    printf("{\"probe\": \"ffma32\", \"tflops\": %.4f}\n", 2.0 * 128 * iters * (double)grid * 256 / ms / 1e9);
+  }
+  {
+    const int grid = sms * 4, iters = 400;
+    float ms = best_ms([&] { dmma_loop<<<grid, 256>>>(out, iters); }, 3);
+    printf("{\"probe\": \"dmma_m8n8k4\", \"tflops\": %.4f}\n", 2.0 * 256 * 8 * iters * (double)grid * 8 / ms / 1e9);
+  }
+  fflush(stdout);
+  double* A;
+  CK(cudaMalloc(&A, sizeof(double) * n * n));
+  cublasHandle_t bh;
+  cublasCreate(&bh);
+  {
+    const int N = 8192;
+    double *B, *C;
+    CK(cudaMalloc(&B, sizeof(double) * N * N));
+    CK(cudaMalloc(&C, sizeof(double) * N * N));
+    fill_spd<<<4096, 256>>>(B, N);
+    const double one = 1, zero = 0;
+    float ms = best_ms([&] { cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_T, N, N, N, &one, B, N, B, N, &zero, C, N); }, 2);
+    printf("{\"probe\": \"cublas_dgemm\", \"n\": %d, \"tflops\": %.4f}\n", N, 2.0 * N * N * (double)N / ms / 1e9);
+    cudaFree(B);
+    cudaFree(C);
+  }
+  fflush(stdout);
+  if (potrf) {
+    cusolverDnHandle_t sh;
+    cusolverDnCreate(&sh);
+    int* info;
+    CK(cudaMalloc(&info, sizeof(int)));
+    int lw = 0;
+    cusolverDnDpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, &lw);
+    double* W;
+    CK(cudaMalloc(&W, sizeof(double) * (lw + 1)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < 2; ++r) {  // first call warms up
+      fill_spd<<<4096, 256>>>(A, n);
+      CK(cudaDeviceSynchronize());
+      cudaEventRecord(e0);
+      cusolverDnDpotrf(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, W, lw, info);
+      cudaEventRecord(e1);
+      CK(cudaEventSynchronize(e1));
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) best = ms;
+    }
+    int hinfo = -1;
+    cudaMemcpy(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost);
+    printf("{\"probe\": \"cusolver_dpotrf\", \"n\": %lld, \"ms\": %.3f, \"tflops\": %.4f, \"info\": %d}\n", n, best,
+           (double)n * n * (double)n / 3.0 / best / 1e9, hinfo);
+    fflush(stdout);
+    float* Af;
+    CK(cudaMalloc(&Af, sizeof(float) * n * n));
+    int lwf = 0;
+    cusolverDnSpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, (int)n, Af, (int)n, &lwf);
+    float* Wf;
+    CK(cudaMalloc(&Wf, sizeof(float) * (lwf + 1)));
+    for (int r = 0; r < 2; ++r) {
+      fill_spd<<<4096, 256>>>(A, n);
+      to_float<<<4096, 256>>>(A, Af, n * n);
+      CK(cudaDeviceSynchronize());
+      cudaEventRecord(e0);
+      cusolverDnSpotrf(sh, CUBLAS_FILL_MODE_LOWER, (int)n, Af, (int)n, Wf, lwf, info);
+      cudaEventRecord(e1);
+      CK(cudaEventSynchronize(e1));
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) best = ms;
+    }
+    printf("{\"probe\": \"cusolver_spotrf\", \"n\": %lld, \"ms\": %.3f, \"tflops\": %.4f}\n", n, best,
+           (double)n * n * (double)n / 3.0 / best / 1e9);
+  }
+  return 0;
+}

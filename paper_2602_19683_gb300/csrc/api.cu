@@ -53,7 +53,7 @@ gp_status cuda_status(cudaError_t e) {
   } while (0)
 #define GP_CUDA(x) GP_TRY(cuda_status(x))
 
-using TaskKey = std::tuple<int, int, int, int, int>;  // graph kind, Mt, Mc, T, workers
+using TaskKey = std::tuple<int, int, int, int, int, int>;  // graph kind, Mt, Mc, T, workers, mixed
 
 struct TaskBuf {
   DevBuf buf;
@@ -67,8 +67,8 @@ struct gp_ctx {
   cudaStream_t stream = nullptr;
   gp_config cfg{};
   int sms = 0;
-  int ctas_per_sm = 1;
-  int grid = 0;
+  int ctas_per_sm[2] = {1, 1};  // [0] FP64 kernel, [1] mixed kernel
+  int grid[2] = {0, 0};
   gpk::DevStatus* d_status = nullptr;
   double* d_scalar = nullptr;  // small device scratch for scalar results
   long long launches = 0;
@@ -81,7 +81,9 @@ struct gp_factor {
   gp_hyper h{};
   const double* X = nullptr;  // caller's device array (not owned)
   DevBuf Kt, cK;              // packed lower tiles and their counters
-  DevBuf bvec, cMean;         // y -> beta -> alpha, and the solve counters
+  DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
+  DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
+  DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
   DevBuf V, S, cCov;          // covariance workspace
   bool factored = false, alpha_valid = false;
 };
@@ -97,22 +99,24 @@ int auto_tile(long long n) {
   return 32;
 }
 
-gpk::CostModel cost_model(const gp_ctx* c) {
+gpk::CostModel cost_model(const gp_ctx* c, bool mixed) {
   gpk::CostModel cm;
-  // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it.
-  cm.sec_per_flop = (double)c->ctas_per_sm / 7.8e9;
+  // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
+  cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
+  cm.sec_per_flop32 = 1.0 / 3.0e11;
+  cm.mixed = mixed;
   return cm;
 }
 
 // Returns the device task list of graph `kind` (0 Cholesky, 1 covariance, 2 mean), building and
 // uploading it on first use.
-gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, const TaskBuf** out) {
-  const int workers = c->grid;
-  TaskKey key{kind, Mt, Mc, T, workers};
+gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, const TaskBuf** out) {
+  const int workers = c->grid[mixed ? 1 : 0];
+  TaskKey key{kind, Mt, Mc, T, workers, mixed ? 1 : 0};
   auto it = c->tasks.find(key);
   if (it == c->tasks.end()) {
     std::vector<gpk::Task4> v;
-    const gpk::CostModel cm = cost_model(c);
+    const gpk::CostModel cm = cost_model(c, mixed);
     if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
     if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
@@ -141,15 +145,33 @@ gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
   return a;
 }
 
-gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb) {
+gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb, bool mixed) {
   if (tb->ntasks == 0) return GP_OK;
   GP_CUDA(cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), c->stream));
   a.tasks = (const int4*)tb->buf.p;
   a.ntasks = tb->ntasks;
-  const int grid = c->grid < tb->ntasks ? c->grid : tb->ntasks;
-  GP_CUDA(gpk::launch_dag(a, grid, c->stream));
+  const int g = c->grid[mixed ? 1 : 0];
+  const int grid = g < tb->ntasks ? g : tb->ntasks;
+  GP_CUDA(gpk::launch_dag(a, grid, mixed, c->stream));
   count_launch(c);
   return GP_OK;
+}
+
+// Mean-solve DAG (L beta = b, L^T x = beta) on f->bvec in place; FP64 arithmetic in both modes.
+gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
+  const int T = f->T, Mt = f->Mt, nch = T / 32;
+  const size_t ncnt = (size_t)Mt * nch * 2 + (size_t)Mt * 2;
+  GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 2, Mt, 0, T, false, &tb));
+  gpk::DagArgs a = base_args(c, f);
+  a.bvec = (double*)f->bvec.p;
+  int* cm = (int*)f->cMean.p;
+  a.cF = cm;
+  a.cB = cm + (size_t)Mt * nch;
+  a.dF = cm + (size_t)Mt * nch * 2;
+  a.dB = a.dF + Mt;
+  return run_dag(c, a, tb, false);
 }
 
 bool valid_hyper(const gp_hyper& h) {
@@ -200,10 +222,13 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   ctx->stream = (cudaStream_t)stream;
   ctx->cfg = c;
   ctx->sms = prop.multiProcessorCount;
-  int occ = gpk::dag_max_ctas_per_sm();
-  ctx->ctas_per_sm = occ >= 2 ? 2 : 1;
-  ctx->grid = c.grid > 0 ? c.grid : ctx->sms * ctx->ctas_per_sm;
-  if (c.grid > 0) ctx->ctas_per_sm = (c.grid + ctx->sms - 1) / ctx->sms;
+  for (int mixed = 0; mixed < 2; ++mixed) {
+    const int occ = gpk::dag_max_ctas_per_sm(mixed != 0);
+    const int cap = mixed ? 1 : 2;
+    ctx->ctas_per_sm[mixed] = occ >= cap ? cap : (occ > 0 ? occ : 1);
+    ctx->grid[mixed] = c.grid > 0 ? c.grid : ctx->sms * ctx->ctas_per_sm[mixed];
+    if (c.grid > 0) ctx->ctas_per_sm[mixed] = (c.grid + ctx->sms - 1) / ctx->sms;
+  }
   if (cudaMalloc(&ctx->d_status, sizeof(gpk::DevStatus)) != cudaSuccess ||
       cudaMalloc(&ctx->d_scalar, 64 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -242,10 +267,11 @@ gp_status gp_set_stream(gp_ctx* c, void* stream) {
 
 int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
 
-int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t* out,
-                          int64_t cap) {
+int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
+                          int32_t* out, int64_t cap) {
   if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 2) return -1;
   gpk::CostModel cm;
+  cm.mixed = mixed != 0;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
@@ -279,6 +305,10 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   cudaStreamSynchronize(c->stream);
   release(f->Kt);
   release(f->cK);
+  release(f->Kt0);
+  release(f->alpha);
+  release(f->rvec);
+  release(f->part);
   release(f->bvec);
   release(f->cMean);
   release(f->V);
@@ -301,8 +331,10 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
     if (!f) return GP_ERR_OOM;
   }
   const size_t ntiles = (size_t)Mt * (Mt + 1) / 2;
+  const bool mixed = c->cfg.precision == GP_FP32;
   gp_status s = grow(f->Kt, ntiles * T * T * sizeof(double));
   if (s == GP_OK) s = grow(f->cK, ntiles * sizeof(int));
+  if (s == GP_OK && mixed) s = grow(f->Kt0, ntiles * T * T * sizeof(double));
   if (s != GP_OK) {
     if (fresh) gp_factor_free(c, f);
     return s;
@@ -318,6 +350,8 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   f->alpha_valid = false;
   GP_CUDA(gpk::launch_assemble_tiles(X, n, D, h.l, h.v, h.s2, (double*)f->Kt.p, T, (int)Mt, c->stream));
   count_launch(c);
+  if (mixed)
+    GP_CUDA(cudaMemcpyAsync(f->Kt0.p, f->Kt.p, ntiles * T * T * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   *K_out = f;
   return GP_OK;
 }
@@ -326,11 +360,12 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   if (!c || !f || !f->Kt.p) return GP_ERR_INVALID_ARG;
   if (f->factored) return GP_ERR_INVALID_ARG;  // already holds L
   GP_CUDA(cudaSetDevice(c->device));
+  const bool mixed = f->precision == GP_FP32;
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, &tb));
+  GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, mixed, &tb));
   const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
   GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
-  GP_TRY(run_dag(c, base_args(c, f), tb));
+  GP_TRY(run_dag(c, base_args(c, f), tb, mixed));
   f->factored = true;
   return GP_OK;
 }
@@ -341,30 +376,51 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   GP_CUDA(cudaSetDevice(c->device));
   const int T = f->T, Mt = f->Mt, nch = T / 32;
   const size_t npad = (size_t)Mt * T;
+  const bool mixed = f->precision == GP_FP32;
   GP_TRY(grow(f->bvec, npad * sizeof(double)));
-  const size_t ncnt = (size_t)Mt * nch * 2 + (size_t)Mt * 2;
-  GP_TRY(grow(f->cMean, ncnt * sizeof(int)));
+  GP_TRY(grow(f->alpha, npad * sizeof(double)));
+  GP_TRY(grow(f->cMean, ((size_t)Mt * nch * 2 + (size_t)Mt * 2) * sizeof(int)));
+  // alpha = L^{-T} L^{-1} y (Eq. 2's two substitutions)
   GP_CUDA(cudaMemsetAsync(f->bvec.p, 0, npad * sizeof(double), c->stream));
   GP_CUDA(cudaMemcpyAsync(f->bvec.p, y, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
-  const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 2, Mt, 0, T, &tb));
-  gpk::DagArgs a = base_args(c, f);
-  a.bvec = (double*)f->bvec.p;
-  int* cm = (int*)f->cMean.p;
-  a.cF = cm;
-  a.cB = cm + (size_t)Mt * nch;
-  a.dF = cm + (size_t)Mt * nch * 2;
-  a.dB = a.dF + Mt;
-  GP_TRY(run_dag(c, a, tb));
+  GP_TRY(solve_in_place(c, f));
+  GP_CUDA(cudaMemcpyAsync(f->alpha.p, f->bvec.p, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  gp_status result = GP_OK;
+  int iters = 0;
+  if (mixed) {
+    // Classic iterative refinement: r = y - K alpha in FP64 against the stored FP64 K, correction
+    // through the mixed-precision factor, until ||r|| / ||y|| <= ir_tol.
+    GP_TRY(grow(f->rvec, npad * sizeof(double)));
+    GP_TRY(grow(f->part, (size_t)2 * Mt * nch * sizeof(double)));
+    bool converged = false;
+    for (int it = 0;; ++it) {
+      GP_CUDA(gpk::launch_residual((const double*)f->Kt0.p, T, Mt, f->n, y, (const double*)f->alpha.p,
+                                   (double*)f->bvec.p, (double*)f->part.p, c->d_scalar, c->stream));
+      count_launch(c, 2);
+      double norms[2];
+      GP_CUDA(cudaMemcpyAsync(norms, c->d_scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      GP_CUDA(cudaStreamSynchronize(c->stream));
+      if (!(norms[0] == norms[0])) break;  // NaN: the device status (if any) reports why
+      if (std::sqrt(norms[0]) <= c->cfg.ir_tol * std::sqrt(norms[1])) {
+        converged = true;
+        break;
+      }
+      if (it >= c->cfg.ir_maxit) break;
+      GP_TRY(solve_in_place(c, f));  // bvec = K~^{-1} r
+      GP_CUDA(gpk::launch_axpy((double*)f->alpha.p, (const double*)f->bvec.p, f->n, c->stream));
+      count_launch(c);
+      ++iters;
+    }
+    if (!converged) result = GP_ERR_NO_CONVERGENCE;
+  }
   f->alpha_valid = true;
   if (m > 0) {
-    GP_CUDA(gpk::launch_mean_gemv(Xs, m, f->X, f->n, f->D, f->h.l, f->h.v, (const double*)f->bvec.p, mean_out,
+    GP_CUDA(gpk::launch_mean_gemv(Xs, m, f->X, f->n, f->D, f->h.l, f->h.v, (const double*)f->alpha.p, mean_out,
                                   c->stream));
     count_launch(c);
   }
-  if (ir_iters_out) *ir_iters_out = 0;
-  return GP_OK;
+  if (ir_iters_out) *ir_iters_out = iters;
+  return result;
 }
 
 gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, double* cov_out) {
@@ -386,8 +442,9 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
                                      (double*)f->S.p, (long long)ldv, (long long)ldv, (long long)ldv, c->stream));
   count_launch(c, 2);
   GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
+  const bool mixed = f->precision == GP_FP32;
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 1, Mt, (int)Mc, T, &tb));
+  GP_TRY(get_tasks(c, 1, Mt, (int)Mc, T, mixed, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.V = (double*)f->V.p;
   a.ldv = (long long)ldv;
@@ -396,7 +453,7 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   a.lds = (long long)ldv;
   a.cV = (int*)f->cCov.p;
   a.cS = a.cV + (size_t)Mt * Mc;
-  GP_TRY(run_dag(c, a, tb));
+  GP_TRY(run_dag(c, a, tb, mixed));
   GP_CUDA(gpk::launch_cov_copy((const double*)f->S.p, (long long)ldv, cov_out, m, c->stream));
   count_launch(c);
   return GP_OK;
@@ -413,7 +470,7 @@ gp_status gp_factor_rows(gp_ctx* c, const gp_factor* f, int64_t row0, int64_t nr
 gp_status gp_alpha(gp_ctx* c, const gp_factor* f, double* out) {
   if (!c || !f || !out || !f->alpha_valid) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
-  GP_CUDA(cudaMemcpyAsync(out, f->bvec.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  GP_CUDA(cudaMemcpyAsync(out, f->alpha.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   return GP_OK;
 }
 

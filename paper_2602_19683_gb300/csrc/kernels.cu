@@ -4,7 +4,7 @@
 #include <climits>
 
 #include "kernels.h"
-#include "tiles_f64.cuh"
+#include "tiles_f32.cuh"
 
 namespace gpk {
 
@@ -166,10 +166,20 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
   return false;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) dag_kernel(DagArgs a) {
-  __shared__ TileSmem s;
+// The persistent kernel: each CTA repeatedly takes the next task in dispatch order, waits (bounded)
+// until the counters of the tiles it reads say their producers are done, runs the tile operation,
+// and publishes its own tile's counter. kMixed selects FP32 arithmetic for the trailing updates,
+// the panel TRSMs after the first block column and the covariance solve; POTRF, the first block
+// column's TRSM and the vector solves stay FP64.
+template <bool kMixed>
+__global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a) {
+  __shared__ union {
+    TileSmem d;
+    TileSmemF32 f;
+  } u;
   __shared__ int s_task;
   __shared__ double s_red[kThreads / 32][32];
+  TileSmem& s = u.d;
   const int T = a.T;
   const size_t TT = (size_t)T * T;
   while (true) {
@@ -195,24 +205,37 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(DagArgs a) {
         break;
       }
       case TASK_TRSM:
-        cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
+        if (kMixed && q > 0)
+          cta_trsm_right_f32(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, u.f);
+        else
+          cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
       case TASK_UPD:
-        cta_gemm_sub<A_MK, B_NK>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T, T,
-                                 p == q, 0, s.g);
+        if (kMixed)
+          cta_gemm_sub_f32<0, 0>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T,
+                                 T, p == q, u.f.g);
+        else
+          cta_gemm_sub<A_MK, B_NK>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T,
+                                   T, T, p == q, 0, s.g);
         cta_publish(a.cK + tri(p, q), r + 1);
         break;
       case TASK_VTRSM: {
         double* B = a.V + (size_t)p * T * a.ldv + (size_t)q * T;
-        cta_trsm_left(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, s);
+        if (kMixed)
+          cta_trsm_left_f32(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, u.f);
+        else
+          cta_trsm_left(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, s);
         cta_publish(a.cV + (size_t)p * a.Mc + q, p + 1);
         break;
       }
       case TASK_VGEMM: {
         double* C = a.V + (size_t)p * T * a.ldv + (size_t)r * T;
         const double* B = a.V + (size_t)q * T * a.ldv + (size_t)r * T;
-        cta_gemm_sub<A_MK, B_KN>(C, (int)a.ldv, a.Kt + tri(p, q) * TT, T, B, (int)a.ldv, T, T, T, false, 0, s.g);
+        if (kMixed)
+          cta_gemm_sub_f32<0, 1>(C, (int)a.ldv, a.Kt + tri(p, q) * TT, T, B, (int)a.ldv, T, T, T, false, u.f.g);
+        else
+          cta_gemm_sub<A_MK, B_KN>(C, (int)a.ldv, a.Kt + tri(p, q) * TT, T, B, (int)a.ldv, T, T, T, false, 0, s.g);
         cta_publish(a.cV + (size_t)p * a.Mc + r, q + 1);
         break;
       }
@@ -220,12 +243,15 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(DagArgs a) {
         double* C = a.S + (size_t)p * T * a.lds + (size_t)q * T;
         const double* Va = a.V + (size_t)r * T * a.ldv + (size_t)p * T;
         const double* Vb = a.V + (size_t)r * T * a.ldv + (size_t)q * T;
-        cta_gemm_sub<A_KM, B_KN>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, 0, s.g);
+        if (kMixed)
+          cta_gemm_sub_f32<1, 1>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, u.f.g);
+        else
+          cta_gemm_sub<A_KM, B_KN>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, 0, s.g);
         cta_publish(a.cS + tri(p, q), r + 1);
         break;
       }
       case TASK_FSOLVE:
-        cta_trsv_lower(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0]);
+        cta_trsv_lower(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
         cta_publish(a.dF + p, 1);
         break;
       case TASK_FGEMV:
@@ -234,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(DagArgs a) {
         cta_publish(a.cF + (size_t)p * a.nch + r, q + 1);
         break;
       case TASK_BSOLVE:
-        cta_trsv_lower_T(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0]);
+        cta_trsv_lower_T(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
         cta_publish(a.dB + p, 1);
         break;
       case TASK_BGEMV:
@@ -244,6 +270,102 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(DagArgs a) {
         break;
     }
   }
+}
+
+// r = y - K alpha for the 32 rows (tile row I = blockIdx.x / nch, chunk ch) from the packed lower
+// FP64 tiles of the symmetric K (diagonal tiles hold both triangles): row part from tiles (I, J<=I),
+// transposed part from tiles (J>I, I). Per-block partial sums of r^2 and y^2 go to partial[2b..2b+1].
+__global__ void __launch_bounds__(kThreads) residual_kernel(const double* __restrict__ Kt, int T, int Mt,
+                                                            long long n, const double* __restrict__ y,
+                                                            const double* __restrict__ alpha, double* __restrict__ r,
+                                                            double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32][32];
+  const int nch = T / 32;
+  const int I = blockIdx.x / nch, ch = blockIdx.x % nch;
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const size_t TT = (size_t)T * T;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // rows ch*32 + w*4 + k, lane-partial
+  for (int J = 0; J <= I; ++J) {
+    const double* tile = Kt + tri(I, J) * TT + (size_t)(ch * 32 + w * 4) * T;
+    const double* aJ = alpha + (size_t)J * T;
+    for (int c = lane; c < T; c += 32) {
+      const double av = aJ[c];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = fma(tile[(size_t)k * T + c], av, acc[k]);
+    }
+  }
+  double accT = 0.0;  // column ch*32 + lane, warp-partial over rows
+  for (int J = I + 1; J < Mt; ++J) {
+    const double* tile = Kt + tri(J, I) * TT + ch * 32 + lane;
+    const double* aJ = alpha + (size_t)J * T;
+    for (int rr = w; rr < T; rr += kThreads / 32) accT = fma(tile[(size_t)rr * T], aJ[rr], accT);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  }
+  red[w][lane] = accT;
+  __syncthreads();
+  __shared__ double rowsum[32];
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q][threadIdx.x];
+    rowsum[threadIdx.x] = t;
+  }
+  __syncthreads();
+  __shared__ double sq[2][32];
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int row = ch * 32 + w * 4 + k;
+      const long long gi = (long long)I * T + row;
+      const double tot = acc[k] + rowsum[w * 4 + k];
+      const double yi = gi < n ? y[gi] : 0.0;
+      const double ri = gi < n ? yi - tot : 0.0;
+      r[gi] = ri;
+      sq[0][w * 4 + k] = ri * ri;
+      sq[1][w * 4 + k] = yi * yi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += sq[threadIdx.x][k];
+    partial[2 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// out[0] = sum of even partials (||r||^2), out[1] = sum of odd partials (||y||^2); one CTA.
+__global__ void __launch_bounds__(kThreads) sum_pairs_kernel(const double* __restrict__ partial, int nb,
+                                                             double* __restrict__ out) {
+  __shared__ double red[2][kThreads / 32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    s0 += partial[2 * b];
+    s1 += partial[2 * b + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (threadIdx.x % 32 == 0) {
+    red[0][threadIdx.x / 32] = s0;
+    red[1][threadIdx.x / 32] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[threadIdx.x][q];
+    out[threadIdx.x] = t;
+  }
+}
+
+// alpha[i] += d[i] for i < n.
+__global__ void axpy_kernel(double* __restrict__ alpha, const double* __restrict__ d, long long n) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    alpha[i] += d[i];
 }
 
 // out[r*n + j] = lower triangle of the tiled matrix, rows row0.. row0+nrows (0 above the diagonal).
@@ -331,12 +453,6 @@ cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_dag(const DagArgs& a, int grid, cudaStream_t st) {
-  if (a.ntasks == 0) return cudaSuccess;
-  dag_kernel<<<grid, kThreads, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st) {
   logdet_kernel<<<1, kThreads, 0, st>>>(Kt, T, n, out);
   return cudaGetLastError();
@@ -347,16 +463,43 @@ cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long r
   if (nrows <= 0) return cudaSuccess;
   for (long long r = 0; r < nrows; r += 65535) {
     const long long cnt = (nrows - r) < 65535 ? (nrows - r) : 65535;
-    dim3 grid((unsigned)((n + kThreads - 1) / kThreads < 64 ? (n + kThreads - 1) / kThreads : 64), (unsigned)cnt);
+    const long long bx = (n + kThreads - 1) / kThreads;
+    dim3 grid((unsigned)(bx < 64 ? bx : 64), (unsigned)cnt);
     factor_rows_kernel<<<grid, kThreads, 0, st>>>(Kt, T, n, row0 + r, out + (size_t)r * n);
   }
   return cudaGetLastError();
 }
 
-int dag_max_ctas_per_sm() {
+cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st) {
+  if (a.ntasks == 0) return cudaSuccess;
+  if (mixed)
+    dag_kernel<true><<<grid, kThreads, 0, st>>>(a);
+  else
+    dag_kernel<false><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+int dag_max_ctas_per_sm(bool mixed) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel, kThreads, 0);
+  if (mixed)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false>, kThreads, 0);
   return nb;
+}
+
+cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
+                            double* r, double* partial, double* norms, cudaStream_t st) {
+  const int nb = Mt * (T / 32);
+  residual_kernel<<<nb, kThreads, 0, st>>>(Kt, T, Mt, n, y, alpha, r, partial);
+  sum_pairs_kernel<<<1, kThreads, 0, st>>>(partial, nb, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double* alpha, const double* d, long long n, cudaStream_t st) {
+  const long long b = (n + kThreads - 1) / kThreads;
+  axpy_kernel<<<(unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096), kThreads, 0, st>>>(alpha, d, n);
+  return cudaGetLastError();
 }
 
 }  // namespace gpk

@@ -56,7 +56,12 @@ cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long lo
 cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long row0, long long nrows, double* out,
                                cudaStream_t st);
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st);
-cudaError_t launch_dag(const DagArgs& a, int grid, cudaStream_t st);
-int dag_max_ctas_per_sm();
+cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st);
+int dag_max_ctas_per_sm(bool mixed);
+// r = y - K alpha from packed lower FP64 tiles; norms[0] = ||r||^2, norms[1] = ||y||^2.
+// partial needs 2 * Mt * (T/32) doubles.
+cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
+                            double* r, double* partial, double* norms, cudaStream_t st);
+cudaError_t launch_axpy(double* alpha, const double* d, long long n, cudaStream_t st);
 
 }  // namespace gpk

@@ -89,15 +89,18 @@ inline size_t tri(int I, int J) { return (size_t)I * (I + 1) / 2 + J; }
 std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& cm) {
   Builder b;
   const double t3 = (double)T * T * T;
+  const double spf_upd = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
   const double c_potrf = cm.task_overhead + cm.sec_per_flop * t3 / 3.0 / cm.potrf_eff;
-  const double c_trsm = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
-  const double c_gemm = cm.task_overhead + cm.sec_per_flop * 2.0 * t3 / cm.gemm_eff;
-  const double c_syrk = cm.task_overhead + cm.sec_per_flop * (t3 + 64.0 * T * T) / cm.gemm_eff;
+  const double c_trsm0 = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
+  const double c_trsm = cm.task_overhead + spf_upd * t3 / cm.trsm_eff;
+  const double c_gemm = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
+  const double c_syrk = cm.task_overhead + spf_upd * (t3 + 64.0 * T * T) / cm.gemm_eff;
   std::vector<int> last(tri(Mt, 0), -1);  // last task that wrote each lower tile
   for (int J = 0; J < Mt; ++J) {
     const int po = b.add(TASK_POTRF, J, 0, 0, c_potrf, {last[tri(J, J)]});
     last[tri(J, J)] = po;
-    for (int I = J + 1; I < Mt; ++I) last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, c_trsm, {po, last[tri(I, J)]});
+    for (int I = J + 1; I < Mt; ++I)
+      last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, J == 0 ? c_trsm0 : c_trsm, {po, last[tri(I, J)]});
     for (int I = J + 1; I < Mt; ++I)
       for (int K = J + 1; K <= I; ++K)
         last[tri(I, K)] =
@@ -109,8 +112,9 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
 std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm) {
   Builder b;
   const double t3 = (double)T * T * T;
-  const double c_trsm = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
-  const double c_gemm = cm.task_overhead + cm.sec_per_flop * 2.0 * t3 / cm.gemm_eff;
+  const double spf = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
+  const double c_trsm = cm.task_overhead + spf * t3 / cm.trsm_eff;
+  const double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
   std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1);
   for (int J = 0; J < Mt; ++J) {
     for (int c = 0; c < Mc; ++c)

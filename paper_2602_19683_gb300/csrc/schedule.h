@@ -11,7 +11,9 @@ struct Task4 {
 
 // Relative speed model used to order tasks (seconds per flop of one CTA, plus a fixed overhead).
 struct CostModel {
-  double sec_per_flop = 1.0 / 3.9e9;   // one CTA on a shared SM, FP64 FFMA
+  double sec_per_flop = 1.0 / 3.9e9;     // FP64 work: one CTA on a shared SM, FP64 FFMA
+  double sec_per_flop32 = 1.0 / 3.0e11;  // FP32 work (mixed mode): one CTA per SM
+  bool mixed = false;                    // trailing updates / later panel TRSMs / V solve in FP32
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
 };

@@ -306,20 +306,19 @@ __device__ void cta_trsm_left(const double* L, int ldl, double* B, int ldb, int 
 
 // ---------------------------------------------------------------- vector solves (Eq. 2)
 
-// b[0..nb) <- L^{-1} b (forward substitution with one diagonal tile). Warp 0 solves each 32-row
-// strip (lane i owns row i), then all threads update the rows below with the strip's columns.
-__device__ void cta_trsv_lower(const double* L, int ldl, double* b, int nb, double* xs /*smem[32]*/) {
+// b[0..nb) <- L^{-1} b (forward substitution with one diagonal tile). Each 32-row strip: its 32 x 32
+// diagonal block is staged in smem, warp 0 solves it (lane i owns row i), then all threads update the
+// rows below with the strip's columns.
+__device__ void cta_trsv_lower(const double* L, int ldl, double* b, int nb, double* xs /*smem[32]*/, Tri32& tri) {
   const int t = threadIdx.x;
   for (int k0 = 0; k0 < nb; k0 += 32) {
+    tri32_load(tri, L + (size_t)k0 * ldl + k0, ldl);
     if (t < 32) {
       double bi = ldcg(b + k0 + t);
-      const double* Lr = L + (size_t)(k0 + t) * ldl + k0;
       for (int j = 0; j < 32; ++j) {
-        double xj = 0.0;
-        if (t == j) xj = bi / ldcg(Lr + j);
-        xj = __shfl_sync(0xffffffffu, xj, j);
+        const double xj = __shfl_sync(0xffffffffu, bi * tri.inv[j], j);
         if (t == j) bi = xj;
-        if (t > j) bi = fma(-ldcg(Lr + j), xj, bi);
+        if (t > j) bi = fma(-tri.l[t][j], xj, bi);
       }
       xs[t] = bi;
       b[k0 + t] = bi;
@@ -337,17 +336,16 @@ __device__ void cta_trsv_lower(const double* L, int ldl, double* b, int nb, doub
 }
 
 // b[0..nb) <- L^{-T} b (backward substitution with one diagonal tile), strips from the bottom.
-__device__ void cta_trsv_lower_T(const double* L, int ldl, double* b, int nb, double* xs) {
+__device__ void cta_trsv_lower_T(const double* L, int ldl, double* b, int nb, double* xs, Tri32& tri) {
   const int t = threadIdx.x;
   for (int k0 = nb - 32; k0 >= 0; k0 -= 32) {
+    tri32_load(tri, L + (size_t)k0 * ldl + k0, ldl);
     if (t < 32) {
       double bi = ldcg(b + k0 + t);
       for (int j = 31; j >= 0; --j) {
-        double xj = 0.0;
-        if (t == j) xj = bi / ldcg(L + (size_t)(k0 + j) * ldl + k0 + j);
-        xj = __shfl_sync(0xffffffffu, xj, j);
+        const double xj = __shfl_sync(0xffffffffu, bi * tri.inv[j], j);
         if (t == j) bi = xj;
-        if (t < j) bi = fma(-ldcg(L + (size_t)(k0 + j) * ldl + k0 + t), xj, bi);
+        if (t < j) bi = fma(-tri.l[j][t], xj, bi);
       }
       xs[t] = bi;
       b[k0 + t] = bi;

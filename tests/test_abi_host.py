@@ -48,18 +48,18 @@ def test_no_gpu_or_bad_args_are_rejected(lib):
     assert lib.gp_status_string(N.GP_ERR_NOT_PD) == b"matrix not positive definite"
 
 
-def tasks(lib, graph, Mt, Mc, T, workers):
-    cnt = lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, None, 0)
+def tasks(lib, graph, Mt, Mc, T, workers, mixed=0):
+    cnt = lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, mixed, None, 0)
     out = np.zeros((cnt, 4), dtype=np.int32)
-    assert lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, out.ctypes.data, cnt) == cnt
+    assert lib.gp_schedule_tasks(graph, Mt, Mc, T, workers, mixed, out.ctypes.data, cnt) == cnt
     return out
 
 
-@pytest.mark.parametrize("Mt,workers", [(1, 4), (2, 1), (5, 3), (9, 304), (16, 304)])
-def test_cholesky_schedule_is_topological(lib, Mt, workers):
+@pytest.mark.parametrize("Mt,workers,mixed", [(1, 4, 0), (2, 1, 0), (5, 3, 1), (9, 304, 0), (16, 304, 1)])
+def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
     """Every tile of the lower triangle receives POTRF/TRSM once and its updates J = 0..min-1 in order,
     and each task appears after the tasks whose tiles it reads (Fig. 1's dependencies)."""
-    t = tasks(lib, 0, Mt, 0, 64, workers)
+    t = tasks(lib, 0, Mt, 0, 64, workers, mixed)
     assert len(t) == Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
     cnt = {}  # tile -> updates applied (+1 once final)
     for kind, p, q, r in t:
@@ -121,6 +121,6 @@ def test_mean_schedule_is_topological(lib, Mt, T, workers):
 
 
 def test_schedule_rejects_bad_arguments(lib):
-    assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, None, 0) == -1
-    assert lib.gp_schedule_tasks(3, 4, 0, 64, 1, None, 0) == -1
-    assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(3, 4, 0, 64, 1, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1
