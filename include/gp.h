@@ -66,7 +66,9 @@ typedef struct {
 typedef struct {
   int32_t tile;           /* tile edge T (multiple of 32, 32..1024); 0 = choose automatically        */
   int32_t precision;      /* GP_FP64 or GP_FP32                                                       */
-  double ir_tol;          /* refinement stops when ||y - K alpha||_2 / ||y||_2 <= ir_tol (0 = 1e-14)  */
+  double ir_tol;          /* refinement stops when the normwise backward error ||y - K alpha||_inf /
+                             (||K||_inf ||alpha||_inf + ||y||_inf) <= ir_tol (0 = 1e-15), or when it
+                             stagnates at <= 100 ir_tol; otherwise GP_ERR_NO_CONVERGENCE            */
   int32_t ir_maxit;       /* refinement iteration limit (0 = 10)                                      */
   int32_t noisy_prior;    /* 1: K_{Xs,Xs} includes s2 on its diagonal (noisy-target covariance)       */
   int64_t timeout_ns;     /* bound on any single device-side wait (0 = 60 s)                          */
@@ -136,11 +138,43 @@ gp_status gp_factor_free(gp_ctx* ctx, gp_factor* f);
  * (GP_OK if none). *info (host, may be NULL) receives its detail (failing column for NOT_PD). */
 gp_status gp_sync(gp_ctx* ctx, int64_t* info);
 
+/* ---------------------------------------------------------------- batches of independent GPs
+ * Many independent GPs of uneven size are assembled, factored and predicted together: one batched
+ * assembly kernel, ONE persistent task-DAG launch running every GP's tiled Cholesky (Sec. 3.2), mean
+ * solve (Eq. 2) and covariance solve (Eq. 3) in a single list-scheduled order, and one output kernel,
+ * captured once into a CUDA graph. Not in the paper (its GPs are solved one at a time). */
+typedef struct {
+  const double* X;   /* device, n x D       */
+  const double* y;   /* device, n           */
+  const double* Xs;  /* device, m x D       */
+  int64_t n, m;
+  int32_t D;
+  int32_t tile;      /* tile edge for this GP (multiple of 32); 0 = library choice by n       */
+  gp_hyper h;
+  double* mean_out;  /* device, m                                                               */
+  double* cov_out;   /* device, m x m (both triangles), or NULL for the mean only              */
+} gp_batch_desc;
+
+typedef struct gp_batch gp_batch;
+
+/* Allocates the batch's workspace, builds its task order and captures its CUDA graph. The device
+ * pointers in descs are baked into the graph: they must stay valid (their contents may change)
+ * until gp_batch_free. Precision follows the context: GP_FP32 runs the FP32 trailing updates of
+ * the mixed mode without the refinement step. */
+gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp_batch** out);
+/* Launches the captured graph on the context's stream (asynchronous; errors via gp_sync, where a
+ * NOT_PD info holds the GP index in its high 32 bits and the column in the low 32 bits). */
+gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
+gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
+
 /* Host-only introspection of the persistent kernel's dispatch order: writes the task list of graph
- * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve) for Mt tile rows, Mc covariance
- * tile columns, tile edge T and `workers` CTAs as int32 quadruples {kind, p, q, r} (kinds as in the
+ * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
+ * Cholesky used by gp_nlml_grad) for Mt tile rows, Mc covariance
+ * tile columns, tile edge T, `workers` CTAs and the cost model of precision `mixed` (0 = FP64,
+ * 1 = GP_FP32) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
- * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch)) into out (host, room
+ * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
+ * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J)) into out (host, room
  * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap);

@@ -29,6 +29,12 @@ class gp_config(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 5)]
 
 
+class gp_batch_desc(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("Xs", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("D", ctypes.c_int32), ("tile", ctypes.c_int32), ("h", gp_hyper),
+                ("mean_out", ctypes.c_void_p), ("cov_out", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "gp_create": ([ctypes.POINTER(_P), _I32, _P, ctypes.POINTER(gp_config)], _I32),
     "gp_destroy": ([_P], _I32),
@@ -39,6 +45,9 @@ SIGNATURES = {
     "gp_predict_full_cov": ([_P, _P, _P, _I64, _P], _I32),
     "gp_logdet": ([_P, _P, ctypes.POINTER(_D)], _I32),
     "gp_nlml_grad": ([_P, _P, _P, _I64, _I32, gp_hyper, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I32),
+    "gp_batch_create": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(_P)], _I32),
+    "gp_batch_run": ([_P, _P], _I32),
+    "gp_batch_free": ([_P, _P], _I32),
     "gp_factor_rows": ([_P, _P, _I64, _I64, _P], _I32),
     "gp_alpha": ([_P, _P, _P], _I32),
     "gp_factor_free": ([_P, _P], _I32),

@@ -7,6 +7,7 @@ GPError(status, info).
 from __future__ import annotations
 
 import ctypes
+import warnings
 
 import torch
 
@@ -143,8 +144,12 @@ def gp_predict_mean(ctx: Context, f: Factor, y: torch.Tensor, Xs: torch.Tensor, 
         out = torch.empty(m, dtype=torch.float64, device=Xs.device)
     _dev(out, "mean_out", (m,))
     it = ctypes.c_int32(0)
-    _check(ctx.lib.gp_predict_mean(ctx.h, f.h, y.data_ptr(), Xs.data_ptr(), m, out.data_ptr(),
-                                   ctypes.byref(it) if want_iters else None), "gp_predict_mean")
+    s = ctx.lib.gp_predict_mean(ctx.h, f.h, y.data_ptr(), Xs.data_ptr(), m, out.data_ptr(),
+                                ctypes.byref(it) if want_iters else None)
+    if s == N.GP_ERR_NO_CONVERGENCE:  # the refined result is still returned
+        warnings.warn("gp_predict_mean: iterative refinement stopped above its tolerance", RuntimeWarning)
+    else:
+        _check(s, "gp_predict_mean")
     return (out, it.value) if want_iters else out
 
 
@@ -186,6 +191,94 @@ def gp_nlml_grad(ctx: Context, X: torch.Tensor, y: torch.Tensor, hyper: Hyper):
     _check(ctx.lib.gp_nlml_grad(ctx.h, X.data_ptr(), y.data_ptr(), n, D, Hyper(*hyper).c, ctypes.byref(nl), g),
            "gp_nlml_grad")
     return nl.value, [g[0], g[1], g[2]]
+
+
+class Batch:
+    """A gp_batch: many independent GPs assembled, factored and predicted by one captured CUDA graph
+    (batched assembly, one persistent task-DAG launch, outputs). Entries are (X, y, Xs, hyper) or
+    (X, y, Xs, hyper, tile); outputs are allocated here and refilled by every run()."""
+
+    def __init__(self, ctx: Context, gps, want_cov: bool = True):
+        self.ctx = ctx
+        self.inputs = []
+        self.means, self.covs = [], []
+        descs = (N.gp_batch_desc * len(gps))()
+        for g, e in enumerate(gps):
+            X, y, Xs, hyper = e[:4]
+            tile = e[4] if len(e) > 4 else 0
+            n, D = X.shape
+            m = Xs.shape[0]
+            _dev(X, "X")
+            _dev(y, "y", (n,))
+            _dev(Xs, "Xs", (m, D))
+            mean = torch.empty(m, dtype=torch.float64, device=X.device)
+            cov = torch.empty((m, m), dtype=torch.float64, device=X.device) if want_cov else None
+            self.inputs.append((X, y, Xs))
+            self.means.append(mean)
+            self.covs.append(cov)
+            d = descs[g]
+            d.X, d.y, d.Xs, d.n, d.m, d.D, d.tile = X.data_ptr(), y.data_ptr(), Xs.data_ptr(), n, m, D, tile
+            d.h = Hyper(*hyper).c
+            d.mean_out = mean.data_ptr()
+            d.cov_out = cov.data_ptr() if cov is not None else None
+        self.h = ctypes.c_void_p()
+        _check(ctx.lib.gp_batch_create(ctx.h, len(gps), descs, ctypes.byref(self.h)), "gp_batch_create")
+
+    def run(self):
+        _check(self.ctx.lib.gp_batch_run(self.ctx.h, self.h), "gp_batch_run")
+
+    def free(self):
+        if self.h and self.h.value:
+            self.ctx.lib.gp_batch_free(self.ctx.h, self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class GPNLML(torch.autograd.Function):
+    """nlml(l, v, s2) for fixed data, with the gradient from the library's blocked Cholesky adjoint.
+
+    forward runs gp_nlml_grad once (value and gradient together); backward scales the stored gradient
+    by the incoming gradient. X and y get no gradient."""
+
+    @staticmethod
+    def forward(fctx, X, y, l, v, s2, ctx):
+        nl, g = gp_nlml_grad(ctx, X, y, Hyper(float(l), float(v), float(s2)))
+        fctx.save_for_backward(torch.tensor(g, dtype=torch.float64, device=l.device))
+        return torch.tensor(nl, dtype=torch.float64, device=l.device)
+
+    @staticmethod
+    def backward(fctx, gout):
+        (g,) = fctx.saved_tensors
+        g = g * gout
+        return None, None, g[0], g[1], g[2], None
+
+
+def nlml(X, y, l, v, s2, ctx: Context):
+    """Differentiable negative log marginal likelihood in (l, v, s2) (0-d float64 tensors)."""
+    return GPNLML.apply(X, y, l, v, s2, ctx)
+
+
+def fit_adam(ctx: Context, X, y, theta0=(0.5, 2.0, 0.5), steps: int = 50, lr: float = 0.05, floor: float = 1e-6):
+    """Hyperparameter fitting with torch's Adam (textbook update, beta = (0.9, 0.999), eps = 1e-8) on
+    the raw (l, v, s2), each clamped to >= floor after every step. Returns [(theta, nlml, grad)]."""
+    params = [torch.tensor(float(t), dtype=torch.float64, device=X.device, requires_grad=True) for t in theta0]
+    opt = torch.optim.Adam(params, lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        loss = nlml(X, y, *params, ctx)
+        loss.backward()
+        hist.append(([float(p) for p in params], float(loss), [float(p.grad) for p in params]))
+        opt.step()
+        with torch.no_grad():
+            for p in params:
+                p.clamp_(min=floor)
+    return hist
 
 
 def predict(X, y, Xs, hyper=Hyper(), ctx: Context | None = None, full_cov: bool = True):

@@ -1,5 +1,6 @@
 // C ABI of libgp (declared in include/gp.h): contexts, factor objects, workspace and the entry
 // points of the hot path (assembly, tiled Cholesky, mean and covariance prediction).
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -73,6 +74,15 @@ struct gp_ctx {
   double* d_scalar = nullptr;  // small device scratch for scalar results
   long long launches = 0;
   std::map<TaskKey, TaskBuf> tasks;
+  gp_factor* grad_factor = nullptr;  // reused by gp_nlml_grad across calls of the same size
+};
+
+struct gp_batch {
+  int B = 0, ntasks = 0, npre = 0, npost = 0;
+  bool mixed = false;
+  size_t counter_bytes = 0;
+  DevBuf work, counters, descs, tasks, items;
+  cudaGraphExec_t exec = nullptr;
 };
 
 struct gp_factor {
@@ -84,8 +94,10 @@ struct gp_factor {
   DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
+  DevBuf Bt, Wt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, counters, L^{-1} y
   DevBuf V, S, cCov;          // covariance workspace
   bool factored = false, alpha_valid = false;
+  double ir_eta = 0.0;        // backward error reached by the last refinement
 };
 
 namespace {
@@ -120,6 +132,7 @@ gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, cons
     if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
     if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
+    if (kind == 3) v = gpk::cholesky_adjoint_tasks(Mt, T, workers, cm);
     TaskBuf tb;
     GP_TRY(grow(tb.buf, v.size() * sizeof(gpk::Task4)));
     if (!v.empty())
@@ -212,7 +225,7 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   if (cfg) c = *cfg;
   if (c.tile != 0 && (c.tile < 32 || c.tile > 1024 || c.tile % 32)) return GP_ERR_INVALID_ARG;
   if (c.precision != GP_FP64 && c.precision != GP_FP32) return GP_ERR_INVALID_ARG;
-  if (c.ir_tol <= 0) c.ir_tol = 1e-14;
+  if (c.ir_tol <= 0) c.ir_tol = 1e-15;
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
   GP_CUDA(cudaSetDevice(device));
@@ -252,6 +265,7 @@ gp_status gp_destroy(gp_ctx* c) {
   if (!c) return GP_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->grad_factor) gp_factor_free(c, c->grad_factor);
   for (auto& kv : c->tasks) release(kv.second.buf);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalar) cudaFree(c->d_scalar);
@@ -269,13 +283,14 @@ int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
 
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap) {
-  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 2) return -1;
+  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 3) return -1;
   gpk::CostModel cm;
   cm.mixed = mixed != 0;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
   if (graph == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
+  if (graph == 3) v = gpk::cholesky_adjoint_tasks(Mt, T, workers, cm);
   if (out) {
     const int64_t k = (int64_t)v.size() < cap ? (int64_t)v.size() : cap;
     std::memcpy(out, v.data(), (size_t)k * sizeof(gpk::Task4));
@@ -309,6 +324,10 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->alpha);
   release(f->rvec);
   release(f->part);
+  release(f->Bt);
+  release(f->Wt);
+  release(f->cRev);
+  release(f->beta);
   release(f->bvec);
   release(f->cMean);
   release(f->V);
@@ -389,23 +408,34 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   int iters = 0;
   if (mixed) {
     // Classic iterative refinement: r = y - K alpha in FP64 against the stored FP64 K, correction
-    // through the mixed-precision factor, until ||r|| / ||y|| <= ir_tol.
+    // through the mixed-precision factor. Stops when the normwise backward error
+    // eta = ||r||_inf / (||K||_inf ||alpha||_inf + ||y||_inf) <= ir_tol, or when eta stagnates (less
+    // than a halving per step) at a level <= 100 ir_tol (the attainable FP64 accuracy).
     GP_TRY(grow(f->rvec, npad * sizeof(double)));
-    GP_TRY(grow(f->part, (size_t)2 * Mt * nch * sizeof(double)));
+    GP_TRY(grow(f->part, (size_t)6 * Mt * nch * sizeof(double)));
     bool converged = false;
+    double eta_prev = 0.0;
     for (int it = 0;; ++it) {
       GP_CUDA(gpk::launch_residual((const double*)f->Kt0.p, T, Mt, f->n, y, (const double*)f->alpha.p,
                                    (double*)f->bvec.p, (double*)f->part.p, c->d_scalar, c->stream));
       count_launch(c, 2);
-      double norms[2];
-      GP_CUDA(cudaMemcpyAsync(norms, c->d_scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      double nr[6];
+      GP_CUDA(cudaMemcpyAsync(nr, c->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       GP_CUDA(cudaStreamSynchronize(c->stream));
-      if (!(norms[0] == norms[0])) break;  // NaN: the device status (if any) reports why
-      if (std::sqrt(norms[0]) <= c->cfg.ir_tol * std::sqrt(norms[1])) {
+      const double den = nr[3] * nr[4] + nr[5];
+      const double eta = den > 0 ? nr[2] / den : 0.0;
+      f->ir_eta = eta;
+      if (!(eta == eta)) break;  // NaN: the device status (if any) reports why
+      if (eta <= c->cfg.ir_tol) {
         converged = true;
         break;
       }
+      if (it > 0 && eta > 0.5 * eta_prev) {
+        converged = eta <= 100.0 * c->cfg.ir_tol;
+        break;
+      }
       if (it >= c->cfg.ir_maxit) break;
+      eta_prev = eta;
       GP_TRY(solve_in_place(c, f));  // bvec = K~^{-1} r
       GP_CUDA(gpk::launch_axpy((double*)f->alpha.p, (const double*)f->bvec.p, f->n, c->stream));
       count_launch(c);
@@ -486,8 +516,235 @@ gp_status gp_logdet(gp_ctx* c, gp_factor* f, double* out) {
 
 gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
                        double* nlml_out, double grad_out[3]) {
-  (void)c; (void)X; (void)y; (void)n; (void)D; (void)h; (void)nlml_out; (void)grad_out;
-  return GP_ERR_INVALID_ARG;
+  if (!c || !X || !y || !nlml_out || !grad_out || n < 1 || D < 1 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  // forward: K, L, alpha (refined in mixed mode)
+  GP_TRY(gp_assemble(c, X, n, D, h, &c->grad_factor));
+  gp_factor* f = c->grad_factor;
+  GP_TRY(gp_cholesky(c, f));
+  gp_status st = gp_predict_mean(c, f, y, nullptr, 0, nullptr, nullptr);
+  if (st != GP_OK && st != GP_ERR_NO_CONVERGENCE) return st;
+  const int T = f->T, Mt = f->Mt, nch = T / 32;
+  const bool mixed = f->precision == GP_FP32;
+  const size_t ntiles = (size_t)Mt * (Mt + 1) / 2, npad = (size_t)Mt * T, TT = (size_t)T * T;
+  GP_TRY(grow(f->Bt, ntiles * TT * sizeof(double)));
+  GP_TRY(grow(f->Wt, (size_t)Mt * TT * sizeof(double)));
+  GP_TRY(grow(f->cRev, (ntiles * 2 + Mt) * sizeof(int)));
+  GP_TRY(grow(f->beta, npad * sizeof(double)));
+  GP_TRY(grow(f->part, std::max((size_t)6 * Mt * nch, (size_t)3 * ntiles * nch) * sizeof(double)));
+  const double* L = (const double*)f->Kt.p;
+  double* alpha = (double*)f->alpha.p;
+  double* beta = (double*)f->beta.p;
+  // nlml = 1/2 y^T alpha + sum log L_ii + n/2 log(2 pi)
+  GP_CUDA(gpk::launch_dot(y, alpha, n, c->d_scalar + 8, c->stream));
+  GP_CUDA(gpk::launch_logdet(L, T, n, c->d_scalar + 9, c->stream));
+  // Lbar of the NLML w.r.t. L: -tril(alpha beta^T) + diag(1/L_ii), beta = L^{-1} y = L^T alpha
+  GP_CUDA(gpk::launch_beta(L, T, Mt, alpha, beta, c->stream));
+  GP_CUDA(gpk::launch_init_lbar(L, (double*)f->Bt.p, T, Mt, n, alpha, beta, c->stream));
+  count_launch(c, 4);
+  // reverse sweep of the tiled Cholesky: Lbar -> Abar (the adjoint of K's stored lower entries)
+  GP_CUDA(cudaMemsetAsync(f->cRev.p, 0, (ntiles * 2 + Mt) * sizeof(int), c->stream));
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 3, Mt, 0, T, mixed, &tb));
+  gpk::DagArgs a = base_args(c, f);
+  a.Bt = (double*)f->Bt.p;
+  a.Wt = (double*)f->Wt.p;
+  a.rc = (int*)f->cRev.p;
+  a.fa = a.rc + ntiles;
+  a.rd = a.fa + ntiles;
+  if (tb->ntasks > 0) {
+    GP_CUDA(cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), c->stream));
+    a.tasks = (const int4*)tb->buf.p;
+    a.ntasks = tb->ntasks;
+    const int g = c->grid[mixed ? 1 : 0];
+    GP_CUDA(gpk::launch_dag(a, g < tb->ntasks ? g : tb->ntasks, mixed, c->stream, true));
+    count_launch(c);
+  }
+  // contraction with dK/dtheta recomputed from X (dK never stored)
+  GP_CUDA(gpk::launch_grad_contract((const double*)f->Bt.p, T, Mt, X, n, D, h.l, h.v, (double*)f->part.p,
+                                    c->d_scalar + 10, c->stream));
+  count_launch(c, 2);
+  double hv[5];
+  GP_CUDA(cudaMemcpyAsync(hv, c->d_scalar + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int64_t info = 0;
+  const gp_status dev = gp_sync(c, &info);
+  if (dev != GP_OK) return dev;
+  *nlml_out = 0.5 * hv[0] + 0.5 * hv[1] + 0.5 * (double)n * std::log(2.0 * 3.14159265358979323846);
+  grad_out[0] = hv[2];
+  grad_out[1] = hv[3];
+  grad_out[2] = hv[4];
+  return st;
+}
+
+// ---------------------------------------------------------------- batches
+
+static int batch_tile(long long n) {
+  if (n < 512) return 32;
+  if (n < 1536) return 64;
+  return 128;
+}
+
+gp_status gp_batch_free(gp_ctx* c, gp_batch* b);
+
+gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_batch** out) {
+  if (!c || !descs || !out || B < 1) return GP_ERR_INVALID_ARG;
+  for (int g = 0; g < B; ++g) {
+    const gp_batch_desc& d = descs[g];
+    if (!d.X || !d.y || d.n < 1 || d.D < 1 || d.m < 0 || (d.m > 0 && (!d.Xs || !d.mean_out)) || !valid_hyper(d.h))
+      return GP_ERR_INVALID_ARG;
+    if (d.tile != 0 && (d.tile < 32 || d.tile > 1024 || d.tile % 32)) return GP_ERR_INVALID_ARG;
+    if (g >= (1 << 27)) return GP_ERR_INVALID_ARG;
+  }
+  GP_CUDA(cudaSetDevice(c->device));
+  const bool mixed = c->cfg.precision == GP_FP32;
+  bool want_cov = false;
+  for (int g = 0; g < B; ++g) want_cov |= descs[g].cov_out != nullptr && descs[g].m > 0;
+  gp_batch* b = new (std::nothrow) gp_batch();
+  if (!b) return GP_ERR_OOM;
+  b->B = B;
+  b->mixed = mixed;
+  // sizes and workspace layout: one double buffer and one int buffer for the whole batch
+  std::vector<gpk::GpDesc> hd(B);
+  std::vector<gpk::BatchGp> shapes(B);
+  size_t dbl = 0, ints = 0;
+  std::vector<size_t> offK(B), offV(B), offS(B), offb(B), offc(B);
+  for (int g = 0; g < B; ++g) {
+    const gp_batch_desc& d = descs[g];
+    const int T = d.tile ? d.tile : batch_tile(d.n);
+    const long long Mt = (d.n + T - 1) / T, Mc = d.m > 0 ? (d.m + T - 1) / T : 0;
+    const bool cov = want_cov && d.cov_out && d.m > 0;
+    const size_t ntiles = (size_t)Mt * (Mt + 1) / 2, npad = (size_t)Mt * T, ldv = (size_t)Mc * T;
+    shapes[g] = {(int)Mt, cov ? (int)Mc : 0, T};
+    offK[g] = dbl; dbl += ntiles * T * T;
+    offV[g] = dbl; dbl += cov ? npad * ldv : 0;
+    offS[g] = dbl; dbl += cov ? ldv * ldv : 0;
+    offb[g] = dbl; dbl += npad;
+    const int nch = T / 32;
+    offc[g] = ints;
+    ints += ntiles + (cov ? (size_t)Mt * Mc + (size_t)Mc * (Mc + 1) / 2 : 0) + (size_t)Mt * nch * 2 + (size_t)Mt * 2;
+    gpk::GpDesc& e = hd[g];
+    std::memset(&e, 0, sizeof(e));
+    e.X = d.X; e.y = d.y; e.Xs = d.Xs; e.mean = d.mean_out; e.cov = cov ? d.cov_out : nullptr;
+    e.n = d.n; e.m = d.m; e.ldv = (long long)ldv; e.lds = (long long)ldv;
+    e.l = d.h.l; e.v = d.h.v; e.s2 = d.h.s2;
+    e.D = d.D; e.T = T; e.Mt = (int)Mt; e.Mc = cov ? (int)Mc : 0; e.nch = nch;
+  }
+  gp_status st = grow(b->work, dbl * sizeof(double));
+  if (st == GP_OK) st = grow(b->counters, ints * sizeof(int));
+  if (st == GP_OK) st = grow(b->descs, (size_t)B * sizeof(gpk::GpDesc));
+  if (st != GP_OK) {
+    gp_batch_free(c, b);
+    return st;
+  }
+  b->counter_bytes = ints * sizeof(int);
+  double* W = (double*)b->work.p;
+  int* C = (int*)b->counters.p;
+  std::vector<int4> pre, post;
+  for (int g = 0; g < B; ++g) {
+    gpk::GpDesc& e = hd[g];
+    const int T = e.T, Mt = e.Mt, Mc = e.Mc, nch = e.nch;
+    const size_t ntiles = (size_t)Mt * (Mt + 1) / 2;
+    e.Kt = W + offK[g];
+    e.V = W + offV[g];
+    e.S = W + offS[g];
+    e.bvec = W + offb[g];
+    int* cc = C + offc[g];
+    e.cK = cc; cc += ntiles;
+    if (Mc > 0) {
+      e.cV = cc; cc += (size_t)Mt * Mc;
+      e.cS = cc; cc += (size_t)Mc * (Mc + 1) / 2;
+    }
+    e.cF = cc; cc += (size_t)Mt * nch;
+    e.cB = cc; cc += (size_t)Mt * nch;
+    e.dF = cc; cc += Mt;
+    e.dB = cc;
+    for (size_t t = 0; t < ntiles; ++t)
+      for (int ch = 0; ch < T / 32; ++ch) pre.push_back(make_int4(0, g, (int)t, ch));
+    if (Mc > 0) {
+      for (long long r = 0; r < (long long)Mt * T; r += 8) pre.push_back(make_int4(1, g, (int)r, 0));
+      for (long long r = 0; r < (long long)Mc * T; r += 8) pre.push_back(make_int4(2, g, (int)r, 0));
+      for (long long r = 0; r < e.m; r += 8) post.push_back(make_int4(1, g, (int)r, 0));
+    }
+    pre.push_back(make_int4(3, g, 0, 0));
+    for (long long r = 0; r < e.m; r += 8) post.push_back(make_int4(0, g, (int)r, 0));
+  }
+  // task order over all GPs (cached per batch: the plan owns it)
+  const int workers = c->grid[mixed ? 1 : 0];
+  std::vector<gpk::Task4> tasks = gpk::batch_tasks(shapes, want_cov, workers, cost_model(c, mixed));
+  st = grow(b->tasks, tasks.size() * sizeof(gpk::Task4));
+  if (st == GP_OK) st = grow(b->items, (pre.size() + post.size()) * sizeof(int4));
+  if (st != GP_OK) {
+    gp_batch_free(c, b);
+    return st;
+  }
+  b->ntasks = (int)tasks.size();
+  b->npre = (int)pre.size();
+  b->npost = (int)post.size();
+  cudaError_t e = cudaMemcpy(b->descs.p, hd.data(), (size_t)B * sizeof(gpk::GpDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tasks.empty())
+    e = cudaMemcpy(b->tasks.p, tasks.data(), tasks.size() * sizeof(gpk::Task4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pre.empty()) e = cudaMemcpy(b->items.p, pre.data(), pre.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !post.empty())
+    e = cudaMemcpy((int4*)b->items.p + pre.size(), post.data(), post.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    gp_batch_free(c, b);
+    return cuda_status(e);
+  }
+  // capture: reset counters and dispatch counter, assemble, one persistent launch, outputs
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(b->counters.p, 0, b->counter_bytes, cs);
+    cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), cs);
+    gpk::launch_batch_pre((const int4*)b->items.p, b->npre, (const gpk::GpDesc*)b->descs.p, c->cfg.noisy_prior != 0, cs);
+    gpk::DagArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.descs = (const gpk::GpDesc*)b->descs.p;
+    a.tasks = (const int4*)b->tasks.p;
+    a.ntasks = b->ntasks;
+    a.st = c->d_status;
+    a.timeout_ns = c->cfg.timeout_ns;
+    a.withhold_task = -1;
+    const int occ = gpk::dag_max_ctas_per_sm_batch(mixed);
+    const int cap = mixed ? 1 : 2;
+    const int grid = c->sms * (occ >= cap ? cap : (occ > 0 ? occ : 1));
+    gpk::launch_dag(a, grid < b->ntasks ? grid : b->ntasks, mixed, cs, false, true);
+    gpk::launch_batch_post((const int4*)b->items.p + b->npre, b->npost, (const gpk::GpDesc*)b->descs.p, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    gp_batch_free(c, b);
+    return cuda_status(e);
+  }
+  *out = b;
+  return GP_OK;
+}
+
+gp_status gp_batch_run(gp_ctx* c, gp_batch* b) {
+  if (!c || !b || !b->exec) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(cudaGraphLaunch(b->exec, c->stream));
+  count_launch(c, 3);
+  return GP_OK;
+}
+
+gp_status gp_batch_free(gp_ctx* c, gp_batch* b) {
+  if (!c || !b) return GP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  release(b->work);
+  release(b->counters);
+  release(b->descs);
+  release(b->tasks);
+  release(b->items);
+  delete b;
+  return GP_OK;
 }
 
 }  // extern "C"

@@ -138,21 +138,25 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
     case TASK_UPD:  // (I=p, K=q, J=r)
       return wait_ge(a.cK + tri(p, r), r + 1, st, to, ti) && wait_ge(a.cK + tri(q, r), r + 1, st, to, ti) &&
              wait_ge(a.cK + tri(p, q), r, st, to, ti);
+    // The solve tasks also wait for the factor tiles they read to be final (immediately true when the
+    // factorisation ran in an earlier launch; needed when one launch runs a GP's whole pipeline).
     case TASK_VTRSM:  // (J=p, c=q)
-      return wait_ge(a.cV + (size_t)p * a.Mc + q, p, st, to, ti);
+      return wait_ge(a.cK + tri(p, p), p + 1, st, to, ti) && wait_ge(a.cV + (size_t)p * a.Mc + q, p, st, to, ti);
     case TASK_VGEMM:  // (I=p, J=q, c=r)
-      return wait_ge(a.cV + (size_t)q * a.Mc + r, q + 1, st, to, ti) &&
+      return wait_ge(a.cK + tri(p, q), q + 1, st, to, ti) && wait_ge(a.cV + (size_t)q * a.Mc + r, q + 1, st, to, ti) &&
              wait_ge(a.cV + (size_t)p * a.Mc + r, q, st, to, ti);
     case TASK_WSYRK:  // (a=p, b=q, J=r)
       return wait_ge(a.cV + (size_t)r * a.Mc + p, r + 1, st, to, ti) &&
              wait_ge(a.cV + (size_t)r * a.Mc + q, r + 1, st, to, ti) && wait_ge(a.cS + tri(p, q), r, st, to, ti);
     case TASK_FSOLVE: {  // (J=p)
+      if (!wait_ge(a.cK + tri(p, p), p + 1, st, to, ti)) return false;
       for (int ch = 0; ch < a.nch; ++ch)
         if (!wait_ge(a.cF + (size_t)p * a.nch + ch, p, st, to, ti)) return false;
       return true;
     }
     case TASK_FGEMV:  // (I=p, J=q, ch=r)
-      return wait_ge(a.dF + q, 1, st, to, ti) && wait_ge(a.cF + (size_t)p * a.nch + r, q, st, to, ti);
+      return wait_ge(a.cK + tri(p, q), q + 1, st, to, ti) && wait_ge(a.dF + q, 1, st, to, ti) &&
+             wait_ge(a.cF + (size_t)p * a.nch + r, q, st, to, ti);
     case TASK_BSOLVE: {  // (J=p)
       if (!wait_ge(a.dF + p, 1, st, to, ti)) return false;
       for (int ch = 0; ch < a.nch; ++ch)
@@ -160,8 +164,18 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
       return true;
     }
     case TASK_BGEMV:  // (J=p, I=q, ch=r)
-      return wait_ge(a.dB + q, 1, st, to, ti) && wait_ge(a.dF + p, 1, st, to, ti) &&
-             wait_ge(a.cB + (size_t)p * a.nch + r, a.Mt - 1 - q, st, to, ti);
+      return wait_ge(a.cK + tri(q, p), p + 1, st, to, ti) && wait_ge(a.dB + q, 1, st, to, ti) &&
+             wait_ge(a.dF + p, 1, st, to, ti) && wait_ge(a.cB + (size_t)p * a.nch + r, a.Mt - 1 - q, st, to, ti);
+    case TASK_RUPD: {  // (P=p, K=q, J=r)
+      const int hi = p > q ? p : q, lo = p > q ? q : p;
+      return wait_ge(a.fa + tri(hi, lo), 1, st, to, ti) && wait_ge(a.rc + tri(p, r), q - r - 1, st, to, ti);
+    }
+    case TASK_RTRSM:  // (P=p, J=q)
+      return wait_ge(a.rc + tri(p, q), a.Mt - 1 - q, st, to, ti);
+    case TASK_RDIAG:  // (P=p, J=q)
+      return wait_ge(a.fa + tri(p, q), 1, st, to, ti) && wait_ge(a.rd + q, p - q - 1, st, to, ti);
+    case TASK_RPOTRF:  // (J=p)
+      return wait_ge(a.rd + p, a.Mt - 1 - p, st, to, ti);
   }
   return false;
 }
@@ -171,8 +185,10 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
 // and publishes its own tile's counter. kMixed selects FP32 arithmetic for the trailing updates,
 // the panel TRSMs after the first block column and the covariance solve; POTRF, the first block
 // column's TRSM and the vector solves stay FP64.
-template <bool kMixed>
-__global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a) {
+// A batched launch (kBatch) runs the tasks of many independent GPs: each task names its GP in the
+// high bits of its kind, and the CTA takes that GP's pointers and sizes from the descriptor table.
+template <bool kMixed, bool kRev, bool kBatch>
+__global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a0) {
   __shared__ union {
     TileSmem d;
     TileSmemF32 f;
@@ -180,25 +196,51 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
   __shared__ int s_task;
   __shared__ double s_red[kThreads / 32][32];
   TileSmem& s = u.d;
-  const int T = a.T;
-  const size_t TT = (size_t)T * T;
   while (true) {
-    if (threadIdx.x == 0) s_task = ld_relaxed(&a.st->abort) ? INT_MAX : (int)atomicAdd(&a.st->next_task, 1ull);
+    if (threadIdx.x == 0) s_task = ld_relaxed(&a0.st->abort) ? INT_MAX : (int)atomicAdd(&a0.st->next_task, 1ull);
     __syncthreads();
     const int ti = s_task;
     __syncthreads();
-    if (ti >= a.ntasks) break;
-    const int4 tk = a.tasks[ti];
+    if (ti >= a0.ntasks) break;
+    int4 tk = a0.tasks[ti];
+    DagArgs a = a0;
+    long long gp_tag = 0;  // error detail: GP index in the high 32 bits for batched launches
+    if constexpr (kBatch) {
+      const int g = tk.x >> kBatchKindBits;
+      tk.x &= (1 << kBatchKindBits) - 1;
+      const GpDesc& d = a0.descs[g];
+      a.Kt = d.Kt;
+      a.T = d.T;
+      a.Mt = d.Mt;
+      a.V = d.V;
+      a.ldv = d.ldv;
+      a.Mc = d.Mc;
+      a.S = d.S;
+      a.lds = d.lds;
+      a.bvec = d.bvec;
+      a.nch = d.nch;
+      a.cK = d.cK;
+      a.cV = d.cV;
+      a.cS = d.cS;
+      a.cF = d.cF;
+      a.cB = d.cB;
+      a.dF = d.dF;
+      a.dB = d.dB;
+      gp_tag = (long long)g << 32;
+    }
+    const int T = a.T;
+    const size_t TT = (size_t)T * T;
     bool ok = true;
     if (threadIdx.x == 0) ok = wait_deps(a, tk, ti);
     if (__syncthreads_or(!ok)) break;
     const int p = tk.y, q = tk.z, r = tk.w;
     if (ti == a.withhold_task) continue;  // test hook: this task's completion is never published
-    switch (tk.x) {
+    if constexpr (!kRev) {
+      switch (tk.x) {
       case TASK_POTRF: {
         const int fail = cta_potrf(a.Kt + tri(p, p) * TT, T, T, s);
         if (fail) {
-          if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, (long long)p * T + fail);
+          if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, gp_tag + (long long)p * T + fail);
           return;
         }
         cta_publish(a.cK + tri(p, p), p + 1);
@@ -268,96 +310,170 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
                        a.bvec + (size_t)p * T + r * 32, T, 32, s_red);
         cta_publish(a.cB + (size_t)p * a.nch + r, a.Mt - q);
         break;
+      }
+    } else {
+      switch (tk.x) {
+      case TASK_RUPD: {  // Lbar_PJ -= Abar~_PK L_KJ, Abar~ the symmetric adjoint (diagonal tiles hold Abar + Abar^T)
+        double* C = a.Bt + tri(p, r) * TT;
+        const double* Lkj = a.Kt + tri(q, r) * TT;
+        if (p >= q) {
+          if (kMixed)
+            cta_gemm_sub_f32<0, 1>(C, T, a.Bt + tri(p, q) * TT, T, Lkj, T, T, T, T, false, u.f.g);
+          else
+            cta_gemm_sub<A_MK, B_KN>(C, T, a.Bt + tri(p, q) * TT, T, Lkj, T, T, T, T, false, 0, s.g);
+        } else {
+          if (kMixed)
+            cta_gemm_sub_f32<1, 1>(C, T, a.Bt + tri(q, p) * TT, T, Lkj, T, T, T, T, false, u.f.g);
+          else
+            cta_gemm_sub<A_KM, B_KN>(C, T, a.Bt + tri(q, p) * TT, T, Lkj, T, T, T, T, false, 0, s.g);
+        }
+        cta_publish(a.rc + tri(p, r), q - r);
+        break;
+      }
+      case TASK_RTRSM:  // Abar_PJ = Lbar_PJ L_JJ^{-1}
+        cta_trsm_right_N(a.Kt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, T, T, s);
+        cta_publish(a.fa + tri(p, q), 1);
+        break;
+      case TASK_RDIAG:  // Lbar_JJ -= tril(Abar_PJ^T L_PJ)
+        if (kMixed)
+          cta_gemm_sub_f32<1, 1>(a.Bt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, T,
+                                 true, u.f.g);
+        else
+          cta_gemm_sub<A_KM, B_KN>(a.Bt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T,
+                                   T, T, true, 0, s.g);
+        cta_publish(a.rd + q, p - q);
+        break;
+      case TASK_RPOTRF: {  // Abar_JJ (+ its transpose) from Lbar_JJ, W = -L^{-T} Phi(L^T Lbar) L^{-1}
+        const double* L = a.Kt + tri(p, p) * TT;
+        double* B = a.Bt + tri(p, p) * TT;
+        double* W = a.Wt + (size_t)p * TT;
+        for (size_t e = threadIdx.x; e < TT; e += kThreads) W[e] = 0.0;
+        __syncthreads();
+        cta_gemm_sub<A_KM, B_KN>(W, T, L, T, B, T, T, T, T, true, 0, s.g);  // W = -tril(L^T Lbar)
+        for (int i = threadIdx.x; i < T; i += kThreads) W[(size_t)i * T + i] *= 0.5;
+        __syncthreads();
+        cta_trsm_right_N(L, T, W, T, T, T, s);
+        cta_trsm_left_T(L, T, W, T, T, T, s);
+        for (size_t e = threadIdx.x; e < TT; e += kThreads) {
+          const size_t i = e / T, j = e % T;
+          B[e] = -(ldcg(W + i * T + j) + ldcg(W + j * T + i));
+        }
+        cta_publish(a.fa + tri(p, p), 1);
+        break;
+      }
+      }
     }
   }
 }
 
 // r = y - K alpha for the 32 rows (tile row I = blockIdx.x / nch, chunk ch) from the packed lower
 // FP64 tiles of the symmetric K (diagonal tiles hold both triangles): row part from tiles (I, J<=I),
-// transposed part from tiles (J>I, I). Per-block partial sums of r^2 and y^2 go to partial[2b..2b+1].
+// transposed part from tiles (J>I, I). Per-block partials (6 doubles): sum r^2, sum y^2,
+// max |r|, max row sum |K_i.|, max |alpha|, max |y| (for the normwise backward error).
 __global__ void __launch_bounds__(kThreads) residual_kernel(const double* __restrict__ Kt, int T, int Mt,
                                                             long long n, const double* __restrict__ y,
                                                             const double* __restrict__ alpha, double* __restrict__ r,
                                                             double* __restrict__ partial) {
   __shared__ double red[kThreads / 32][32];
+  __shared__ double redabs[kThreads / 32][32];
+  __shared__ double rowsum[32], rowabs[32];
+  __shared__ double stat[6][32];
   const int nch = T / 32;
   const int I = blockIdx.x / nch, ch = blockIdx.x % nch;
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   const size_t TT = (size_t)T * T;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // rows ch*32 + w*4 + k, lane-partial
+  double abs4[4] = {0.0, 0.0, 0.0, 0.0};
   for (int J = 0; J <= I; ++J) {
     const double* tile = Kt + tri(I, J) * TT + (size_t)(ch * 32 + w * 4) * T;
     const double* aJ = alpha + (size_t)J * T;
     for (int c = lane; c < T; c += 32) {
       const double av = aJ[c];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = fma(tile[(size_t)k * T + c], av, acc[k]);
+      for (int k = 0; k < 4; ++k) {
+        const double kv = tile[(size_t)k * T + c];
+        acc[k] = fma(kv, av, acc[k]);
+        abs4[k] += fabs(kv);
+      }
     }
   }
-  double accT = 0.0;  // column ch*32 + lane, warp-partial over rows
+  double accT = 0.0, absT = 0.0;  // column ch*32 + lane, warp-partial over rows
   for (int J = I + 1; J < Mt; ++J) {
     const double* tile = Kt + tri(J, I) * TT + ch * 32 + lane;
     const double* aJ = alpha + (size_t)J * T;
-    for (int rr = w; rr < T; rr += kThreads / 32) accT = fma(tile[(size_t)rr * T], aJ[rr], accT);
+    for (int rr = w; rr < T; rr += kThreads / 32) {
+      const double kv = tile[(size_t)rr * T];
+      accT = fma(kv, aJ[rr], accT);
+      absT += fabs(kv);
+    }
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+      abs4[k] += __shfl_xor_sync(0xffffffffu, abs4[k], o);
+    }
   }
   red[w][lane] = accT;
+  redabs[w][lane] = absT;
   __syncthreads();
-  __shared__ double rowsum[32];
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) t += red[q][threadIdx.x];
+    double t = 0.0, u = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) {
+      t += red[q][threadIdx.x];
+      u += redabs[q][threadIdx.x];
+    }
     rowsum[threadIdx.x] = t;
+    rowabs[threadIdx.x] = u;
   }
   __syncthreads();
-  __shared__ double sq[2][32];
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int row = ch * 32 + w * 4 + k;
       const long long gi = (long long)I * T + row;
       const double tot = acc[k] + rowsum[w * 4 + k];
-      const double yi = gi < n ? y[gi] : 0.0;
-      const double ri = gi < n ? yi - tot : 0.0;
+      const bool in = gi < n;
+      const double yi = in ? y[gi] : 0.0;
+      const double ri = in ? yi - tot : 0.0;
       r[gi] = ri;
-      sq[0][w * 4 + k] = ri * ri;
-      sq[1][w * 4 + k] = yi * yi;
+      const int q = w * 4 + k;
+      stat[0][q] = ri * ri;
+      stat[1][q] = yi * yi;
+      stat[2][q] = fabs(ri);
+      stat[3][q] = in ? abs4[k] + rowabs[q] : 0.0;
+      stat[4][q] = in ? fabs(alpha[gi]) : 0.0;
+      stat[5][q] = fabs(yi);
     }
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x < 6) {
     double t = 0.0;
-    for (int k = 0; k < 32; ++k) t += sq[threadIdx.x][k];
-    partial[2 * blockIdx.x + threadIdx.x] = t;
+    for (int k = 0; k < 32; ++k) t = threadIdx.x < 2 ? t + stat[threadIdx.x][k] : fmax(t, stat[threadIdx.x][k]);
+    partial[6 * blockIdx.x + threadIdx.x] = t;
   }
 }
 
-// out[0] = sum of even partials (||r||^2), out[1] = sum of odd partials (||y||^2); one CTA.
-__global__ void __launch_bounds__(kThreads) sum_pairs_kernel(const double* __restrict__ partial, int nb,
-                                                             double* __restrict__ out) {
-  __shared__ double red[2][kThreads / 32];
-  double s0 = 0.0, s1 = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kThreads) {
-    s0 += partial[2 * b];
-    s1 += partial[2 * b + 1];
-  }
+// out[0..2) = sums and out[2..6) = maxima of the per-block residual partials; one CTA.
+__global__ void __launch_bounds__(kThreads) reduce_residual_kernel(const double* __restrict__ partial, int nb,
+                                                                   double* __restrict__ out) {
+  __shared__ double red[6][kThreads / 32];
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += kThreads)
+    for (int k = 0; k < 6; ++k) v[k] = k < 2 ? v[k] + partial[6 * b + k] : fmax(v[k], partial[6 * b + k]);
+  for (int k = 0; k < 6; ++k) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-  }
-  if (threadIdx.x % 32 == 0) {
-    red[0][threadIdx.x / 32] = s0;
-    red[1][threadIdx.x / 32] = s1;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double x = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = k < 2 ? v[k] + x : fmax(v[k], x);
+    }
+    if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x < 6) {
     double t = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) t += red[threadIdx.x][q];
+    for (int q = 0; q < kThreads / 32; ++q) t = threadIdx.x < 2 ? t + red[threadIdx.x][q] : fmax(t, red[threadIdx.x][q]);
     out[threadIdx.x] = t;
   }
 }
@@ -397,6 +513,223 @@ __global__ void __launch_bounds__(kThreads) logdet_kernel(const double* __restri
     double t = 0.0;
     for (int q = 0; q < kThreads / 32; ++q) t += red[q];
     out[0] = 2.0 * t;
+  }
+}
+
+// beta_I[c] = sum_{K>=I} sum_r L_KI[r][c] alpha_K[r]  (beta = L^T alpha); one CTA per (I, 32-column chunk).
+__global__ void __launch_bounds__(kThreads) beta_kernel(const double* __restrict__ Lt, int T, int Mt,
+                                                        const double* __restrict__ alpha, double* __restrict__ beta) {
+  __shared__ double red[kThreads / 32][32];
+  const int nch = T / 32;
+  const int I = blockIdx.x / nch, ch = blockIdx.x % nch;
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const size_t TT = (size_t)T * T;
+  double acc = 0.0;
+  for (int K = I; K < Mt; ++K) {
+    const double* tile = Lt + tri(K, I) * TT + ch * 32 + lane;
+    const double* aK = alpha + (size_t)K * T;
+    for (int rr = w; rr < T; rr += kThreads / 32) acc = fma(tile[(size_t)rr * T], aK[rr], acc);
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q][threadIdx.x];
+    beta[(size_t)I * T + ch * 32 + threadIdx.x] = t;
+  }
+}
+
+// Lbar = -tril(alpha beta^T) + diag(1/L_ii) on the first n rows/columns, 0 elsewhere (and above the
+// diagonal of diagonal tiles). Tile blockIdx.x, rows [blockIdx.y*32, +32).
+__global__ void __launch_bounds__(kThreads) init_lbar_kernel(const double* __restrict__ Lt, double* __restrict__ Bt,
+                                                             int T, long long n, const double* __restrict__ alpha,
+                                                             const double* __restrict__ beta) {
+  const long long t = blockIdx.x;
+  long long I = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > t) --I;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  const long long J = t - I * (I + 1) / 2;
+  const size_t base = (size_t)t * T * T;
+  for (int e = threadIdx.x; e < 32 * T; e += kThreads) {
+    const int r = blockIdx.y * 32 + e / T, c = e % T;
+    const long long i = I * T + r, j = J * T + c;
+    double v = 0.0;
+    if (i < n && j < n && i >= j) {
+      v = -alpha[i] * beta[j];
+      if (i == j) v += 1.0 / Lt[base + (size_t)r * T + c];
+    }
+    Bt[base + (size_t)r * T + c] = v;
+  }
+}
+
+// Per-(tile, 32-row chunk) partial sums of Abar_ij * dK_ij/dtheta over stored lower entries with
+// i, j < n, theta = (l, v, s2), the kernel entries recomputed from X.
+template <int D>
+__global__ void __launch_bounds__(kThreads) grad_contract_kernel(const double* __restrict__ Bt, int T,
+                                                                 const double* __restrict__ X, long long n, int Dr,
+                                                                 double l, double v, double* __restrict__ partial) {
+  __shared__ double red[3][kThreads / 32];
+  const long long t = blockIdx.x;
+  long long I = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > t) --I;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  const long long J = t - I * (I + 1) / 2;
+  const size_t base = (size_t)t * T * T;
+  const double neg_half_inv_l2 = -0.5 / (l * l), inv_l3 = 1.0 / (l * l * l);
+  double gl = 0.0, gv = 0.0, gs = 0.0;
+  for (int e = threadIdx.x; e < 32 * T; e += kThreads) {
+    const int r = blockIdx.y * 32 + e / T, c = e % T;
+    const long long i = I * T + r, j = J * T + c;
+    if (i >= n || j >= n || j > i) continue;
+    double wgt = Bt[base + (size_t)r * T + c];
+    if (i == j) wgt *= 0.5;  // diagonal tiles hold Abar + Abar^T
+    const double r2 = sqdist_t<D>(X + i * Dr, X + j * Dr, Dr);
+    const double ex = exp(r2 * neg_half_inv_l2);
+    gl = fma(wgt, v * ex * r2 * inv_l3, gl);
+    gv = fma(wgt, ex, gv);
+    if (i == j) gs += wgt;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gl += __shfl_xor_sync(0xffffffffu, gl, o);
+    gv += __shfl_xor_sync(0xffffffffu, gv, o);
+    gs += __shfl_xor_sync(0xffffffffu, gs, o);
+  }
+  if (threadIdx.x % 32 == 0) {
+    red[0][threadIdx.x / 32] = gl;
+    red[1][threadIdx.x / 32] = gv;
+    red[2][threadIdx.x / 32] = gs;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) s += red[threadIdx.x][q];
+    partial[3 * ((size_t)blockIdx.x * gridDim.y + blockIdx.y) + threadIdx.x] = s;
+  }
+}
+
+// out[k] = sum_b partial[3b + k], k < 3 (one CTA, fixed order).
+__global__ void __launch_bounds__(kThreads) sum3_kernel(const double* __restrict__ partial, long long nb,
+                                                        double* __restrict__ out) {
+  __shared__ double red[3][kThreads / 32];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long b = threadIdx.x; b < nb; b += kThreads)
+    for (int k = 0; k < 3; ++k) s[k] += partial[3 * b + k];
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (threadIdx.x % 32 == 0) red[k][threadIdx.x / 32] = s[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[threadIdx.x][q];
+    out[threadIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                       long long n, double* __restrict__ out) {
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += kThreads) s = fma(a[i], b[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+    out[0] = t;
+  }
+}
+
+// Batched assembly and right-hand sides, one work item per CTA (see launch_batch_pre).
+__global__ void __launch_bounds__(kThreads) batch_pre_kernel(const int4* __restrict__ items,
+                                                             const GpDesc* __restrict__ descs, int noisy_prior) {
+  const int4 it = items[blockIdx.x];
+  const GpDesc& d = descs[it.y];
+  const double c = -0.5 / (d.l * d.l);
+  const int T = d.T;
+  if (it.x == 0) {  // K tile it.z, rows [it.w*32, +32)
+    const long long t = it.z;
+    long long I = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    const long long J = t - I * (I + 1) / 2;
+    double* tile = d.Kt + (size_t)t * T * T;
+    for (int e = threadIdx.x; e < 32 * T; e += kThreads) {
+      const int r = it.w * 32 + e / T, cc = e % T;
+      const long long i = I * T + r, j = J * T + cc;
+      double val;
+      if (i < d.n && j < d.n)
+        val = d.v * exp(sqdist_t<0>(d.X + i * d.D, d.X + j * d.D, d.D) * c) + (i == j ? d.s2 : 0.0);
+      else
+        val = (i == j) ? 1.0 : 0.0;
+      tile[(size_t)r * T + cc] = val;
+    }
+  } else if (it.x == 1 || it.x == 2) {  // dense rows [it.z, it.z + 8) of K_{X,Xs} (V) or K_{Xs,Xs} (S)
+    const bool isV = it.x == 1;
+    double* out = isV ? d.V : d.S;
+    const long long ld = isV ? d.ldv : d.lds;
+    const double* A = isV ? d.X : d.Xs;
+    const long long na = isV ? d.n : d.m;
+    const double diag = (!isV && noisy_prior) ? d.s2 : 0.0;
+    for (int q = 0; q < 8; ++q) {
+      const long long i = (long long)it.z + q;
+      for (long long j = threadIdx.x; j < ld; j += kThreads) {
+        double val = 0.0;
+        if (i < na && j < d.m)
+          val = d.v * exp(sqdist_t<0>(A + i * d.D, d.Xs + j * d.D, d.D) * c) + ((!isV && i == j) ? diag : 0.0);
+        out[(size_t)i * ld + j] = val;
+      }
+    }
+  } else {  // right-hand side of the mean solve
+    const long long npad = (long long)d.Mt * T;
+    for (long long i = threadIdx.x; i < npad; i += kThreads) d.bvec[i] = i < d.n ? d.y[i] : 0.0;
+  }
+}
+
+// Batched outputs: fused mean GEMV (8 test points per item) and covariance copy (8 rows per item).
+__global__ void __launch_bounds__(kThreads) batch_post_kernel(const int4* __restrict__ items,
+                                                              const GpDesc* __restrict__ descs) {
+  __shared__ double red[8][kThreads / 32];
+  const int4 it = items[blockIdx.x];
+  const GpDesc& d = descs[it.y];
+  if (it.x == 0) {
+    const double c = -0.5 / (d.l * d.l);
+    const long long i0 = it.z;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (long long j = threadIdx.x; j < d.n; j += kThreads) {
+      const double aj = d.bvec[j];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + q < d.m)
+          acc[q] = fma(d.v * exp(sqdist_t<0>(d.Xs + (i0 + q) * d.D, d.X + j * d.D, d.D) * c), aj, acc[q]);
+    }
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[q][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && i0 + threadIdx.x < d.m) {
+      double t = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) t += red[threadIdx.x][q];
+      d.mean[i0 + threadIdx.x] = t;
+    }
+  } else if (d.cov) {
+    for (int q = 0; q < 8; ++q) {
+      const long long a = (long long)it.z + q;
+      if (a >= d.m) break;
+      for (long long b = threadIdx.x; b < d.m; b += kThreads)
+        d.cov[a * d.m + b] = (a >= b) ? d.S[a * d.lds + b] : d.S[b * d.lds + a];
+    }
   }
 }
 
@@ -470,21 +803,42 @@ cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long r
   return cudaGetLastError();
 }
 
-cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st) {
+cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse, bool batch) {
   if (a.ntasks == 0) return cudaSuccess;
-  if (mixed)
-    dag_kernel<true><<<grid, kThreads, 0, st>>>(a);
-  else
-    dag_kernel<false><<<grid, kThreads, 0, st>>>(a);
+  if (batch) {
+    if (mixed)
+      dag_kernel<true, false, true><<<grid, kThreads, 0, st>>>(a);
+    else
+      dag_kernel<false, false, true><<<grid, kThreads, 0, st>>>(a);
+  } else if (reverse) {
+    if (mixed)
+      dag_kernel<true, true, false><<<grid, kThreads, 0, st>>>(a);
+    else
+      dag_kernel<false, true, false><<<grid, kThreads, 0, st>>>(a);
+  } else {
+    if (mixed)
+      dag_kernel<true, false, false><<<grid, kThreads, 0, st>>>(a);
+    else
+      dag_kernel<false, false, false><<<grid, kThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
+}
+
+int dag_max_ctas_per_sm_batch(bool mixed) {
+  int nb = 0;
+  if (mixed)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, true>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false, false, true>, kThreads, 0);
+  return nb;
 }
 
 int dag_max_ctas_per_sm(bool mixed) {
   int nb = 0;
   if (mixed)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, false>, kThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false, false, false>, kThreads, 0);
   return nb;
 }
 
@@ -492,7 +846,50 @@ cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const 
                             double* r, double* partial, double* norms, cudaStream_t st) {
   const int nb = Mt * (T / 32);
   residual_kernel<<<nb, kThreads, 0, st>>>(Kt, T, Mt, n, y, alpha, r, partial);
-  sum_pairs_kernel<<<1, kThreads, 0, st>>>(partial, nb, norms);
+  reduce_residual_kernel<<<1, kThreads, 0, st>>>(partial, nb, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs, bool noisy_prior, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  batch_pre_kernel<<<nitems, kThreads, 0, st>>>(items, descs, noisy_prior ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_post(const int4* items, int nitems, const GpDesc* descs, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  batch_post_kernel<<<nitems, kThreads, 0, st>>>(items, descs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_beta(const double* Lt, int T, int Mt, const double* alpha, double* beta, cudaStream_t st) {
+  beta_kernel<<<Mt * (T / 32), kThreads, 0, st>>>(Lt, T, Mt, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_lbar(const double* Lt, double* Bt, int T, int Mt, long long n, const double* alpha,
+                             const double* beta, cudaStream_t st) {
+  dim3 grid((unsigned)((long long)Mt * (Mt + 1) / 2), (unsigned)(T / 32));
+  init_lbar_kernel<<<grid, kThreads, 0, st>>>(Lt, Bt, T, n, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* X, long long n, int D, double l,
+                                 double v, double* partial, double* out, cudaStream_t st) {
+  const long long ntiles = (long long)Mt * (Mt + 1) / 2;
+  dim3 grid((unsigned)ntiles, (unsigned)(T / 32));
+  switch (D) {
+    case 4: grad_contract_kernel<4><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
+    case 8: grad_contract_kernel<8><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
+    case 16: grad_contract_kernel<16><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
+    default: grad_contract_kernel<0><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
+  }
+  sum3_kernel<<<1, kThreads, 0, st>>>(partial, ntiles * (T / 32), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* out, cudaStream_t st) {
+  dot_kernel<<<1, kThreads, 0, st>>>(a, b, n, out);
   return cudaGetLastError();
 }
 

@@ -18,8 +18,41 @@ enum TaskKind {
   TASK_FSOLVE = 6,  // (J)        b_J = L_JJ^{-1} b_J                    Eq. (2), L beta = y
   TASK_FGEMV = 7,   // (I, J, ch) b_I[ch] -= L_IJ[ch,:] b_J
   TASK_BSOLVE = 8,  // (J)        b_J = L_JJ^{-T} b_J                    Eq. (2), L^T alpha = beta
-  TASK_BGEMV = 9    // (J, I, ch) b_J[ch] -= L_IJ[:,ch]^T b_I
+  TASK_BGEMV = 9,   // (J, I, ch) b_J[ch] -= L_IJ[:,ch]^T b_I
+  // Reverse sweep of the tiled Cholesky (the adjoint of Fig. 1's algorithm, for the NLML gradient):
+  // Lbar -> Kbar tile by tile, columns J = Mt-1 .. 0. Bt holds Lbar, then Abar (the adjoint of K's
+  // stored lower entries; a diagonal tile holds Abar + Abar^T).
+  TASK_RUPD = 10,   // (P, K, J)  Lbar_PJ -= Abar~_PK L_KJ    (reverse of step J's SYRK/GEMM updates)
+  TASK_RTRSM = 11,  // (P, J)     Abar_PJ = Lbar_PJ L_JJ^{-1} (reverse of TRSM(P, J))
+  TASK_RDIAG = 12,  // (P, J)     Lbar_JJ -= tril(Abar_PJ^T L_PJ)
+  TASK_RPOTRF = 13  // (J)        Abar_JJ = sym(L^{-T} Phi(L^T Lbar_JJ) L^{-1})  (reverse of POTRF(J))
 };
+
+// One GP of a batch: its inputs, outputs, hyperparameters and workspace (all device pointers).
+struct GpDesc {
+  const double* X;    // n x D
+  const double* y;    // n
+  const double* Xs;   // m x D
+  double* mean;       // m (output)
+  double* cov;        // m x m (output, may be null)
+  double* Kt;         // packed lower tiles
+  double* V;          // Mt*T x ldv
+  double* S;          // Mc*T x lds
+  double* bvec;       // Mt*T
+  int* cK;            // counters: lower tiles
+  int* cV;            // V tiles
+  int* cS;            // lower S tiles
+  int* cF;            // forward chunks
+  int* cB;            // backward chunks
+  int* dF;            // forward solve done
+  int* dB;            // backward solve done
+  long long n, m, ldv, lds;
+  double l, v, s2;
+  int D, T, Mt, Mc, nch, pad;
+};
+
+// Batched task encoding: kind | (gp index << 4) in the first component.
+constexpr int kBatchKindBits = 4;
 
 struct DagArgs {
   double* Kt;       // packed lower tiles (T x T row-major each), tile (I,J) at I(I+1)/2 + J
@@ -38,6 +71,12 @@ struct DagArgs {
   int* cB;          // per (tile row, chunk): backward updates applied
   int* dF;          // per tile row: forward solve done
   int* dB;          // per tile row: backward solve done
+  double* Bt;       // adjoint tiles (same packing as Kt)
+  double* Wt;       // per-diagonal-tile FP64 workspace of the reverse POTRF (Mt x T x T)
+  int* rc;          // per lower tile: reverse updates applied to Lbar_PJ
+  int* fa;          // per lower tile: Abar final
+  int* rd;          // per diagonal tile: reverse diagonal updates applied
+  const GpDesc* descs;  // batched launch: per-GP views (null otherwise)
   const int4* tasks;
   int ntasks;
   DevStatus* st;
@@ -56,12 +95,31 @@ cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long lo
 cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long row0, long long nrows, double* out,
                                cudaStream_t st);
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st);
-cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st);
+cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,
+                       bool batch = false);
+int dag_max_ctas_per_sm_batch(bool mixed);
+// Batched pre/post work, one CTA per work item {kind, gp, a, b}:
+//   pre:  0 = K tile a rows [b*32, +32); 1 = K_{X,Xs} rows [a, a+8); 2 = K_{Xs,Xs} rows [a, a+8);
+//         3 = rhs vector (y, zero padded)
+//   post: 0 = mean rows [a, a+8) (fused K_{Xs,X} alpha); 1 = covariance rows [a, a+8) copied/mirrored
+cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs, bool noisy_prior, cudaStream_t st);
+cudaError_t launch_batch_post(const int4* items, int nitems, const GpDesc* descs, cudaStream_t st);
 int dag_max_ctas_per_sm(bool mixed);
-// r = y - K alpha from packed lower FP64 tiles; norms[0] = ||r||^2, norms[1] = ||y||^2.
-// partial needs 2 * Mt * (T/32) doubles.
+// r = y - K alpha from packed lower FP64 tiles; norms = {||r||_2^2, ||y||_2^2, ||r||_inf, ||K||_inf,
+// ||alpha||_inf, ||y||_inf}. partial needs 6 * Mt * (T/32) doubles.
 cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
                             double* r, double* partial, double* norms, cudaStream_t st);
 cudaError_t launch_axpy(double* alpha, const double* d, long long n, cudaStream_t st);
+// beta = L^T alpha from the factor tiles (so that beta = L^{-1} y when alpha = K^{-1} y).
+cudaError_t launch_beta(const double* Lt, int T, int Mt, const double* alpha, double* beta, cudaStream_t st);
+// Lbar of the NLML w.r.t. L: -alpha beta^T on the lower triangle plus diag(1/L_ii), i, j < n.
+cudaError_t launch_init_lbar(const double* Lt, double* Bt, int T, int Mt, long long n, const double* alpha,
+                             const double* beta, cudaStream_t st);
+// Partials of sum over stored lower entries of Abar_ij dK_ij/d(l, v, s2), dK recomputed from X; then
+// out[0..3) = the three sums. partial needs 3 * Mt(Mt+1)/2 * (T/32) doubles.
+cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* X, long long n, int D, double l,
+                                 double v, double* partial, double* out, cudaStream_t st);
+// out[0] = sum_{i<n} a_i b_i (one CTA).
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* out, cudaStream_t st);
 
 }  // namespace gpk

@@ -131,6 +131,115 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
   return b.ordered(workers);
 }
 
+// Reverse of Fig. 1's algorithm for the adjoint Lbar -> Abar: for J = Mt-1 down to 0, first undo
+// step J's trailing updates (RUPD: Lbar_PJ -= Abar~_PK L_KJ for every P, K > J, K ascending), then
+// its TRSMs (RTRSM: Abar_PJ = Lbar_PJ L_JJ^{-1}, and RDIAG: Lbar_JJ -= tril(Abar_PJ^T L_PJ)), then
+// its POTRF (RPOTRF).
+std::vector<Task4> cholesky_adjoint_tasks(int Mt, int T, int workers, const CostModel& cm) {
+  Builder b;
+  const double t3 = (double)T * T * T;
+  const double spf_upd = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
+  const double c_rupd = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
+  const double c_rtrsm = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
+  const double c_rdiag = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
+  const double c_rpotrf = cm.task_overhead + cm.sec_per_flop * 3.0 * t3 / cm.trsm_eff;
+  std::vector<int> last(tri(Mt, 0), -1);   // last writer of Lbar/Abar of each lower tile
+  std::vector<int> final_(tri(Mt, 0), -1);  // task that made Abar of the tile final
+  for (int J = Mt - 1; J >= 0; --J) {
+    for (int P = J + 1; P < Mt; ++P)
+      for (int K = J + 1; K < Mt; ++K) {
+        const int hi = P > K ? P : K, lo = P > K ? K : P;
+        last[tri(P, J)] = b.add(TASK_RUPD, P, K, J, c_rupd, {final_[tri(hi, lo)], last[tri(P, J)]});
+      }
+    for (int P = J + 1; P < Mt; ++P) {
+      const int t = b.add(TASK_RTRSM, P, J, 0, c_rtrsm, {last[tri(P, J)]});
+      last[tri(P, J)] = t;
+      final_[tri(P, J)] = t;
+    }
+    for (int P = J + 1; P < Mt; ++P)
+      last[tri(J, J)] = b.add(TASK_RDIAG, P, J, 0, c_rdiag, {final_[tri(P, J)], last[tri(J, J)]});
+    const int t = b.add(TASK_RPOTRF, J, 0, 0, c_rpotrf, {last[tri(J, J)]});
+    last[tri(J, J)] = t;
+    final_[tri(J, J)] = t;
+  }
+  return b.ordered(workers);
+}
+
+namespace {
+
+// Appends GP g's Cholesky, mean-solve and (optionally) covariance tasks, with the cross-graph
+// dependencies on the factor tiles.
+void append_gp(Builder& b, int g, const BatchGp& gp, bool want_cov, const CostModel& cm) {
+  const int Mt = gp.Mt, Mc = gp.Mc, T = gp.T, nch = T / 32;
+  const int tag = g << kBatchKindBits;
+  const double t3 = (double)T * T * T;
+  const double spf = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
+  const double c_potrf = cm.task_overhead + cm.sec_per_flop * t3 / 3.0 / cm.potrf_eff;
+  const double c_trsm = cm.task_overhead + spf * t3 / cm.trsm_eff;
+  const double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
+  const double c_solve = cm.task_overhead + cm.sec_per_flop * (double)T * T / cm.vec_eff;
+  const double c_gemv = cm.task_overhead + cm.sec_per_flop * 2.0 * 32.0 * T / cm.vec_eff;
+  std::vector<int> last(tri(Mt, 0), -1);
+  for (int J = 0; J < Mt; ++J) {
+    const int po = b.add(TASK_POTRF | tag, J, 0, 0, c_potrf, {last[tri(J, J)]});
+    last[tri(J, J)] = po;
+    for (int I = J + 1; I < Mt; ++I) last[tri(I, J)] = b.add(TASK_TRSM | tag, I, J, 0, c_trsm, {po, last[tri(I, J)]});
+    for (int I = J + 1; I < Mt; ++I)
+      for (int K = J + 1; K <= I; ++K)
+        last[tri(I, K)] = b.add(TASK_UPD | tag, I, K, J, c_gemm, {last[tri(I, J)], last[tri(K, J)], last[tri(I, K)]});
+  }
+  // last[] now holds the task that made each factor tile final
+  std::vector<int> lastF((size_t)Mt * nch, -1), lastB((size_t)Mt * nch, -1), fsolve(Mt, -1);
+  for (int J = 0; J < Mt; ++J) {
+    b.tasks.push_back({TASK_FSOLVE | tag, J, 0, 0});
+    b.cost.push_back(c_solve);
+    std::vector<int> pr{last[tri(J, J)]};
+    for (int ch = 0; ch < nch; ++ch)
+      if (lastF[(size_t)J * nch + ch] >= 0) pr.push_back(lastF[(size_t)J * nch + ch]);
+    b.preds.push_back(pr);
+    fsolve[J] = (int)b.tasks.size() - 1;
+    for (int I = J + 1; I < Mt; ++I)
+      for (int ch = 0; ch < nch; ++ch)
+        lastF[(size_t)I * nch + ch] =
+            b.add(TASK_FGEMV | tag, I, J, ch, c_gemv, {fsolve[J], last[tri(I, J)], lastF[(size_t)I * nch + ch]});
+  }
+  for (int I = Mt - 1; I >= 0; --I) {
+    b.tasks.push_back({TASK_BSOLVE | tag, I, 0, 0});
+    b.cost.push_back(c_solve);
+    std::vector<int> pr{fsolve[I]};
+    for (int ch = 0; ch < nch; ++ch)
+      if (lastB[(size_t)I * nch + ch] >= 0) pr.push_back(lastB[(size_t)I * nch + ch]);
+    b.preds.push_back(pr);
+    const int bs = (int)b.tasks.size() - 1;
+    for (int J = 0; J < I; ++J)
+      for (int ch = 0; ch < nch; ++ch)
+        lastB[(size_t)J * nch + ch] =
+            b.add(TASK_BGEMV | tag, J, I, ch, c_gemv, {bs, fsolve[J], last[tri(I, J)], lastB[(size_t)J * nch + ch]});
+  }
+  if (!want_cov) return;
+  std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1);
+  for (int J = 0; J < Mt; ++J) {
+    for (int c = 0; c < Mc; ++c)
+      lastV[(size_t)J * Mc + c] = b.add(TASK_VTRSM | tag, J, c, 0, c_trsm, {last[tri(J, J)], lastV[(size_t)J * Mc + c]});
+    for (int I = J + 1; I < Mt; ++I)
+      for (int c = 0; c < Mc; ++c)
+        lastV[(size_t)I * Mc + c] = b.add(TASK_VGEMM | tag, I, J, c, c_gemm,
+                                          {last[tri(I, J)], lastV[(size_t)J * Mc + c], lastV[(size_t)I * Mc + c]});
+    for (int a = 0; a < Mc; ++a)
+      for (int bb = 0; bb <= a; ++bb)
+        lastS[tri(a, bb)] = b.add(TASK_WSYRK | tag, a, bb, J, c_gemm,
+                                  {lastV[(size_t)J * Mc + a], lastV[(size_t)J * Mc + bb], lastS[tri(a, bb)]});
+  }
+}
+
+}  // namespace
+
+std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm) {
+  Builder b;
+  for (size_t g = 0; g < gps.size(); ++g) append_gp(b, (int)g, gps[g], want_cov, cm);
+  return b.ordered(workers);
+}
+
 std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm) {
   Builder b;
   const int nch = T / 32;

@@ -24,8 +24,18 @@ struct CostModel {
 std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& cm);
 // Tasks of L V = B (B: Mt x Mc tiles) followed by S -= V^T V on the Mc x Mc lower tiles.
 std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm);
+// Tasks of the reverse sweep of the tiled Cholesky (adjoint of Fig. 1), columns J = Mt-1 .. 0.
+std::vector<Task4> cholesky_adjoint_tasks(int Mt, int T, int workers, const CostModel& cm);
 // Tasks of L beta = y then L^T alpha = beta on Mt tiles, vector chunks of 32 rows.
 std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm);
+
+// One dispatch order for a batch of independent GPs, each running its tiled Cholesky, the two
+// substitutions of the mean solve and the covariance solve (each solve task depending on the factor
+// tiles it reads). Task kinds carry the GP index in their high bits (kind | g << 4).
+struct BatchGp {
+  int Mt, Mc, T;
+};
+std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm);
 
 // Generic list scheduling: returns the start order of tasks with the given costs and
 // predecessor lists, simulated on `workers` identical workers.

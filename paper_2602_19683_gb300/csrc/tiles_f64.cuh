@@ -304,6 +304,58 @@ __device__ void cta_trsm_left(const double* L, int ldl, double* B, int ldb, int 
   }
 }
 
+// TRSM from the right with L not transposed: B[rows x nb] <- B L^{-1} (G L = B, columns solved from
+// the last: g_c = (b_c - sum_{k>c} g_k L_kc) / L_cc). Used by the Cholesky adjoint.
+__device__ void cta_trsm_right_N(const double* L, int ldl, double* B, int ldb, int rows, int nb, TileSmem& s) {
+  for (int k0 = nb - 32; k0 >= 0; k0 -= 32) {
+    tri32_load(s.tri, L + (size_t)k0 * ldl + k0, ldl);
+    for (int r = threadIdx.x; r < rows; r += kThreads) {
+      double x[32];
+      double* row = B + (size_t)r * ldb + k0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = ldcg(row + c);
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        double acc = x[c];
+#pragma unroll
+        for (int k = c + 1; k < 32; ++k) acc = fma(-x[k], s.tri.l[k][c], acc);
+        x[c] = acc * s.tri.inv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) row[c] = x[c];
+    }
+    __syncthreads();
+    if (k0 > 0)  // B[:, 0:k0] -= G[:, k0:k0+32] L[k0:k0+32, 0:k0]
+      cta_gemm_sub<A_MK, B_KN>(B, ldb, B + k0, ldb, L + (size_t)k0 * ldl, ldl, rows, k0, 32, false, 0, s.g);
+  }
+}
+
+// TRSM from the left with L transposed: B[nb x ncols] <- L^{-T} B (rows solved from the bottom:
+// x_i = (b_i - sum_{k>i} L_ki x_k) / L_ii). Used by the Cholesky adjoint.
+__device__ void cta_trsm_left_T(const double* L, int ldl, double* B, int ldb, int nb, int ncols, TileSmem& s) {
+  for (int k0 = nb - 32; k0 >= 0; k0 -= 32) {
+    tri32_load(s.tri, L + (size_t)k0 * ldl + k0, ldl);
+    for (int c = threadIdx.x; c < ncols; c += kThreads) {
+      double x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = ldcg(B + (size_t)(k0 + i) * ldb + c);
+#pragma unroll
+      for (int i = 31; i >= 0; --i) {
+        double acc = x[i];
+#pragma unroll
+        for (int k = i + 1; k < 32; ++k) acc = fma(-s.tri.l[k][i], x[k], acc);
+        x[i] = acc * s.tri.inv[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) B[(size_t)(k0 + i) * ldb + c] = x[i];
+    }
+    __syncthreads();
+    if (k0 > 0)  // B[0:k0, :] -= L[k0:k0+32, 0:k0]^T X
+      cta_gemm_sub<A_KM, B_KN>(B, ldb, L + (size_t)k0 * ldl, ldl, B + (size_t)k0 * ldb, ldb, k0, ncols, 32, false, 0,
+                               s.g);
+  }
+}
+
 // ---------------------------------------------------------------- vector solves (Eq. 2)
 
 // b[0..nb) <- L^{-1} b (forward substitution with one diagonal tile). Each 32-row strip: its 32 x 32

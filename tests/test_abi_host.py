@@ -120,7 +120,35 @@ def test_mean_schedule_is_topological(lib, Mt, T, workers):
     assert df == db == set(range(Mt))
 
 
+@pytest.mark.parametrize("Mt,workers,mixed", [(1, 2, 0), (2, 1, 0), (5, 7, 1), (9, 304, 0)])
+def test_adjoint_schedule_is_topological(lib, Mt, workers, mixed):
+    """The reverse sweep (adjoint of Fig. 1): for each J from the last column down, RUPD(P, K, J) for
+    all P, K > J with K ascending per P, after the adjoint of tile (max(P,K), min(P,K)) is final;
+    RTRSM(P, J) after all of them; RDIAG(P, J) in P order; RPOTRF(J) last. Mirrors the device's
+    counter waits."""
+    t = tasks(lib, 3, Mt, 0, 64, workers, mixed)
+    assert len(t) == sum((Mt - 1 - J) ** 2 + 2 * (Mt - 1 - J) + 1 for J in range(Mt))
+    rc, fa, rd = {}, set(), {}
+    for kind, p, q, r in t:
+        if kind == 10:
+            hi, lo = max(p, q), min(p, q)
+            assert p > r and q > r and (hi, lo) in fa and rc.get((p, r), 0) == q - r - 1
+            rc[(p, r)] = q - r
+        elif kind == 11:
+            assert rc.get((p, q), 0) == Mt - 1 - q
+            fa.add((p, q))
+        elif kind == 12:
+            assert (p, q) in fa and rd.get(q, 0) == p - q - 1
+            rd[q] = p - q
+        elif kind == 13:
+            assert rd.get(p, 0) == Mt - 1 - p
+            fa.add((p, p))
+        else:
+            raise AssertionError(kind)
+    assert fa == {(I, J) for I in range(Mt) for J in range(I + 1)}
+
+
 def test_schedule_rejects_bad_arguments(lib):
     assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
-    assert lib.gp_schedule_tasks(3, 4, 0, 64, 1, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(4, 4, 0, 64, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1

@@ -1,0 +1,72 @@
+"""Batched prediction of many independent GPs in one persistent launch (captured CUDA graph), against
+the single-GP entry points and the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import nfir
+import oracle
+from oracle import Hyper
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    __graft_entry__.build()
+    from paper_2602_19683_gb300 import api as A
+    return A
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def make_gps(B, m, seed0=2000):
+    rng = np.random.default_rng(seed0)
+    gps = []
+    for g in range(B):
+        n = int(rng.integers(40, 1400))
+        D = int(rng.choice([4, 8, 16]))
+        h = Hyper(float(rng.uniform(0.7, 1.5)), float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.05, 0.3)))
+        X, y, Xs, _ = nfir.make_dataset(n, m, D, seed0 + 2 * g)
+        gps.append((X, y, Xs, h))
+    return gps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_single_gp_and_oracle(api, precision):
+    gps = make_gps(14, 48)
+    ctx = api.Context(0, precision=precision)
+    batch = api.Batch(ctx, [(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(Xs).cuda(), h)
+                            for X, y, Xs, h in gps], want_cov=True)
+    for rep in range(2):  # the graph is relaunched with the same (reused) buffers
+        batch.run()
+        api.gp_sync(ctx)
+        for g, (X, y, Xs, h) in enumerate(gps):
+            ref = oracle.gp_predict(X, y, Xs, h)
+            em = rel(batch.means[g].cpu().numpy(), ref["mean"])
+            ec = rel(batch.covs[g].cpu().numpy(), ref["cov"])
+            if precision == "fp64":
+                assert em <= 1e-10 and ec <= 1e-9, (g, em, ec)
+            else:  # FP32 trailing updates, no refinement: FP32-class results
+                assert em <= 1e-3 and ec <= 1e-4, (g, em, ec)
+    batch.free()
+
+
+def test_batch_tiles_and_errors(api):
+    """Per-GP tile sizes (including tiles larger than n), and a not-positive-definite GP reported with
+    its index in the high bits of info."""
+    X1, y1, Xs1, _ = nfir.make_dataset(300, 16, 8, 1)
+    X2 = np.array([[0.0], [1.0], [0.0]])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = api.Context(0)
+    b = api.Batch(ctx, [(dev(X1), dev(y1), dev(Xs1), Hyper(1, 1, 0.1), 256),
+                        (dev(X2), dev(np.ones(3)), dev(X2), Hyper(1, 1, 0.0), 32)], want_cov=False)
+    b.run()
+    with pytest.raises(api.GPError) as e:
+        api.gp_sync(ctx)
+    assert e.value.status == 2 and (e.value.info >> 32) == 1 and (e.value.info & 0xFFFFFFFF) == 3
+    b.free()
