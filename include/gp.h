@@ -167,6 +167,23 @@ gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp
 gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
 gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
 
+/* Predictive mean (Eq. 2) of a small GP, end to end, without allocating anything -- no
+ * counterpart in the paper; it exists for callers that cannot call cudaMalloc (a real-time loop that
+ * must not touch the device allocator, a process whose device memory is fixed up front, or a host
+ * application that owns all device memory and lends the library only its inputs and outputs).
+ * X (n x D), y (n), Xs (m x D) and mean_out (m) are the caller's device arrays; nothing else is
+ * needed: no context, no factor. The library's workspace is one file-scope device array of about
+ * 4.5 MB (tiles of edge 64, counters, task lists, status word) that every GPU loading the library
+ * holds until the process exits; its address is looked up once per device, with that device
+ * current, on the first call made on it. n must be <= 1024 (larger n returns GP_ERR_INVALID_ARG).
+ * Runs on `cuda_stream` of the current device and waits for it, then returns the device status
+ * (GP_ERR_NOT_PD with *info = failing column, GP_ERR_TIMEOUT; info may be NULL). Every call shares
+ * the one array and leaves its contents behind; each call clears what must start at zero, but calls
+ * that overlap on the GPU (other streams or host threads) race on it. */
+gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
+                                  const double* Xs, int64_t m, double* mean_out, void* cuda_stream,
+                                  int64_t* info);
+
 /* Host-only introspection of the persistent kernel's dispatch order: writes the task list of graph
  * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
  * Cholesky used by gp_nlml_grad) for Mt tile rows, Mc covariance

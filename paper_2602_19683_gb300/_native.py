@@ -54,6 +54,7 @@ SIGNATURES = {
     "gp_sync": ([_P, ctypes.POINTER(_I64)], _I32),
     "gp_status_string": ([_I32], ctypes.c_char_p),
     "gp_launch_count": ([_P], _I64),
+    "gp_predict_mean_noalloc": ([_P, _P, _I64, _I32, gp_hyper, _P, _I64, _P, _P, ctypes.POINTER(_I64)], _I32),
     "gp_schedule_tasks": ([_I32, _I32, _I32, _I32, _I32, _I32, _P, _I64], _I64),
 }
 

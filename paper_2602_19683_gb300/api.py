@@ -193,6 +193,25 @@ def gp_nlml_grad(ctx: Context, X: torch.Tensor, y: torch.Tensor, hyper: Hyper):
     return nl.value, [g[0], g[1], g[2]]
 
 
+def gp_predict_mean_noalloc(X: torch.Tensor, y: torch.Tensor, Xs: torch.Tensor, hyper: Hyper, out: torch.Tensor,
+                            stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Mean of a small GP (n <= 1024) through the allocation-free entry point; `out` is caller-owned."""
+    n, D = X.shape
+    m = Xs.shape[0]
+    _dev(X, "X")
+    _dev(y, "y", (n,))
+    _dev(Xs, "Xs", (m, D))
+    _dev(out, "mean_out", (m,))
+    lib = N.load()
+    stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+    info = ctypes.c_int64(0)
+    s = lib.gp_predict_mean_noalloc(X.data_ptr(), y.data_ptr(), n, D, Hyper(*hyper).c, Xs.data_ptr(), m,
+                                    out.data_ptr(), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(info))
+    if s != N.GP_OK:
+        raise GPError(s, info.value, "gp_predict_mean_noalloc")
+    return out
+
+
 class Batch:
     """A gp_batch: many independent GPs assembled, factored and predicted by one captured CUDA graph
     (batched assembly, one persistent task-DAG launch, outputs). Entries are (X, y, Xs, hyper) or
