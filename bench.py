@@ -40,6 +40,9 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="solve", choices=["solve", "batch", "nlml"],
+                   help="solve: one large GP (the headline); batch: 512 uneven GPs in one graph launch; "
+                        "nlml: NLML gradient and Adam fitting at n = 16384")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--m", type=int, default=4096)
@@ -378,12 +381,122 @@ def ctx_tile(n, tile):
     return 256 if n >= 16384 else 128 if n >= 2048 else 64 if n >= 256 else 32
 
 
+def run_batch(args):
+    """512 independent GPs, n ~ U[128, 4096], m = 256, D in {4, 8, 16}: one CUDA-graph launch (batched
+    assembly + one persistent DAG launch + outputs) against a per-GP sequential loop over the single-GP
+    entry points. Metric: GPs per second (FP64 and FP32)."""
+    import torch
+    import nfir
+    from paper_2602_19683_gb300 import api
+    dev = torch.device("cuda", 0)
+    B, m = 512, 256
+    data = nfir.make_batch(B, m)
+    gps = [tuple(torch.from_numpy(a).to(dev) for a in (X, y, Xs)) + (api.Hyper(1.0, 1.0, 0.1),)
+           for X, y, Xs, _ in data]
+    res = {}
+    for prec in ("fp64", "fp32"):
+        ctx = api.Context(0, precision=prec)
+        b = api.Batch(ctx, gps, want_cov=True)
+        for _ in range(args.warmup):
+            b.run()
+        api.gp_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(args.steps):
+            b.run()
+        e1.record(ctx.stream)
+        api.gp_sync(ctx)
+        t = e0.elapsed_time(e1) / args.steps / 1e3
+        means64 = [x.clone() for x in b.means] if prec == "fp64" else None
+        res[prec] = {"s_per_batch": t, "gps_per_s": B / t}
+        if prec == "fp64":
+            ref_means = means64
+        else:
+            res[prec]["mean_err_vs_fp64"] = max(float((a - r).abs().max() / r.abs().max())
+                                                for a, r in zip(b.means, ref_means))
+        b.free()
+        # per-GP sequential loop over the single-GP entry points (same kernels, one GP at a time)
+        ctx2 = api.Context(0, precision=prec)
+        outs = [(torch.empty(m, dtype=torch.float64, device=dev), torch.empty((m, m), dtype=torch.float64, device=dev))
+                for _ in gps]
+
+        def loop():
+            for (X, y, Xs, h), (mo, co) in zip(gps, outs):
+                f = api.gp_assemble(ctx2, X, h)
+                api.gp_cholesky(ctx2, f)
+                api.gp_predict_mean(ctx2, f, y, Xs, out=mo)
+                api.gp_predict_full_cov(ctx2, f, Xs, out=co)
+                f.free()
+        loop()
+        api.gp_sync(ctx2)
+        e0.record(ctx2.stream)
+        loop()
+        e1.record(ctx2.stream)
+        api.gp_sync(ctx2)
+        tl = e0.elapsed_time(e1) / 1e3
+        res[prec]["loop_s"] = tl
+        res[prec]["loop_gps_per_s"] = B / tl
+        res[prec]["speedup_vs_loop"] = tl / t
+    line = {"metric": "batched GP prediction (512 uneven GPs, mean + full cov)", "value": res["fp64"]["gps_per_s"],
+            "unit": "GPs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fp64"]["s_per_batch"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic NFIR, 512 seeded trajectories",
+            "config": {"workload": "512 GPs, n ~ U[128,4096], m=256, D in {4,8,16}", "modes": res}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_nlml(args):
+    """NLML and its gradient at n = 16384 (D = 8) through the blocked Cholesky adjoint, FP64 and mixed,
+    then Adam from (l, v, s2) = (0.5, 2.0, 0.5) in mixed precision (50 steps) with the FP64 loss at
+    the end point."""
+    import torch
+    import nfir
+    from paper_2602_19683_gb300 import api
+    n = 16384
+    X, y, _, _ = nfir.make_dataset(n, 1, 8, 0)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        ctx = api.Context(0, precision=prec)
+        h = api.Hyper(1.0, 1.0, 0.1)
+        for _ in range(max(1, args.warmup)):
+            api.gp_nlml_grad(ctx, Xd, yd, h)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            nl, g = api.gp_nlml_grad(ctx, Xd, yd, h)
+        t = (time.perf_counter() - t0) / args.steps
+        res[prec] = {"s_per_grad": t, "nlml": nl, "grad": g,
+                     "tflops": (n ** 3 / 3 + 2 * n ** 3 / 3) / t / 1e12}
+    res["grad_rel_diff_fp32_vs_fp64"] = max(abs(a - b) for a, b in zip(res["fp32"]["grad"], res["fp64"]["grad"])) / \
+        max(abs(b) for b in res["fp64"]["grad"])
+    ctx = api.Context(0, precision="fp32")
+    t0 = time.perf_counter()
+    hist = api.fit_adam(ctx, Xd, yd, (0.5, 2.0, 0.5), steps=50)
+    t_adam = time.perf_counter() - t0
+    th = hist[-1][0]
+    nl64, _ = api.gp_nlml_grad(api.Context(0), Xd, yd, api.Hyper(*th))
+    res["adam_mixed"] = {"steps": 50, "s_total": t_adam, "theta_final": th, "nlml_final_fp32": hist[-1][1],
+                         "nlml_final_fp64": nl64}
+    line = {"metric": "NLML gradient s/grad at n=16384 (blocked Cholesky adjoint)", "value": res["fp64"]["s_per_grad"],
+            "unit": "s/grad", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fp64"]["s_per_grad"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic NFIR (seeded)",
+            "config": {"workload": "nlml grad n=16384 D=8", "modes": res}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "nlml":
+        return run_nlml(args)
     return run_ours(args)
 
 

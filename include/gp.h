@@ -53,8 +53,9 @@ enum {
  * (the diagonal POTRFs, the first block column's TRSMs and every residual stay FP64). */
 enum {
   GP_FP64 = 0,      /* everything FP64                                                          */
-  GP_FP32 = 1       /* FP32 trailing updates with FP32 accumulation; FP64 POTRF, first-column TRSM,
-                       FP64 iterative refinement of K^{-1} y                                     */
+  GP_FP32 = 1       /* FP32-class trailing updates with FP32 accumulation (tensor cores with 3xTF32
+                       split products, or FP32 FMAs); FP64 POTRF, first-column TRSM, FP64
+                       iterative refinement of K^{-1} y                                          */
 };
 
 typedef struct {
@@ -78,7 +79,12 @@ typedef struct {
                              its completion, so the bounded waits of the tasks that depend on it expire
                              and the call ends with GP_ERR_TIMEOUT. Leave both fields 0.              */
   int32_t withhold_enable;
-  int32_t reserved[5];
+  int32_t tensor_cores;   /* GP_FP32 trailing updates: 0 = tensor cores (tcgen05, 3xTF32 split products)
+                             when the tile edge is a multiple of 128, -1 = FP32 FMA pipes only       */
+  int32_t trace;          /* 1: the persistent kernel records, per task, the CTA and the %globaltimer
+                             times at which the task was taken, became ready and finished (read with
+                             gp_trace); 0 = off                                                       */
+  int32_t reserved[3];
 } gp_config;
 
 typedef struct gp_ctx gp_ctx;
@@ -195,6 +201,13 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap);
+
+/* Task trace of the last persistent-kernel launch on this context (cfg.trace = 1): for each task in
+ * dispatch order, {kind, p, q, r} as gp_schedule_tasks describes them (batched launches carry the GP
+ * index in kind's bits 4 and up) followed by {CTA, t_taken, t_ready, t_done} in ns of %globaltimer,
+ * 8 int64 per task, into out (host, room for cap tasks). Waits for the stream. Returns the task
+ * count, or -1 when tracing is off or nothing was traced. */
+int64_t gp_trace(gp_ctx* ctx, int64_t* out, int64_t cap);
 
 /* Human-readable name of a status code (static string). */
 const char* gp_status_string(gp_status s);

@@ -26,7 +26,7 @@ class gp_config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("precision", ctypes.c_int32), ("ir_tol", ctypes.c_double),
                 ("ir_maxit", ctypes.c_int32), ("noisy_prior", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("withhold_task", ctypes.c_int32), ("withhold_enable", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("tensor_cores", ctypes.c_int32), ("trace", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class gp_batch_desc(ctypes.Structure):
@@ -54,6 +54,7 @@ SIGNATURES = {
     "gp_sync": ([_P, ctypes.POINTER(_I64)], _I32),
     "gp_status_string": ([_I32], ctypes.c_char_p),
     "gp_launch_count": ([_P], _I64),
+    "gp_trace": ([_P, _P, _I64], _I64),
     "gp_predict_mean_noalloc": ([_P, _P, _I64, _I32, gp_hyper, _P, _I64, _P, _P, ctypes.POINTER(_I64)], _I32),
     "gp_schedule_tasks": ([_I32, _I32, _I32, _I32, _I32, _I32, _P, _I64], _I64),
 }

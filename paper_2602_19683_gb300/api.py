@@ -54,7 +54,8 @@ class Context:
 
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, tile: int = 0,
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
-                 timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None):
+                 timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
+                 tensor_cores: bool = True, trace: bool = False):
         self.lib = N.load()
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -66,6 +67,8 @@ class Context:
         cfg.noisy_prior = int(noisy_prior)
         cfg.timeout_ns = int(timeout_s * 1e9)
         cfg.grid = grid
+        cfg.tensor_cores = 0 if tensor_cores else -1
+        cfg.trace = int(trace)
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1
@@ -112,6 +115,35 @@ class Factor:
             self.free()
         except Exception:
             pass
+
+
+TASK_NAMES = ["POTRF", "TRSM", "UPDATE", "VTRSM", "VGEMM", "WSYRK", "FSOLVE", "FGEMV", "BSOLVE", "BGEMV",
+              "RUPD", "RTRSM", "RDIAG", "RPOTRF"]
+
+
+def gp_trace(ctx: Context):
+    """Per-task trace of the last persistent-kernel launch (Context(trace=True)): an int64 array of
+    rows {kind, p, q, r, cta, t_taken, t_ready, t_done} (ns)."""
+    import numpy as np
+    n = ctx.lib.gp_trace(ctx.h, None, 0)
+    if n < 0:
+        raise RuntimeError("no trace: create the context with trace=True and run a factorisation first")
+    out = np.zeros((n, 8), dtype=np.int64)
+    ctx.lib.gp_trace(ctx.h, out.ctypes.data, n)
+    return out
+
+
+def trace_to_chrome(rows, path: str):
+    """Writes a trace from gp_trace as Chrome-trace JSON (one row per CTA; wait and run slices)."""
+    import json
+    t0 = int(rows[:, 5].min())
+    ev = []
+    for kind, p, q, r, cta, tt, tr, td in rows.tolist():
+        name = f"{TASK_NAMES[kind & 15]}({p},{q},{r})" + (f" gp{kind >> 4}" if kind >> 4 else "")
+        ev.append({"name": "wait", "ph": "X", "pid": 0, "tid": cta, "ts": (tt - t0) / 1e3, "dur": (tr - tt) / 1e3})
+        ev.append({"name": name, "ph": "X", "pid": 0, "tid": cta, "ts": (tr - t0) / 1e3, "dur": (td - tr) / 1e3})
+    with open(path, "w") as fh:
+        json.dump({"traceEvents": ev}, fh)
 
 
 def gp_sync(ctx: Context) -> None:

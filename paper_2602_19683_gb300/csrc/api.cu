@@ -75,6 +75,9 @@ struct gp_ctx {
   long long launches = 0;
   std::map<TaskKey, TaskBuf> tasks;
   gp_factor* grad_factor = nullptr;  // reused by gp_nlml_grad across calls of the same size
+  DevBuf trace;                      // per-task timing records of the last launch (cfg.trace)
+  const void* trace_tasks = nullptr; // its task list (device)
+  int trace_ntasks = 0;
 };
 
 struct gp_batch {
@@ -155,6 +158,7 @@ gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
   a.st = c->d_status;
   a.timeout_ns = c->cfg.timeout_ns;
   a.withhold_task = c->cfg.withhold_enable ? c->cfg.withhold_task : -1;
+  a.use_umma = (f->precision == GP_FP32 && c->cfg.tensor_cores >= 0) ? 1 : 0;
   return a;
 }
 
@@ -163,6 +167,13 @@ gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb, bool mixed) {
   GP_CUDA(cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), c->stream));
   a.tasks = (const int4*)tb->buf.p;
   a.ntasks = tb->ntasks;
+  if (c->cfg.trace) {
+    GP_TRY(grow(c->trace, (size_t)tb->ntasks * 4 * sizeof(long long)));
+    GP_CUDA(cudaMemsetAsync(c->trace.p, 0, (size_t)tb->ntasks * 4 * sizeof(long long), c->stream));
+    a.trace = (long long*)c->trace.p;
+    c->trace_tasks = tb->buf.p;
+    c->trace_ntasks = tb->ntasks;
+  }
   const int g = c->grid[mixed ? 1 : 0];
   const int grid = g < tb->ntasks ? g : tb->ntasks;
   GP_CUDA(gpk::launch_dag(a, grid, mixed, c->stream));
@@ -235,6 +246,11 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   ctx->stream = (cudaStream_t)stream;
   ctx->cfg = c;
   ctx->sms = prop.multiProcessorCount;
+  if (gpk::dag_enable_umma() != cudaSuccess) {
+    cudaGetLastError();
+    c.tensor_cores = -1;  // no room for the tensor-core path's shared memory: FP32 FMAs instead
+    ctx->cfg.tensor_cores = -1;
+  }
   for (int mixed = 0; mixed < 2; ++mixed) {
     const int occ = gpk::dag_max_ctas_per_sm(mixed != 0);
     const int cap = mixed ? 1 : 2;
@@ -267,6 +283,7 @@ gp_status gp_destroy(gp_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->grad_factor) gp_factor_free(c, c->grad_factor);
   for (auto& kv : c->tasks) release(kv.second.buf);
+  release(c->trace);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalar) cudaFree(c->d_scalar);
   delete c;
@@ -280,6 +297,31 @@ gp_status gp_set_stream(gp_ctx* c, void* stream) {
 }
 
 int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
+
+int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
+  if (!c || !c->cfg.trace || !c->trace_tasks || c->trace_ntasks <= 0) return -1;
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const int64_t n = c->trace_ntasks;
+  if (out && cap > 0) {
+    const int64_t k = n < cap ? n : cap;
+    std::vector<int4> tk((size_t)k);
+    std::vector<long long> rec((size_t)k * 4);
+    if (cudaMemcpy(tk.data(), c->trace_tasks, (size_t)k * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(rec.data(), c->trace.p, (size_t)k * 4 * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    for (int64_t i = 0; i < k; ++i) {
+      int64_t* o = out + 8 * i;
+      o[0] = tk[i].x; o[1] = tk[i].y; o[2] = tk[i].z; o[3] = tk[i].w;
+      for (int j = 0; j < 4; ++j) o[4 + j] = rec[4 * i + j];
+    }
+  }
+  return n;
+}
 
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap) {
@@ -706,6 +748,7 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     a.st = c->d_status;
     a.timeout_ns = c->cfg.timeout_ns;
     a.withhold_task = -1;
+    a.use_umma = (mixed && c->cfg.tensor_cores >= 0) ? 1 : 0;
     const int occ = gpk::dag_max_ctas_per_sm_batch(mixed);
     const int cap = mixed ? 1 : 2;
     const int grid = c->sms * (occ >= cap ? cap : (occ > 0 ? occ : 1));

@@ -4,7 +4,7 @@
 #include <climits>
 
 #include "kernels.h"
-#include "tiles_f32.cuh"
+#include "umma.cuh"
 
 namespace gpk {
 
@@ -196,6 +196,32 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
   __shared__ int s_task;
   __shared__ double s_red[kThreads / 32][32];
   TileSmem& s = u.d;
+  // Tensor-core path of the mixed trailing updates: TMEM accumulator and two mbarriers per CTA.
+  constexpr bool kUmma = kMixed && !kRev;
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  UmmaState um;
+  const bool use_umma = kUmma && a0.use_umma;
+  if (kUmma && use_umma) {
+    if (threadIdx.x < 32) {
+      tmem_alloc(&s_tmem, kUmmaTmemCols);
+      tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma_fence_before();
+    __syncthreads();
+    umma_fence_after();
+    um.smem = reinterpret_cast<uint8_t*>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    um.bar = s_bar;
+    um.tmem = s_tmem;
+    um.phase[0] = um.phase[1] = 0;
+    um.pending[0] = um.pending[1] = 0;
+  }
   while (true) {
     if (threadIdx.x == 0) s_task = ld_relaxed(&a0.st->abort) ? INT_MAX : (int)atomicAdd(&a0.st->next_task, 1ull);
     __syncthreads();
@@ -230,9 +256,18 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     }
     const int T = a.T;
     const size_t TT = (size_t)T * T;
+    bool aborted = false;
     bool ok = true;
+    long long t_taken = 0;
+    if (a0.trace && threadIdx.x == 0) t_taken = (long long)globaltimer();
     if (threadIdx.x == 0) ok = wait_deps(a, tk, ti);
     if (__syncthreads_or(!ok)) break;
+    if (a0.trace && threadIdx.x == 0) {
+      long long* rec = a0.trace + 4 * (size_t)ti;
+      rec[0] = blockIdx.x;
+      rec[1] = t_taken;
+      rec[2] = (long long)globaltimer();
+    }
     const int p = tk.y, q = tk.z, r = tk.w;
     if (ti == a.withhold_task) continue;  // test hook: this task's completion is never published
     if constexpr (!kRev) {
@@ -241,7 +276,8 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         const int fail = cta_potrf(a.Kt + tri(p, p) * TT, T, T, s);
         if (fail) {
           if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, gp_tag + (long long)p * T + fail);
-          return;
+          aborted = true;
+          break;
         }
         cta_publish(a.cK + tri(p, p), p + 1);
         break;
@@ -254,7 +290,13 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
       case TASK_UPD:
-        if (kMixed)
+        if (kUmma && use_umma && T % kUmmaM == 0) {
+          if (!umma_gemm_sub(um, a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T, T,
+                             p == q, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kMixed)
           cta_gemm_sub_f32<0, 0>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T,
                                  T, p == q, u.f.g);
         else
@@ -363,6 +405,13 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       }
       }
     }
+    if (aborted) break;  // uniform across the CTA (set after a barrier-synchronised decision)
+    if (a0.trace && threadIdx.x == 0) a0.trace[4 * (size_t)ti + 3] = (long long)globaltimer();
+  }
+  if (kUmma && use_umma) {
+    umma_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(um.tmem, kUmmaTmemCols);
   }
 }
 
@@ -807,7 +856,7 @@ cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, 
   if (a.ntasks == 0) return cudaSuccess;
   if (batch) {
     if (mixed)
-      dag_kernel<true, false, true><<<grid, kThreads, 0, st>>>(a);
+      dag_kernel<true, false, true><<<grid, kThreads, a.use_umma ? kUmmaSmemBytes : 0, st>>>(a);
     else
       dag_kernel<false, false, true><<<grid, kThreads, 0, st>>>(a);
   } else if (reverse) {
@@ -817,11 +866,20 @@ cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, 
       dag_kernel<false, true, false><<<grid, kThreads, 0, st>>>(a);
   } else {
     if (mixed)
-      dag_kernel<true, false, false><<<grid, kThreads, 0, st>>>(a);
+      dag_kernel<true, false, false><<<grid, kThreads, a.use_umma ? kUmmaSmemBytes : 0, st>>>(a);
     else
       dag_kernel<false, false, false><<<grid, kThreads, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+cudaError_t dag_enable_umma() {
+  cudaError_t e = cudaFuncSetAttribute(dag_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kUmmaSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dag_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kUmmaSmemBytes);
+  return e;
 }
 
 int dag_max_ctas_per_sm_batch(bool mixed) {

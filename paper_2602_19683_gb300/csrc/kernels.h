@@ -82,6 +82,8 @@ struct DagArgs {
   DevStatus* st;
   long long timeout_ns;
   int withhold_task;  // test hook (-1 = off): this task's completion is never published
+  int use_umma;       // mixed mode: trailing updates on the tensor cores (tcgen05, 3xTF32)
+  long long* trace;   // optional: per task {CTA, t_taken, t_ready, t_done} (%globaltimer ns), 4 x int64
 };
 
 cudaError_t launch_assemble_tiles(const double* X, long long n, int D, double l, double v, double s2, double* Kt, int T,
@@ -98,6 +100,8 @@ cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cud
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,
                        bool batch = false);
 int dag_max_ctas_per_sm_batch(bool mixed);
+// Allows the dynamic shared memory of the tensor-core path (once per device).
+cudaError_t dag_enable_umma();
 // Batched pre/post work, one CTA per work item {kind, gp, a, b}:
 //   pre:  0 = K tile a rows [b*32, +32); 1 = K_{X,Xs} rows [a, a+8); 2 = K_{Xs,Xs} rows [a, a+8);
 //         3 = rhs vector (y, zero padded)

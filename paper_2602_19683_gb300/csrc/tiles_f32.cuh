@@ -7,6 +7,36 @@
 
 namespace gpk {
 
+// FP64 <-> FP32 conversions on the integer pipe. On GB300 the cvt instructions between double and
+// float issue on the FP64 pipe (about 2 per clock per SM, like an FP64 FMA), so staging FP64 operands
+// as FP32 with cvt would cost as much FP64 issue as the FP32 FMAs they feed. These do the same
+// IEEE conversion with 32-bit integer operations on the two halves of the double:
+//   narrowing: round to nearest, ties to even; results below the FP32 normal range flush to a
+//              signed zero, values beyond it become a signed infinity, NaN stays NaN;
+//   widening:  exact (FP32 subnormals flush to a signed zero).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const unsigned rem = lo & 0x1FFFFFFFu;                   // the 29 bits rounded away
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u));
+  const int e32 = e - 896;  // rebias 1023 -> 127
+  if (e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned inc = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((sign | ((unsigned)e32 << 23) | m) + inc);  // a mantissa carry bumps the exponent
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const unsigned hi = (e == 0xFFu) ? (sign | 0x7FF00000u | (m >> 3)) : (sign | ((e + 896u) << 20) | (m >> 3));
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+
 constexpr int SBM = 128, SBN = 128, SBK = 16, SPAD = 4;
 
 struct GemmSmemF32 {
@@ -35,11 +65,11 @@ __device__ __forceinline__ void g32_store(float (*s)[SBM + SPAD], const double (
   if (L == 0) {
     const int x = t / 2, k = 8 * (t % 2);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[k + q][x] = (float)r[q];
+    for (int q = 0; q < 8; ++q) s[k + q][x] = f64_to_f32_rn(r[q]);
   } else {
     const int k = t / 16, x = 8 * (t % 16);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[k][x + q] = (float)r[q];
+    for (int q = 0; q < 8; ++q) s[k][x + q] = f64_to_f32_rn(r[q]);
   }
 }
 
@@ -100,7 +130,7 @@ __device__ void cta_gemm_sub_f32(double* C, int ldc, const double* A, int lda, c
         const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
         if (n >= N || (lower && n > m)) continue;
         double* c = C + (size_t)m * ldc + n;
-        *c = ldcg(c) - (double)acc[i][j];
+        *c = ldcg(c) - f32_to_f64(acc[i][j]);
       }
     }
     __syncthreads();
@@ -115,7 +145,7 @@ struct Tri32F {
 __device__ __forceinline__ void tri32f_load(Tri32F& s, const double* L, int ldl) {
   for (int e = threadIdx.x; e < 32 * 32; e += kThreads) {
     const int i = e / 32, j = e % 32;
-    s.l[i][j] = (j <= i) ? (float)ldcg(L + (size_t)i * ldl + j) : 0.f;
+    s.l[i][j] = (j <= i) ? f64_to_f32_rn(ldcg(L + (size_t)i * ldl + j)) : 0.f;
   }
   __syncthreads();
   if (threadIdx.x < 32) s.inv[threadIdx.x] = 1.f / s.l[threadIdx.x][threadIdx.x];
@@ -128,7 +158,7 @@ __device__ void cta_trsm_rows32_f32(const Tri32F& s, double* B, int ldb, int row
     float x[32];
     double* row = B + (size_t)r * ldb;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) x[c] = (float)ldcg(row + c);
+    for (int c = 0; c < 32; ++c) x[c] = f64_to_f32_rn(ldcg(row + c));
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       float acc = x[c];
@@ -137,7 +167,7 @@ __device__ void cta_trsm_rows32_f32(const Tri32F& s, double* B, int ldb, int row
       x[c] = acc * s.inv[c];
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) row[c] = (double)x[c];
+    for (int c = 0; c < 32; ++c) row[c] = f32_to_f64(x[c]);
   }
   __syncthreads();
 }
@@ -147,7 +177,7 @@ __device__ void cta_trsm_cols32_f32(const Tri32F& s, double* B, int ldb, int nco
   for (int c = threadIdx.x; c < ncols; c += kThreads) {
     float x[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) x[i] = (float)ldcg(B + (size_t)i * ldb + c);
+    for (int i = 0; i < 32; ++i) x[i] = f64_to_f32_rn(ldcg(B + (size_t)i * ldb + c));
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       float acc = x[i];
@@ -156,7 +186,7 @@ __device__ void cta_trsm_cols32_f32(const Tri32F& s, double* B, int ldb, int nco
       x[i] = acc * s.inv[i];
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) B[(size_t)i * ldb + c] = (double)x[i];
+    for (int i = 0; i < 32; ++i) B[(size_t)i * ldb + c] = f32_to_f64(x[i]);
   }
   __syncthreads();
 }

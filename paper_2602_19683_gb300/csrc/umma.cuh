@@ -1,0 +1,238 @@
+// Tensor-core (tcgen05) trailing update of the mixed-precision factorisation: C (FP64) -= A B^T with
+// the product formed from three TF32 split products (3xTF32: a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// a = a_hi + a_lo with a_hi the TF32 rounding of the FP32 value and a_lo the FP32 remainder),
+// accumulated in FP32 in tensor memory (TMEM).
+//
+// Per 128 x 128 output block: K is walked in 32-wide chunks; for each chunk all threads load the FP64
+// operands (L2), split them, and store the four operand tiles (A_hi, A_lo, B_hi, B_lo; 128 rows x 128
+// bytes each) in the canonical K-major 128-byte-swizzled layout; one thread issues the 12 MMAs of the
+// chunk (4 K-steps of 8 x 3 products, M = N = 128) and commits them to the chunk's mbarrier. Two
+// operand stages let the next chunk's staging overlap the current chunk's MMAs. The epilogue reads
+// the accumulator with tcgen05.ld (warp w owns TMEM lanes 32(w%4).. and a 64-column half) and
+// subtracts it from C in FP64.
+//
+// Every mbarrier wait is bounded by the task's time limit; a wait that gives up reports
+// GP_ERR_TIMEOUT and the caller returns after freeing its TMEM.
+#pragma once
+#include "tiles_f32.cuh"
+
+namespace gpk {
+
+constexpr int kUmmaM = 128, kUmmaN = 128, kUmmaKChunk = 32;
+constexpr int kUmmaTileBytes = kUmmaM * 128;           // 128 rows x 32 tf32
+constexpr int kUmmaStageBytes = 4 * kUmmaTileBytes;    // A_hi, A_lo, B_hi, B_lo
+constexpr int kUmmaSmemBytes = 2 * kUmmaStageBytes + 1024;  // two stages + alignment slack
+constexpr int kUmmaTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, int ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete. False on time-out / abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, long long timeout_ns,
+                                          long long where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((long long)(globaltimer() - t0) > timeout_ns) {
+      raise_error(st, GP_ERR_TIMEOUT, where);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void umma_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32, both K-major, M = N = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kUmmaN >> 3) << 17) |
+                                ((uint32_t)(kUmmaM >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Per-CTA state of the tensor-core path (lives in the persistent kernel for its whole run).
+struct UmmaState {
+  uint8_t* smem;       // 1024-aligned dynamic shared memory, 2 stages
+  uint64_t* bar;       // 2 mbarriers (smem)
+  uint32_t tmem;       // TMEM base address (128 columns)
+  uint32_t phase[2];   // next parity to wait for, per stage
+  uint32_t pending[2]; // stage has an uncompleted commit
+};
+
+// Waits (thread 0, bounded) until the MMAs committed to stage s have completed; the outcome is made
+// uniform across the CTA. On a time-out thread 0 waits once more (same bound) for the MMAs still in
+// flight, so that the caller can free TMEM, and the CTA returns false.
+__device__ __forceinline__ bool umma_stage_wait(UmmaState& u, int s, DevStatus* st, long long timeout_ns,
+                                                long long where) {
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    ok = mbar_wait(&u.bar[s], u.phase[s], st, timeout_ns, where);
+    if (!ok) {
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&u.bar[s], u.phase[s]) && (long long)(globaltimer() - t0) < timeout_ns) {
+      }
+    }
+  }
+  if (__syncthreads_or(!ok)) return false;
+  u.phase[s] ^= 1u;
+  u.pending[s] = 0;
+  return true;
+}
+
+// Byte offset of element (r, k) (k < 32) in a 128-row K-major tile with 128-byte swizzle.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7))) << 4) + (k & 3) * 4);
+}
+
+// Loads rows [r0, r0+128) x k [k0, k0+32) of the FP64 row-major operand P (ld), splits into TF32
+// hi / FP32 lo and stores both swizzled. 16 elements per thread.
+__device__ __forceinline__ void umma_stage_operand(uint8_t* hi_tile, uint8_t* lo_tile, const double* P, int ld, int r0,
+                                                   int k0) {
+  const int t = threadIdx.x;
+  const int r = t >> 1, kh = (t & 1) * 16;
+  const double2* src = reinterpret_cast<const double2*>(P + (size_t)(r0 + r) * ld + k0 + kh);
+  float hv[16], lv[16];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double2 d = __ldcg(src + q);
+    const float f0 = f64_to_f32_rn(d.x), f1 = f64_to_f32_rn(d.y);
+    const float h0 = __uint_as_float((__float_as_uint(f0) + 0x1000u) & 0xFFFFE000u);
+    const float h1 = __uint_as_float((__float_as_uint(f1) + 0x1000u) & 0xFFFFE000u);
+    hv[2 * q] = h0;
+    hv[2 * q + 1] = h1;
+    // the remainder is exact in FP32; round it to TF32 too (the tensor core would truncate it)
+    lv[2 * q] = __uint_as_float((__float_as_uint(f0 - h0) + 0x1000u) & 0xFFFFE000u);
+    lv[2 * q + 1] = __uint_as_float((__float_as_uint(f1 - h1) + 0x1000u) & 0xFFFFE000u);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t off = sw128_offset(r, kh + 4 * c);
+    *reinterpret_cast<float4*>(hi_tile + off) = make_float4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
+    *reinterpret_cast<float4*>(lo_tile + off) = make_float4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
+  }
+}
+
+// C[128 x 128 block at (m0, n0)] (FP64, ldc) -= A[m0.., 0..K) B[n0.., 0..K)^T, A and B FP64 row-major
+// K-contiguous (K a multiple of 32). lower: write only entries with n <= m (diagonal blocks).
+// Returns false on a time-out (error already raised).
+__device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                               int m0, int n0, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
+  const int nk = K / kUmmaKChunk;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    uint8_t* base = u.smem + s * kUmmaStageBytes;
+    if (u.pending[s]) {  // the MMAs that read this stage two chunks ago must be done
+      if (!umma_stage_wait(u, s, st, timeout_ns, where)) return false;
+    }
+    umma_stage_operand(base, base + kUmmaTileBytes, A, lda, m0, kc * kUmmaKChunk);
+    umma_stage_operand(base + 2 * kUmmaTileBytes, base + 3 * kUmmaTileBytes, B, ldb, n0, kc * kUmmaKChunk);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      umma_fence_after();
+      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + kUmmaTileBytes;
+      const uint32_t b_hi = a_hi + 2 * kUmmaTileBytes, b_lo = a_hi + 3 * kUmmaTileBytes;
+#pragma unroll
+      for (int ks = 0; ks < kUmmaKChunk / 8; ++ks) {
+        const uint32_t o = ks * 32;  // 8 tf32 = 32 bytes along K inside the swizzled row
+        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_hi + o), acc0);
+        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
+        umma_tf32(u.tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
+      }
+      umma_commit(&u.bar[s]);
+    }
+    u.pending[s] = 1;
+  }
+  // wait for every outstanding stage (the last commit covers all earlier MMAs)
+  for (int s = 0; s < 2; ++s)
+    if (u.pending[s]) {
+      if (!umma_stage_wait(u, s, st, timeout_ns, where)) return false;
+    }
+  umma_fence_after();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = (w & 3) * 32 + lane, colh = (w >> 2) * 64;
+  const int m = m0 + row;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    float v[32];
+    tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(colh + 32 * half), v);
+    double* crow = C + (size_t)m * ldc + n0 + colh + 32 * half;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = n0 + colh + 32 * half + j;
+      if (!lower || n <= m) crow[j] = ldcg(crow + j) - f32_to_f64(v[j]);
+    }
+  }
+  umma_fence_before();
+  __syncthreads();  // TMEM may be overwritten by the next block's MMAs
+  return true;
+}
+
+// C[M x N] -= A B^T on the tensor cores for M, N multiples of 128 and K a multiple of 32; lower skips
+// blocks above the diagonal and masks the diagonal blocks. Returns false on a time-out.
+__device__ bool umma_gemm_sub(UmmaState& u, double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                              int M, int N, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
+  for (int m0 = 0; m0 < M; m0 += kUmmaM)
+    for (int n0 = 0; n0 < N; n0 += kUmmaN) {
+      if (lower && n0 > m0) continue;
+      if (!umma_block_sub(u, C, ldc, A, lda, B, ldb, m0, n0, K, lower && n0 == m0, st, timeout_ns, where))
+        return false;
+    }
+  return true;
+}
+
+}  // namespace gpk
