@@ -34,6 +34,21 @@ def algorithmic_flops(n: int, m: int) -> float:
     return n ** 3 / 3 + n * n * m + n * m * m + 2 * n * n + 2 * n * m
 
 
+def max_over_ranks(values, ws: int, device=None):
+    """Element-wise maximum of per-rank timings over all ranks (identity for one rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_tflops(flops_per_replica: float, ws: int, ms: float) -> float:
+    """Throughput of the whole job: every rank solves one replica in the max-over-ranks time."""
+    return flops_per_replica * ws / (ms / 1e3) / 1e12
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -50,6 +65,8 @@ def parse():
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--trace", default="", help="after timing, run one traced Cholesky and write a Chrome trace "
+                                               "to this path; a per-task-kind summary joins the JSON line")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (GP_FP32) leg")
     p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
@@ -313,12 +330,9 @@ def run_ours(args):
             fac32[0].free()
             ctx32.close()
 
-    t = torch.tensor([ms, chol_ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, chol_ms, e2e_ms = t.tolist()
+    ms, chol_ms, e2e_ms = max_over_ranks([ms, chol_ms, e2e["ms"] if e2e else 0.0], ws, dev)
     flops = algorithmic_flops(n, m)
-    value = flops * ws / (ms / 1e3) / 1e12
+    value = whole_job_tflops(flops, ws, ms)
 
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -340,8 +354,10 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clocks}
     if mixed:
         line["mixed"] = mixed
+    if args.trace and rank == 0:
+        line["trace"] = traced_cholesky(api, local, Xd, h, args)
     if e2e:
-        line["e2e"] = {"value": flops * ws / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+        line["e2e"] = {"value": whole_job_tflops(flops, ws, e2e_ms), "unit": "TFLOP/s",
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -373,6 +389,29 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def traced_cholesky(api, local, Xd, h, args):
+    """One Cholesky with the per-task device trace on: per task kind, count and mean run/wait times,
+    plus the share of CTA time spent running tasks. Writes the Chrome trace to args.trace."""
+    import numpy as np
+    ctx = api.Context(local, tile=args.tile, precision=args.precision, trace=True)
+    f = api.gp_assemble(ctx, Xd, h)
+    api.gp_cholesky(ctx, f)
+    api.gp_sync(ctx)
+    rows = api.gp_trace(ctx)
+    api.trace_to_chrome(rows, args.trace)
+    span = (rows[:, 7].max() - rows[:, 5].min()) / 1e6
+    ncta = len(np.unique(rows[:, 4]))
+    out = {"span_ms": float(span), "ctas": int(ncta),
+           "busy_frac": float((rows[:, 7] - rows[:, 6]).sum() / 1e6 / (ncta * span))}
+    for k in np.unique(rows[:, 0] & 15):
+        sel = rows[(rows[:, 0] & 15) == k]
+        out[api.TASK_NAMES[k]] = {"count": int(len(sel)), "run_us": float(((sel[:, 7] - sel[:, 6]) / 1e3).mean()),
+                                  "wait_us": float(((sel[:, 6] - sel[:, 5]) / 1e3).mean())}
+    f.free()
+    ctx.close()
+    return out
 
 
 def ctx_tile(n, tile):

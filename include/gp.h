@@ -120,6 +120,11 @@ gp_status gp_predict_mean(gp_ctx* ctx, gp_factor* L, const double* y, const doub
 /* Eq. (3): cov (m x m, both triangles written) = K_{Xs,Xs} - V^T V with L V = K_{X,Xs}. */
 gp_status gp_predict_full_cov(gp_ctx* ctx, gp_factor* L, const double* Xs, int64_t m, double* cov_out);
 
+/* Predictive variances only, the diagonal of Eq. (3) (the paper notes that the diagonal of the
+ * posterior covariance holds the predictive variances, Sec. 3.1): var[j] = k(xs_j, xs_j) - ||V_:,j||^2
+ * with L V = K_{X,Xs}, without forming V^T V. var_out: device, m. */
+gp_status gp_predict_var(gp_ctx* ctx, gp_factor* L, const double* Xs, int64_t m, double* var_out);
+
 /* log det K = 2 sum log L_ii of the factor (host output; waits for the stream). */
 gp_status gp_logdet(gp_ctx* ctx, gp_factor* L, double* out);
 
@@ -192,7 +197,7 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
 
 /* Host-only introspection of the persistent kernel's dispatch order: writes the task list of graph
  * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
- * Cholesky used by gp_nlml_grad) for Mt tile rows, Mc covariance
+ * Cholesky used by gp_nlml_grad, 4 = the V solve of gp_predict_var) for Mt tile rows, Mc covariance
  * tile columns, tile edge T, `workers` CTAs and the cost model of precision `mixed` (0 = FP64,
  * 1 = GP_FP32) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),

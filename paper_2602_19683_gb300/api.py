@@ -208,6 +208,16 @@ def gp_alpha(ctx: Context, f: Factor) -> torch.Tensor:
     return out
 
 
+def gp_predict_var(ctx: Context, f: Factor, Xs: torch.Tensor, out: torch.Tensor | None = None):
+    m = Xs.shape[0]
+    _dev(Xs, "Xs", (m, f.D))
+    if out is None:
+        out = torch.empty(m, dtype=torch.float64, device=Xs.device)
+    _dev(out, "var_out", (m,))
+    _check(ctx.lib.gp_predict_var(ctx.h, f.h, Xs.data_ptr(), m, out.data_ptr()), "gp_predict_var")
+    return out
+
+
 def gp_logdet(ctx: Context, f: Factor) -> float:
     out = ctypes.c_double(0.0)
     _check(ctx.lib.gp_logdet(ctx.h, f.h, ctypes.byref(out)), "gp_logdet")

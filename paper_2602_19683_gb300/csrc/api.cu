@@ -97,7 +97,8 @@ struct gp_factor {
   DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
-  DevBuf Bt, Wt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, counters, L^{-1} y
+  DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
+                                  // sums, counters, L^{-1} y
   DevBuf V, S, cCov;          // covariance workspace
   bool factored = false, alpha_valid = false;
   double ir_eta = 0.0;        // backward error reached by the last refinement
@@ -136,6 +137,7 @@ gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, cons
     if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
     if (kind == 3) v = gpk::cholesky_adjoint_tasks(Mt, T, workers, cm);
+    if (kind == 4) v = gpk::cov_tasks(Mt, Mc, T, workers, cm, false);
     TaskBuf tb;
     GP_TRY(grow(tb.buf, v.size() * sizeof(gpk::Task4)));
     if (!v.empty())
@@ -325,7 +327,7 @@ int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
 
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap) {
-  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 3) return -1;
+  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4) return -1;
   gpk::CostModel cm;
   cm.mixed = mixed != 0;
   std::vector<gpk::Task4> v;
@@ -333,6 +335,7 @@ int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int3
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
   if (graph == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
   if (graph == 3) v = gpk::cholesky_adjoint_tasks(Mt, T, workers, cm);
+  if (graph == 4) v = gpk::cov_tasks(Mt, Mc, T, workers, cm, false);
   if (out) {
     const int64_t k = (int64_t)v.size() < cap ? (int64_t)v.size() : cap;
     std::memcpy(out, v.data(), (size_t)k * sizeof(gpk::Task4));
@@ -368,6 +371,7 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->part);
   release(f->Bt);
   release(f->Wt);
+  release(f->Pt);
   release(f->cRev);
   release(f->beta);
   release(f->bvec);
@@ -531,6 +535,36 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   return GP_OK;
 }
 
+gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, double* var_out) {
+  if (!c || !f || m < 0 || (m > 0 && (!Xs || !var_out)) || !f->factored) return GP_ERR_INVALID_ARG;
+  if (m == 0) return GP_OK;
+  if (m > 8 * 65535LL || f->Mt * (long long)f->T > 8 * 65535LL) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const int T = f->T, Mt = f->Mt;
+  const long long Mc = (m + T - 1) / T;
+  const size_t ldv = (size_t)Mc * T, npad = (size_t)Mt * T;
+  GP_TRY(grow(f->V, npad * ldv * sizeof(double)));
+  const size_t ncnt = (size_t)Mt * Mc;
+  GP_TRY(grow(f->cCov, ncnt * sizeof(int)));
+  GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
+                                     (long long)npad, (long long)ldv, c->stream));
+  count_launch(c);
+  GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
+  const bool mixed = f->precision == GP_FP32;
+  const TaskBuf* tb;
+  GP_TRY(get_tasks(c, 4, Mt, (int)Mc, T, mixed, &tb));
+  gpk::DagArgs a = base_args(c, f);
+  a.V = (double*)f->V.p;
+  a.ldv = (long long)ldv;
+  a.Mc = (int)Mc;
+  a.cV = (int*)f->cCov.p;
+  GP_TRY(run_dag(c, a, tb, mixed));
+  GP_CUDA(gpk::launch_var_from_v((const double*)f->V.p, (long long)ldv, (long long)npad, f->h.v,
+                                 c->cfg.noisy_prior ? f->h.s2 : 0.0, var_out, m, c->stream));
+  count_launch(c);
+  return GP_OK;
+}
+
 gp_status gp_factor_rows(gp_ctx* c, const gp_factor* f, int64_t row0, int64_t nrows, double* out) {
   if (!c || !f || !out || row0 < 0 || nrows < 0 || row0 + nrows > f->n) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
@@ -571,7 +605,9 @@ gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, i
   const size_t ntiles = (size_t)Mt * (Mt + 1) / 2, npad = (size_t)Mt * T, TT = (size_t)T * T;
   GP_TRY(grow(f->Bt, ntiles * TT * sizeof(double)));
   GP_TRY(grow(f->Wt, (size_t)Mt * TT * sizeof(double)));
-  GP_TRY(grow(f->cRev, (ntiles * 2 + Mt) * sizeof(int)));
+  GP_TRY(grow(f->Pt, (size_t)Mt * gpk::kAdjParts * TT * sizeof(double)));
+  const size_t nrev = ntiles * 2 + (size_t)Mt * gpk::kAdjParts;
+  GP_TRY(grow(f->cRev, nrev * sizeof(int)));
   GP_TRY(grow(f->beta, npad * sizeof(double)));
   GP_TRY(grow(f->part, std::max((size_t)6 * Mt * nch, (size_t)3 * ntiles * nch) * sizeof(double)));
   const double* L = (const double*)f->Kt.p;
@@ -585,12 +621,14 @@ gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, i
   GP_CUDA(gpk::launch_init_lbar(L, (double*)f->Bt.p, T, Mt, n, alpha, beta, c->stream));
   count_launch(c, 4);
   // reverse sweep of the tiled Cholesky: Lbar -> Abar (the adjoint of K's stored lower entries)
-  GP_CUDA(cudaMemsetAsync(f->cRev.p, 0, (ntiles * 2 + Mt) * sizeof(int), c->stream));
+  GP_CUDA(cudaMemsetAsync(f->cRev.p, 0, nrev * sizeof(int), c->stream));
+  GP_CUDA(cudaMemsetAsync(f->Pt.p, 0, (size_t)Mt * gpk::kAdjParts * TT * sizeof(double), c->stream));
   const TaskBuf* tb;
   GP_TRY(get_tasks(c, 3, Mt, 0, T, mixed, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.Bt = (double*)f->Bt.p;
   a.Wt = (double*)f->Wt.p;
+  a.Pt = (double*)f->Pt.p;
   a.rc = (int*)f->cRev.p;
   a.fa = a.rc + ntiles;
   a.rd = a.fa + ntiles;

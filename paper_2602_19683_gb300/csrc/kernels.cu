@@ -166,16 +166,23 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
     case TASK_BGEMV:  // (J=p, I=q, ch=r)
       return wait_ge(a.cK + tri(q, p), p + 1, st, to, ti) && wait_ge(a.dB + q, 1, st, to, ti) &&
              wait_ge(a.dF + p, 1, st, to, ti) && wait_ge(a.cB + (size_t)p * a.nch + r, a.Mt - 1 - q, st, to, ti);
-    case TASK_RUPD: {  // (P=p, K=q, J=r)
+    case TASK_RUPD: {  // (P=p, K=q, J=r); terms applied with K descending
       const int hi = p > q ? p : q, lo = p > q ? q : p;
-      return wait_ge(a.fa + tri(hi, lo), 1, st, to, ti) && wait_ge(a.rc + tri(p, r), q - r - 1, st, to, ti);
+      return wait_ge(a.fa + tri(hi, lo), 1, st, to, ti) && wait_ge(a.rc + tri(p, r), a.Mt - 1 - q, st, to, ti);
     }
     case TASK_RTRSM:  // (P=p, J=q)
       return wait_ge(a.rc + tri(p, q), a.Mt - 1 - q, st, to, ti);
-    case TASK_RDIAG:  // (P=p, J=q)
-      return wait_ge(a.fa + tri(p, q), 1, st, to, ti) && wait_ge(a.rd + q, p - q - 1, st, to, ti);
-    case TASK_RPOTRF:  // (J=p)
-      return wait_ge(a.rd + p, a.Mt - 1 - p, st, to, ti);
+    case TASK_RDIAG: {  // (P=p, J=q): k-th contribution of part (p - q - 1) % kAdjParts
+      const int part = (p - q - 1) % kAdjParts, k = (p - q - 1) / kAdjParts;
+      return wait_ge(a.fa + tri(p, q), 1, st, to, ti) && wait_ge(a.rd + (size_t)q * kAdjParts + part, k, st, to, ti);
+    }
+    case TASK_RPOTRF: {  // (J=p): every part complete
+      for (int part = 0; part < kAdjParts; ++part) {
+        const int cnt = (a.Mt - 1 - p - part + kAdjParts - 1) / kAdjParts;
+        if (cnt > 0 && !wait_ge(a.rd + (size_t)p * kAdjParts + part, cnt, st, to, ti)) return false;
+      }
+      return true;
+    }
   }
   return false;
 }
@@ -273,7 +280,10 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     if constexpr (!kRev) {
       switch (tk.x) {
       case TASK_POTRF: {
-        const int fail = cta_potrf(a.Kt + tri(p, p) * TT, T, T, s);
+        const int fail = (kUmma && use_umma && T <= 128)
+                             ? cta_potrf_smem(a.Kt + tri(p, p) * TT, T, T, reinterpret_cast<double*>(um.smem),
+                                              s.tri.inv, &s.flag)
+                             : cta_potrf(a.Kt + tri(p, p) * TT, T, T, s);
         if (fail) {
           if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, gp_tag + (long long)p * T + fail);
           aborted = true;
@@ -369,27 +379,33 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           else
             cta_gemm_sub<A_KM, B_KN>(C, T, a.Bt + tri(q, p) * TT, T, Lkj, T, T, T, T, false, 0, s.g);
         }
-        cta_publish(a.rc + tri(p, r), q - r);
+        cta_publish(a.rc + tri(p, r), a.Mt - q);
         break;
       }
       case TASK_RTRSM:  // Abar_PJ = Lbar_PJ L_JJ^{-1}
         cta_trsm_right_N(a.Kt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, T, T, s);
         cta_publish(a.fa + tri(p, q), 1);
         break;
-      case TASK_RDIAG:  // Lbar_JJ -= tril(Abar_PJ^T L_PJ)
+      case TASK_RDIAG: {  // part_(P-J-1)%parts of Lbar_JJ -= tril(Abar_PJ^T L_PJ)
+        const int part = (p - q - 1) % kAdjParts;
+        double* Cp = a.Pt + ((size_t)q * kAdjParts + part) * TT;
         if (kMixed)
-          cta_gemm_sub_f32<1, 1>(a.Bt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, T,
-                                 true, u.f.g);
+          cta_gemm_sub_f32<1, 1>(Cp, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, T, true, u.f.g);
         else
-          cta_gemm_sub<A_KM, B_KN>(a.Bt + tri(q, q) * TT, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T,
-                                   T, T, true, 0, s.g);
-        cta_publish(a.rd + q, p - q);
+          cta_gemm_sub<A_KM, B_KN>(Cp, T, a.Bt + tri(p, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, T, true, 0, s.g);
+        cta_publish(a.rd + (size_t)q * kAdjParts + part, (p - q - 1) / kAdjParts + 1);
         break;
+      }
       case TASK_RPOTRF: {  // Abar_JJ (+ its transpose) from Lbar_JJ, W = -L^{-T} Phi(L^T Lbar) L^{-1}
         const double* L = a.Kt + tri(p, p) * TT;
         double* B = a.Bt + tri(p, p) * TT;
         double* W = a.Wt + (size_t)p * TT;
-        for (size_t e = threadIdx.x; e < TT; e += kThreads) W[e] = 0.0;
+        for (size_t e = threadIdx.x; e < TT; e += kThreads) {  // Lbar_JJ = initial + sum of the parts
+          double acc = ldcg(B + e);
+          for (int part = 0; part < kAdjParts; ++part) acc += ldcg(a.Pt + ((size_t)p * kAdjParts + part) * TT + e);
+          B[e] = acc;
+          W[e] = 0.0;
+        }
         __syncthreads();
         cta_gemm_sub<A_KM, B_KN>(W, T, L, T, B, T, T, T, T, true, 0, s.g);  // W = -tril(L^T Lbar)
         for (int i = threadIdx.x; i < T; i += kThreads) W[(size_t)i * T + i] *= 0.5;
@@ -782,6 +798,21 @@ __global__ void __launch_bounds__(kThreads) batch_post_kernel(const int4* __rest
   }
 }
 
+// var[j] = k(Xs_j, Xs_j) (+ s2 when noisy) - sum_i V[i][j]^2: the diagonal of Eq. (3) without forming
+// V^T V. One thread per test column, rows in order (deterministic), coalesced across threads.
+__global__ void __launch_bounds__(kThreads) var_from_v_kernel(const double* __restrict__ V, long long ldv,
+                                                              long long nrows, double v, double diag_add,
+                                                              double* __restrict__ var, long long m) {
+  const long long j = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= m) return;
+  double s = 0.0;
+  for (long long i = 0; i < nrows; ++i) {
+    const double x = V[i * ldv + j];
+    s = fma(x, x, s);
+  }
+  var[j] = (v + diag_add) - s;
+}
+
 // ---------------------------------------------------------------- host launchers
 
 cudaError_t launch_assemble_tiles(const double* X, long long n, int D, double l, double v, double s2, double* Kt, int T,
@@ -825,6 +856,13 @@ cudaError_t launch_mean_gemv(const double* Xs, long long m, const double* X, lon
     case 16: mean_gemv_kernel<16><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
     default: mean_gemv_kernel<0><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_from_v(const double* V, long long ldv, long long nrows, double v, double diag_add, double* var,
+                              long long m, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  var_from_v_kernel<<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(V, ldv, nrows, v, diag_add, var, m);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,10 @@ struct GpDesc {
   int D, T, Mt, Mc, nch, pad;
 };
 
+// Partial sums of the reverse sweep's diagonal adjoint: RDIAG(P, J) accumulates into partial
+// (P - J - 1) mod kAdjParts of column J, so the sum over P runs as kAdjParts parallel chains.
+constexpr int kAdjParts = 8;
+
 // Batched task encoding: kind | (gp index << 4) in the first component.
 constexpr int kBatchKindBits = 4;
 
@@ -73,9 +77,10 @@ struct DagArgs {
   int* dB;          // per tile row: backward solve done
   double* Bt;       // adjoint tiles (same packing as Kt)
   double* Wt;       // per-diagonal-tile FP64 workspace of the reverse POTRF (Mt x T x T)
+  double* Pt;       // partial sums of the diagonal adjoints (Mt x kAdjParts x T x T), zeroed per launch
   int* rc;          // per lower tile: reverse updates applied to Lbar_PJ
   int* fa;          // per lower tile: Abar final
-  int* rd;          // per diagonal tile: reverse diagonal updates applied
+  int* rd;          // per (diagonal tile, part): reverse diagonal updates applied
   const GpDesc* descs;  // batched launch: per-GP views (null otherwise)
   const int4* tasks;
   int ntasks;
@@ -93,6 +98,8 @@ cudaError_t launch_assemble_dense(const double* A, long long na, const double* B
                                   long long cols_pad, cudaStream_t st);
 cudaError_t launch_mean_gemv(const double* Xs, long long m, const double* X, long long n, int D, double l, double v,
                              const double* alpha, double* mean, cudaStream_t st);
+cudaError_t launch_var_from_v(const double* V, long long ldv, long long nrows, double v, double diag_add, double* var,
+                              long long m, cudaStream_t st);
 cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long long m, cudaStream_t st);
 cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long row0, long long nrows, double* out,
                                cudaStream_t st);

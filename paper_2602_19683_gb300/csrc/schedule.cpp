@@ -109,7 +109,7 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   return b.ordered(workers);
 }
 
-std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm) {
+std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm, bool with_w) {
   Builder b;
   const double t3 = (double)T * T * T;
   const double spf = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
@@ -123,6 +123,7 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
       for (int c = 0; c < Mc; ++c)
         lastV[(size_t)I * Mc + c] =
             b.add(TASK_VGEMM, I, J, c, c_gemm, {lastV[(size_t)J * Mc + c], lastV[(size_t)I * Mc + c]});
+    if (!with_w) continue;  // variance only: V is all that is needed
     for (int a = 0; a < Mc; ++a)
       for (int bb = 0; bb <= a; ++bb)
         lastS[tri(a, bb)] = b.add(TASK_WSYRK, a, bb, J, c_gemm,
@@ -145,9 +146,12 @@ std::vector<Task4> cholesky_adjoint_tasks(int Mt, int T, int workers, const Cost
   const double c_rpotrf = cm.task_overhead + cm.sec_per_flop * 3.0 * t3 / cm.trsm_eff;
   std::vector<int> last(tri(Mt, 0), -1);   // last writer of Lbar/Abar of each lower tile
   std::vector<int> final_(tri(Mt, 0), -1);  // task that made Abar of the tile final
+  std::vector<int> lastpart(kAdjParts, -1);
   for (int J = Mt - 1; J >= 0; --J) {
+    // Lbar_PJ accumulates its terms with K descending: the K = J+1 term, the last to become
+    // available, is applied last, so the others run ahead.
     for (int P = J + 1; P < Mt; ++P)
-      for (int K = J + 1; K < Mt; ++K) {
+      for (int K = Mt - 1; K > J; --K) {
         const int hi = P > K ? P : K, lo = P > K ? K : P;
         last[tri(P, J)] = b.add(TASK_RUPD, P, K, J, c_rupd, {final_[tri(hi, lo)], last[tri(P, J)]});
       }
@@ -156,9 +160,20 @@ std::vector<Task4> cholesky_adjoint_tasks(int Mt, int T, int workers, const Cost
       last[tri(P, J)] = t;
       final_[tri(P, J)] = t;
     }
-    for (int P = J + 1; P < Mt; ++P)
-      last[tri(J, J)] = b.add(TASK_RDIAG, P, J, 0, c_rdiag, {final_[tri(P, J)], last[tri(J, J)]});
-    const int t = b.add(TASK_RPOTRF, J, 0, 0, c_rpotrf, {last[tri(J, J)]});
+    // the diagonal adjoint's contributions go to kAdjParts partial sums (P - J - 1 mod kAdjParts)
+    for (int q = 0; q < kAdjParts; ++q) lastpart[q] = -1;
+    for (int P = J + 1; P < Mt; ++P) {
+      const int q = (P - J - 1) % kAdjParts;
+      lastpart[q] = b.add(TASK_RDIAG, P, J, 0, c_rdiag, {final_[tri(P, J)], lastpart[q]});
+    }
+    std::vector<int> deps(lastpart.begin(), lastpart.end());
+    b.tasks.push_back({TASK_RPOTRF, J, 0, 0});
+    b.cost.push_back(c_rpotrf);
+    std::vector<int> pr;
+    for (int x : deps)
+      if (x >= 0) pr.push_back(x);
+    b.preds.push_back(pr);
+    const int t = (int)b.tasks.size() - 1;
     last[tri(J, J)] = t;
     final_[tri(J, J)] = t;
   }

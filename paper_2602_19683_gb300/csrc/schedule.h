@@ -23,7 +23,7 @@ struct CostModel {
 // path). The order is a topological order of the dependency DAG.
 std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& cm);
 // Tasks of L V = B (B: Mt x Mc tiles) followed by S -= V^T V on the Mc x Mc lower tiles.
-std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm);
+std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm, bool with_w = true);
 // Tasks of the reverse sweep of the tiled Cholesky (adjoint of Fig. 1), columns J = Mt-1 .. 0.
 std::vector<Task4> cholesky_adjoint_tasks(int Mt, int T, int workers, const CostModel& cm);
 // Tasks of L beta = y then L^T alpha = beta on Mt tiles, vector chunks of 32 rows.

@@ -152,24 +152,39 @@ __device__ __forceinline__ void tri32f_load(Tri32F& s, const double* L, int ldl)
   __syncthreads();
 }
 
-// B[rows x 32] <- B L^{-T} in FP32 (rows of FP64 storage).
-__device__ void cta_trsm_rows32_f32(const Tri32F& s, double* B, int ldb, int rows) {
-  for (int r = threadIdx.x; r < rows; r += kThreads) {
-    float x[32];
-    double* row = B + (size_t)r * ldb;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) x[c] = f64_to_f32_rn(ldcg(row + c));
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      float acc = x[c];
-#pragma unroll
-      for (int k = 0; k < c; ++k) acc = fmaf(-x[k], s.l[c][k], acc);
-      x[c] = acc * s.inv[c];
+// B[rows x 32] <- B L^{-T} in FP32 (rows of FP64 storage). Blocks of 256 rows are staged through
+// smem (the FP32 GEMM buffers, 256 x 33 floats) with coalesced loads and stores: a warp moves two
+// 32-value row segments per instruction, then each thread solves one row from smem.
+__device__ void cta_trsm_rows32_f32(const Tri32F& s, double* B, int ldb, int rows, float (*stage)[33]) {
+  const int t = threadIdx.x, kp = t & 15, rr = t >> 4;
+  for (int r0 = 0; r0 < rows; r0 += kThreads) {
+    const int nr = rows - r0 < kThreads ? rows - r0 : kThreads;
+    for (int r = rr; r < nr; r += kThreads / 16) {
+      const double2 d = __ldcg(reinterpret_cast<const double2*>(B + (size_t)(r0 + r) * ldb) + kp);
+      stage[r][2 * kp] = f64_to_f32_rn(d.x);
+      stage[r][2 * kp + 1] = f64_to_f32_rn(d.y);
     }
+    __syncthreads();
+    if (t < nr) {
+      float x[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) row[c] = f32_to_f64(x[c]);
+      for (int c = 0; c < 32; ++c) x[c] = stage[t][c];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        float acc = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) acc = fmaf(-x[k], s.l[c][k], acc);
+        x[c] = acc * s.inv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) stage[t][c] = x[c];
+    }
+    __syncthreads();
+    for (int r = rr; r < nr; r += kThreads / 16)
+      reinterpret_cast<double2*>(B + (size_t)(r0 + r) * ldb)[kp] =
+          make_double2(f32_to_f64(stage[r][2 * kp]), f32_to_f64(stage[r][2 * kp + 1]));
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // B[32 x ncols] <- L^{-1} B in FP32.
@@ -192,14 +207,15 @@ __device__ void cta_trsm_cols32_f32(const Tri32F& s, double* B, int ldb, int nco
 }
 
 struct TileSmemF32 {
-  GemmSmemF32 g;
+  GemmSmemF32 g;  // also the 256 x 33 float staging area of the row solves
   Tri32F tri;
 };
+static_assert(sizeof(GemmSmemF32) >= 256 * 33 * sizeof(float), "row-solve staging must fit the GEMM buffers");
 
 __device__ void cta_trsm_right_f32(const double* L, int ldl, double* B, int ldb, int rows, int nb, TileSmemF32& s) {
   for (int k0 = 0; k0 < nb; k0 += 32) {
     tri32f_load(s.tri, L + (size_t)k0 * ldl + k0, ldl);
-    cta_trsm_rows32_f32(s.tri, B + k0, ldb, rows);
+    cta_trsm_rows32_f32(s.tri, B + k0, ldb, rows, reinterpret_cast<float(*)[33]>(&s.g));
     const int rest = nb - k0 - 32;
     if (rest > 0)
       cta_gemm_sub_f32<0, 0>(B + k0 + 32, ldb, B + k0, ldb, L + (size_t)(k0 + 32) * ldl + k0, ldl, rows, rest, 32,

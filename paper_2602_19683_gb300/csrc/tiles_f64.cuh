@@ -279,6 +279,86 @@ __device__ int cta_potrf(double* A, int lda, int nb, TileSmem& s) {
   return 0;
 }
 
+// POTRF of an nb x nb diagonal tile (nb <= 128, a multiple of 32) held entirely in shared memory
+// (sm: nb x (nb + 1) doubles, inv: 32 doubles): coalesced load, 32-wide right-looking strips (warp 0
+// factors the strip's diagonal block, one thread per row solves the rows below it, all threads update
+// the trailing lower triangle), coalesced store with the upper triangle zeroed. Same arithmetic as
+// cta_potrf, without the global-memory round trips that make the critical path latency-bound.
+// Returns 0 or the 1-based failing column.
+__device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* inv, int* flag) {
+  const int ld = nb + 1, t = threadIdx.x;
+  for (int e = t; e < nb * nb; e += kThreads) {
+    const int i = e / nb, j = e % nb;
+    sm[i * ld + j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
+  }
+  if (t == 0) *flag = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    if (t < 32) {  // diagonal block, lane i = row k0 + i
+      const int i = t;
+      double* rowi = sm + (size_t)(k0 + i) * ld + k0;
+      int fail = 0;
+      for (int j = 0; j < 32; ++j) {
+        const double d = sm[(size_t)(k0 + j) * ld + k0 + j];
+        if (!(d > 0.0)) {
+          fail = j + 1;
+          break;
+        }
+        const double ljj = sqrt(d), ij = 1.0 / ljj;
+        __syncwarp();
+        if (i == j) {
+          rowi[j] = ljj;
+          inv[j] = ij;
+        }
+        if (i > j) rowi[j] *= ij;
+        __syncwarp();
+        if (i > j) {
+          const double lij = rowi[j];
+          for (int k = j + 1; k <= i; ++k) rowi[k] = fma(-lij, sm[(size_t)(k0 + k) * ld + k0 + j], rowi[k]);
+        }
+        __syncwarp();
+      }
+      if (i == 0) *flag = fail;
+    }
+    __syncthreads();
+    if (*flag) return k0 + *flag;
+    for (int r = k0 + 32 + t; r < nb; r += kThreads) {  // rows below: x L_kk^T = row
+      double* row = sm + (size_t)r * ld + k0;
+      double x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = row[c];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        double acc = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) acc = fma(-x[k], sm[(size_t)(k0 + c) * ld + k0 + k], acc);
+        x[c] = acc * inv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) row[c] = x[c];
+    }
+    __syncthreads();
+    const int m = nb - k0 - 32;  // trailing lower triangle, entries (i, j), j <= i
+    for (int e = t; e < m * m; e += kThreads) {
+      const int i = e / m, j = e % m;
+      if (j > i) continue;
+      const double* ri = sm + (size_t)(k0 + 32 + i) * ld + k0;
+      const double* rj = sm + (size_t)(k0 + 32 + j) * ld + k0;
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc = fma(ri[c], rj[c], acc);
+      sm[(size_t)(k0 + 32 + i) * ld + k0 + 32 + j] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < nb * nb; e += kThreads) {
+    const int i = e / nb, j = e % nb;
+    A[(size_t)i * lda + j] = (j <= i) ? sm[(size_t)i * ld + j] : 0.0;
+  }
+  __syncthreads();
+  return 0;
+}
+
 // TRSM from the right: B[rows x nb] <- B L^{-T}, L the nb x nb lower factor (Sec. 3.2 TRSM,
 // L_IJ = K_IJ L_JJ^{-T}). Right-looking over 32-wide column strips.
 __device__ void cta_trsm_right(const double* L, int ldl, double* B, int ldb, int rows, int nb, TileSmem& s) {

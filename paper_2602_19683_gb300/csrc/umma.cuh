@@ -21,7 +21,11 @@ namespace gpk {
 constexpr int kUmmaM = 128, kUmmaN = 128, kUmmaKChunk = 32;
 constexpr int kUmmaTileBytes = kUmmaM * 128;           // 128 rows x 32 tf32
 constexpr int kUmmaStageBytes = 4 * kUmmaTileBytes;    // A_hi, A_lo, B_hi, B_lo
-constexpr int kUmmaSmemBytes = 2 * kUmmaStageBytes + 1024;  // two stages + alignment slack
+// Dynamic shared memory of the mixed kernel: the two operand stages, also the home of a 128 x 129 FP64
+// diagonal tile during a shared-memory POTRF; plus alignment slack.
+constexpr int kMixedTileSmemBytes = 128 * 129 * 8;
+constexpr int kUmmaSmemBytes =
+    (2 * kUmmaStageBytes > kMixedTileSmemBytes ? 2 * kUmmaStageBytes : kMixedTileSmemBytes) + 2048;
 constexpr int kUmmaTmemCols = 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -137,31 +141,27 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7))) << 4) + (k & 3) * 4);
 }
 
-// Loads rows [r0, r0+128) x k [k0, k0+32) of the FP64 row-major operand P (ld), splits into TF32
-// hi / FP32 lo and stores both swizzled. 16 elements per thread.
+// TF32 rounding (to nearest) of an FP32 value, on the integer pipe.
+__device__ __forceinline__ float tf32_rn(float f) { return __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u); }
+
+// Loads rows [r0, r0+128) x k [k0, k0+32) of the FP64 row-major operand P (ld), splits each value into
+// a TF32 high part and a TF32-rounded remainder and stores both swizzled. Coalesced: 16 lanes cover a
+// row's 32 values (256 B) with one double2 each, so a warp reads two whole row segments per pass.
 __device__ __forceinline__ void umma_stage_operand(uint8_t* hi_tile, uint8_t* lo_tile, const double* P, int ld, int r0,
                                                    int k0) {
   const int t = threadIdx.x;
-  const int r = t >> 1, kh = (t & 1) * 16;
-  const double2* src = reinterpret_cast<const double2*>(P + (size_t)(r0 + r) * ld + k0 + kh);
-  float hv[16], lv[16];
+  const int kp = t & 15, rr = t >> 4;  // k pair 2kp, 2kp+1; row rr + 16 pass
+  double2 d[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double2 d = __ldcg(src + q);
-    const float f0 = f64_to_f32_rn(d.x), f1 = f64_to_f32_rn(d.y);
-    const float h0 = __uint_as_float((__float_as_uint(f0) + 0x1000u) & 0xFFFFE000u);
-    const float h1 = __uint_as_float((__float_as_uint(f1) + 0x1000u) & 0xFFFFE000u);
-    hv[2 * q] = h0;
-    hv[2 * q + 1] = h1;
-    // the remainder is exact in FP32; round it to TF32 too (the tensor core would truncate it)
-    lv[2 * q] = __uint_as_float((__float_as_uint(f0 - h0) + 0x1000u) & 0xFFFFE000u);
-    lv[2 * q + 1] = __uint_as_float((__float_as_uint(f1 - h1) + 0x1000u) & 0xFFFFE000u);
-  }
+  for (int pass = 0; pass < 8; ++pass)
+    d[pass] = __ldcg(reinterpret_cast<const double2*>(P + (size_t)(r0 + rr + 16 * pass) * ld + k0) + kp);
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const uint32_t off = sw128_offset(r, kh + 4 * c);
-    *reinterpret_cast<float4*>(hi_tile + off) = make_float4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
-    *reinterpret_cast<float4*>(lo_tile + off) = make_float4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
+  for (int pass = 0; pass < 8; ++pass) {
+    const float f0 = f64_to_f32_rn(d[pass].x), f1 = f64_to_f32_rn(d[pass].y);
+    const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
+    const uint32_t off = sw128_offset(rr + 16 * pass, 2 * kp);
+    *reinterpret_cast<float2*>(hi_tile + off) = make_float2(h0, h1);
+    *reinterpret_cast<float2*>(lo_tile + off) = make_float2(tf32_rn(f0 - h0), tf32_rn(f1 - h1));
   }
 }
 
@@ -202,23 +202,46 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const double* A
     if (u.pending[s]) {
       if (!umma_stage_wait(u, s, st, timeout_ns, where)) return false;
     }
+  // epilogue: TMEM -> registers (warp w: lanes 32(w%4).., a 64-column half) -> smem (row-major, the
+  // operand stages are free now) -> coalesced FP64 read-modify-write of C (a warp per row, 4 columns
+  // per lane).
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (w & 3) * 32 + lane, colh = (w >> 2) * 64;
-  const int m = m0 + row;
+  float* acc_s = reinterpret_cast<float*>(u.smem);  // 128 x (128 + 4) floats
+  constexpr int ldacc = kUmmaN + 4;
+  {
+    const int row = (w & 3) * 32 + lane, colh = (w >> 2) * 64;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    float v[32];
-    tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(colh + 32 * half), v);
-    double* crow = C + (size_t)m * ldc + n0 + colh + 32 * half;
+    for (int half = 0; half < 2; ++half) {
+      float v[32];
+      tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(colh + 32 * half), v);
+      float* dst = acc_s + row * ldacc + colh + 32 * half;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int n = n0 + colh + 32 * half + j;
-      if (!lower || n <= m) crow[j] = ldcg(crow + j) - f32_to_f64(v[j]);
+      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
     }
   }
   umma_fence_before();
-  __syncthreads();  // TMEM may be overwritten by the next block's MMAs
+  __syncthreads();
+  for (int r = w; r < kUmmaM; r += kThreads / 32) {
+    const int m = m0 + r, n = n0 + 4 * lane;
+    const float4 a = *reinterpret_cast<const float4*>(acc_s + r * ldacc + 4 * lane);
+    double2* c2 = reinterpret_cast<double2*>(C + (size_t)m * ldc + n);
+    double2 c01 = __ldcg(c2), c23 = __ldcg(c2 + 1);
+    if (!lower || n + 3 <= m) {
+      c01.x -= f32_to_f64(a.x);
+      c01.y -= f32_to_f64(a.y);
+      c23.x -= f32_to_f64(a.z);
+      c23.y -= f32_to_f64(a.w);
+    } else {
+      if (n <= m) c01.x -= f32_to_f64(a.x);
+      if (n + 1 <= m) c01.y -= f32_to_f64(a.y);
+      if (n + 2 <= m) c23.x -= f32_to_f64(a.z);
+      if (n + 3 <= m) c23.y -= f32_to_f64(a.w);
+    }
+    c2[0] = c01;
+    c2[1] = c23;
+  }
+  __syncthreads();  // smem and TMEM are reused by the next block
   return true;
 }
 

@@ -123,25 +123,29 @@ def test_mean_schedule_is_topological(lib, Mt, T, workers):
 @pytest.mark.parametrize("Mt,workers,mixed", [(1, 2, 0), (2, 1, 0), (5, 7, 1), (9, 304, 0)])
 def test_adjoint_schedule_is_topological(lib, Mt, workers, mixed):
     """The reverse sweep (adjoint of Fig. 1): for each J from the last column down, RUPD(P, K, J) for
-    all P, K > J with K ascending per P, after the adjoint of tile (max(P,K), min(P,K)) is final;
-    RTRSM(P, J) after all of them; RDIAG(P, J) in P order; RPOTRF(J) last. Mirrors the device's
-    counter waits."""
+    all P, K > J with K descending per P, after the adjoint of tile (max(P,K), min(P,K)) is final;
+    RTRSM(P, J) after all of them; RDIAG(P, J) in P order within each of 8 partial sums; RPOTRF(J)
+    after every part. Mirrors the device's counter waits."""
     t = tasks(lib, 3, Mt, 0, 64, workers, mixed)
     assert len(t) == sum((Mt - 1 - J) ** 2 + 2 * (Mt - 1 - J) + 1 for J in range(Mt))
+    parts = 8
     rc, fa, rd = {}, set(), {}
     for kind, p, q, r in t:
-        if kind == 10:
+        if kind == 10:  # K descending per (P, J)
             hi, lo = max(p, q), min(p, q)
-            assert p > r and q > r and (hi, lo) in fa and rc.get((p, r), 0) == q - r - 1
-            rc[(p, r)] = q - r
+            assert p > r and q > r and (hi, lo) in fa and rc.get((p, r), 0) == Mt - 1 - q
+            rc[(p, r)] = Mt - q
         elif kind == 11:
             assert rc.get((p, q), 0) == Mt - 1 - q
             fa.add((p, q))
         elif kind == 12:
-            assert (p, q) in fa and rd.get(q, 0) == p - q - 1
-            rd[q] = p - q
+            part, k = (p - q - 1) % parts, (p - q - 1) // parts
+            assert (p, q) in fa and rd.get((q, part), 0) == k
+            rd[(q, part)] = k + 1
         elif kind == 13:
-            assert rd.get(p, 0) == Mt - 1 - p
+            for part in range(parts):
+                cnt = max(0, -(-(Mt - 1 - p - part) // parts))
+                assert rd.get((p, part), 0) == cnt
             fa.add((p, p))
         else:
             raise AssertionError(kind)
@@ -150,5 +154,5 @@ def test_adjoint_schedule_is_topological(lib, Mt, workers, mixed):
 
 def test_schedule_rejects_bad_arguments(lib):
     assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
-    assert lib.gp_schedule_tasks(4, 4, 0, 64, 1, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(5, 4, 0, 64, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1

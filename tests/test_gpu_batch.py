@@ -51,8 +51,8 @@ def test_batch_matches_single_gp_and_oracle(api, precision):
             ec = rel(batch.covs[g].cpu().numpy(), ref["cov"])
             if precision == "fp64":
                 assert em <= 1e-10 and ec <= 1e-9, (g, em, ec)
-            else:  # FP32 trailing updates, no refinement: FP32-class results
-                assert em <= 1e-3 and ec <= 1e-4, (g, em, ec)
+            else:  # FP32-class trailing updates (tensor cores for 128-wide tiles), no refinement
+                assert em <= 1e-3 and ec <= 2e-4, (g, em, ec)
     batch.free()
 
 

@@ -3,10 +3,15 @@
 In this mode the trailing SYRK/GEMM updates, the panel TRSMs after the first block column and the
 covariance solve run in FP32 with FP32 accumulation; the diagonal POTRFs, the first block column's
 TRSMs and the residual of the mean solve stay FP64, and classic iterative refinement recovers the
-FP64 solution of K alpha = y. Stated bounds (max-abs error relative to the oracle's max-abs value):
-  mean (refined)        <= 1e-10   (the FP64 bar)
-  covariance            <= 2e-5    (FP32-class factor and V; Q8 reading)
-  log-determinant       <= 1e-5 relative
+FP64 solution of K alpha = y. Stated bounds (max-abs error relative to the oracle's max-abs value),
+per form of the trailing update:
+                         FP32 FMA     tensor cores (tcgen05, 3xTF32)
+  mean (refined)         <= 1e-10     <= 1e-10   (the FP64 bar)
+  factor ||LL^T-K||/||K|| <= 1e-5     <= 2e-5
+  covariance             <= 2e-5      <= 1e-4
+  log-determinant        <= 1e-5      <= 1e-5 relative
+The tensor-core form is looser because the tensor cores' FP32 accumulation does not round to
+nearest, so its error grows with the 256-long accumulation chains.
 """
 import numpy as np
 import pytest
@@ -39,12 +44,16 @@ def to_dev(*arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).to("cuda") for a in arrs]
 
 
+BOUNDS = {False: {"factor": 1e-5, "cov": 2e-5, "logdet": 1e-5}, True: {"factor": 2e-5, "cov": 1e-4, "logdet": 1e-5}}
+
+
+@pytest.mark.parametrize("tc", [False, True])
 @pytest.mark.parametrize("n,m,D,T,seed", [(1024, 1024, 8, 256, 0), (1500, 300, 8, 128, 1), (700, 70, 4, 64, 2),
                                           (4096, 512, 8, 256, 3)])
-def test_mixed_matches_oracle_within_stated_bounds(api, n, m, D, T, seed):
+def test_mixed_matches_oracle_within_stated_bounds(api, n, m, D, T, seed, tc):
     X, y, Xs, _ = nfir.make_dataset(n, m, D, seed)
     ref = oracle.gp_predict(X, y, Xs, H0)
-    ctx = api.Context(0, tile=T, precision="fp32")
+    ctx = api.Context(0, tile=T, precision="fp32", tensor_cores=tc)
     Xd, yd, Xsd = to_dev(X, y, Xs)
     f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
     api.gp_cholesky(ctx, f)
@@ -57,12 +66,13 @@ def test_mixed_matches_oracle_within_stated_bounds(api, n, m, D, T, seed):
     em = rel(mean.cpu().numpy(), ref["mean"])
     ec = rel(cov.cpu().numpy(), ref["cov"])
     el = abs(logdet - ref["logdet"]) / abs(ref["logdet"])
-    print(f"n={n}: factor {fac_err:.2e} mean {em:.2e} ({iters} IR iterations) cov {ec:.2e} logdet {el:.2e}")
+    print(f"n={n} tc={tc}: factor {fac_err:.2e} mean {em:.2e} ({iters} IR iterations) cov {ec:.2e} logdet {el:.2e}")
+    b = BOUNDS[tc and T % 128 == 0]
     assert 1 <= iters <= 10
-    assert fac_err <= 1e-5
+    assert fac_err <= b["factor"]
     assert em <= 1e-10
-    assert ec <= 2e-5
-    assert el <= 1e-5
+    assert ec <= b["cov"]
+    assert el <= b["logdet"]
 
 
 def test_mixed_first_column_is_fp64(api):

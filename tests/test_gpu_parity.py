@@ -77,6 +77,20 @@ def test_fp64_pipeline_matches_oracle(api, n, m, D, T, h, seed):
     f.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_variance_only_matches_covariance_diagonal(api, precision):
+    """gp_predict_var = diag of Eq. (3) (oracle), without forming V^T V."""
+    X, y, Xs, _ = nfir.make_dataset(900, 150, 8, 13)
+    ref = oracle.gp_predict(X, y, Xs, H0)
+    ctx = api.Context(0, tile=128, precision=precision)
+    Xd, Xsd = to_dev(X, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    var = api.gp_predict_var(ctx, f, Xsd).cpu().numpy()
+    api.gp_sync(ctx)
+    assert rel(var, np.diag(ref["cov"])) <= (1e-9 if precision == "fp64" else 1e-4)
+
+
 def test_noisy_prior_adds_s2(api):
     X, y, Xs, _ = nfir.make_dataset(200, 50, 8, 7)
     ref = oracle.gp_predict(X, y, Xs, H0, noisy_prior=True)
