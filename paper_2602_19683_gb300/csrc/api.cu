@@ -115,8 +115,10 @@ int auto_tile(long long n) {
   return 32;
 }
 
-gpk::CostModel cost_model(const gp_ctx* c, bool mixed) {
+gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
   gpk::CostModel cm;
+  // Mixed tensor-core updates are bound by their FP64 C read-modify-write: group 4 columns per task.
+  cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 4 : 1;
   // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
   cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
   cm.sec_per_flop32 = 1.0 / 3.0e11;
@@ -132,7 +134,7 @@ gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, cons
   auto it = c->tasks.find(key);
   if (it == c->tasks.end()) {
     std::vector<gpk::Task4> v;
-    const gpk::CostModel cm = cost_model(c, mixed);
+    const gpk::CostModel cm = cost_model(c, mixed, T);
     if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
     if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
@@ -330,6 +332,7 @@ int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int3
   if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4) return -1;
   gpk::CostModel cm;
   cm.mixed = mixed != 0;
+  cm.update_group = (mixed && T % 128 == 0) ? 4 : 1;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);

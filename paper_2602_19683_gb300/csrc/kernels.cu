@@ -135,9 +135,12 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
       return wait_ge(a.cK + tri(p, p), p, st, to, ti);
     case TASK_TRSM:  // (I=p, J=q)
       return wait_ge(a.cK + tri(q, q), q + 1, st, to, ti) && wait_ge(a.cK + tri(p, q), q, st, to, ti);
-    case TASK_UPD:  // (I=p, K=q, J=r)
-      return wait_ge(a.cK + tri(p, r), r + 1, st, to, ti) && wait_ge(a.cK + tri(q, r), r + 1, st, to, ti) &&
-             wait_ge(a.cK + tri(p, q), r, st, to, ti);
+    case TASK_UPD: {  // (I=p, K=q, J in [J0, J1)) with r = J0 | J1 << 16 (J1 = 0: the single column J0)
+      const int J0 = r & 0xFFFF, J1 = (r >> 16) ? (r >> 16) : J0 + 1;
+      for (int J = J0; J < J1; ++J)
+        if (!wait_ge(a.cK + tri(p, J), J + 1, st, to, ti) || !wait_ge(a.cK + tri(q, J), J + 1, st, to, ti)) return false;
+      return wait_ge(a.cK + tri(p, q), J0, st, to, ti);
+    }
     // The solve tasks also wait for the factor tiles they read to be final (immediately true when the
     // factorisation ran in an earlier launch; needed when one launch runs a GP's whole pipeline).
     case TASK_VTRSM:  // (J=p, c=q)
@@ -282,8 +285,8 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       case TASK_POTRF: {
         const int fail = (kUmma && use_umma && T <= 128)
                              ? cta_potrf_smem(a.Kt + tri(p, p) * TT, T, T, reinterpret_cast<double*>(um.smem),
-                                              s.tri.inv, &s.flag)
-                             : cta_potrf(a.Kt + tri(p, p) * TT, T, T, s);
+                                              &s_red[0][0], &s.flag)
+                             : cta_potrf<kMixed>(a.Kt + tri(p, p) * TT, T, T, s);
         if (fail) {
           if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, gp_tag + (long long)p * T + fail);
           aborted = true;
@@ -299,21 +302,32 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
-      case TASK_UPD:
-        if (kUmma && use_umma && T % kUmmaM == 0) {
-          if (!umma_gemm_sub(um, a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T, T,
-                             p == q, a.st, a.timeout_ns, ti)) {
+      case TASK_UPD: {  // K_IK -= sum_{J0 <= J < J1} L_IJ L_KJ^T (SYRK when I == K), J in increasing order
+        const int J0 = r & 0xFFFF, J1 = (r >> 16) ? (r >> 16) : J0 + 1;
+        double* C = a.Kt + tri(p, q) * TT;
+        if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
+          UmmaPairs pr;
+          pr.n = J1 - J0;
+          for (int J = J0; J < J1; ++J) {
+            pr.A[J - J0] = a.Kt + tri(p, J) * TT;
+            pr.B[J - J0] = a.Kt + tri(q, J) * TT;
+          }
+          if (!umma_gemm_sub(um, C, T, pr, T, T, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
-        } else if (kMixed)
-          cta_gemm_sub_f32<0, 0>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T, T,
-                                 T, p == q, u.f.g);
-        else
-          cta_gemm_sub<A_MK, B_NK>(a.Kt + tri(p, q) * TT, T, a.Kt + tri(p, r) * TT, T, a.Kt + tri(q, r) * TT, T, T,
-                                   T, T, p == q, 0, s.g);
-        cta_publish(a.cK + tri(p, q), r + 1);
+        } else {
+          for (int J = J0; J < J1; ++J) {
+            if (kMixed)
+              cta_gemm_sub_f32<0, 0>(C, T, a.Kt + tri(p, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, p == q, u.f.g);
+            else
+              cta_gemm_sub<A_MK, B_NK>(C, T, a.Kt + tri(p, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, p == q, 0,
+                                       s.g);
+          }
+        }
+        cta_publish(a.cK + tri(p, q), J1);
         break;
+      }
       case TASK_VTRSM: {
         double* B = a.V + (size_t)p * T * a.ldv + (size_t)q * T;
         if (kMixed)

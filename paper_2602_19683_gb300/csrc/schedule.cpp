@@ -65,6 +65,9 @@ struct Builder {
   std::vector<double> cost;
   std::vector<std::vector<int>> preds;
   int add(int kind, int p, int q, int r, double c, std::initializer_list<int> deps) {
+    return add_v(kind, p, q, r, c, std::vector<int>(deps));
+  }
+  int add_v(int kind, int p, int q, int r, double c, const std::vector<int>& deps) {
     tasks.push_back({kind, p, q, r});
     cost.push_back(c);
     std::vector<int> d;
@@ -95,16 +98,39 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   const double c_trsm = cm.task_overhead + spf_upd * t3 / cm.trsm_eff;
   const double c_gemm = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
   const double c_syrk = cm.task_overhead + spf_upd * (t3 + 64.0 * T * T) / cm.gemm_eff;
+  // Updates of a tile whose critical use is still far away are grouped: columns [J0, J1) in one task
+  // (one pass over the tile's C instead of J1 - J0); the last kTail columns before the tile is needed
+  // stay single so the critical path is not lengthened.
+  const int g = cm.update_group > 1 ? cm.update_group : 1;
+  const int kTail = 2;
   std::vector<int> last(tri(Mt, 0), -1);  // last task that wrote each lower tile
+  std::vector<int> gstart(tri(Mt, 0), 0);  // first column of the open update group of each tile
+  std::vector<int> trsm_of(tri(Mt, 0), -1);
   for (int J = 0; J < Mt; ++J) {
     const int po = b.add(TASK_POTRF, J, 0, 0, c_potrf, {last[tri(J, J)]});
     last[tri(J, J)] = po;
-    for (int I = J + 1; I < Mt; ++I)
+    for (int I = J + 1; I < Mt; ++I) {
       last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, J == 0 ? c_trsm0 : c_trsm, {po, last[tri(I, J)]});
+      trsm_of[tri(I, J)] = last[tri(I, J)];
+    }
     for (int I = J + 1; I < Mt; ++I)
-      for (int K = J + 1; K <= I; ++K)
-        last[tri(I, K)] =
-            b.add(TASK_UPD, I, K, J, I == K ? c_syrk : c_gemm, {last[tri(I, J)], last[tri(K, J)], last[tri(I, K)]});
+      for (int K = J + 1; K <= I; ++K) {
+        const size_t t = tri(I, K);
+        const int lim = K - kTail;  // columns >= lim are applied one by one
+        int J0 = J;
+        if (g > 1 && J < lim) {
+          if ((J + 1) % g != 0 && J + 1 != lim) continue;  // the group stays open
+          J0 = gstart[t];
+        }
+        std::vector<int> deps{last[t]};
+        for (int Jj = J0; Jj <= J; ++Jj) {
+          deps.push_back(trsm_of[tri(I, Jj)]);
+          deps.push_back(trsm_of[tri(K, Jj)]);
+        }
+        const int r = J0 | ((J + 1) << 16);
+        last[t] = b.add_v(TASK_UPD, I, K, r, (J + 1 - J0) * (I == K ? c_syrk : c_gemm), deps);
+        gstart[t] = J + 1;
+      }
   }
   return b.ordered(workers);
 }

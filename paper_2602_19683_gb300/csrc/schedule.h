@@ -14,6 +14,7 @@ struct CostModel {
   double sec_per_flop = 1.0 / 3.9e9;     // FP64 work: one CTA on a shared SM, FP64 FFMA
   double sec_per_flop32 = 1.0 / 3.0e11;  // FP32 work (mixed mode): one CTA per SM
   bool mixed = false;                    // trailing updates / later panel TRSMs / V solve in FP32
+  int update_group = 1;                  // trailing updates per task for tiles off the critical path
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
 };

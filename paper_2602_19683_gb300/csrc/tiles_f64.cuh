@@ -160,42 +160,114 @@ __device__ __forceinline__ void tri32_load(Tri32& s, const double* L, int ldl) {
   __syncthreads();
 }
 
+// CTA-parallel right-looking Cholesky of a 32 x 32 block B (smem, leading dimension ld): step j, thread
+// 0 takes the pivot, 31 threads scale column j, and all 8 warps share the rank-1 update of the trailing
+// triangle (thread t: row j+1+t/8, columns j+1+(t%8), +8, ...), so every SM sub-partition's FP64 unit
+// works (a single warp would reach only a quarter of the SM's FP64 rate). inv receives 1/L_jj.
+// Returns 0 or the 1-based failing column (same in every thread).
+__device__ int cta_potrf32_par(double* B, int ld, double* inv, int* flag) {
+  const int t = threadIdx.x;
+  for (int j = 0; j < 32; ++j) {
+    if (t == 0) {
+      const double d = B[j * ld + j];
+      if (!(d > 0.0)) {
+        *flag = j + 1;
+      } else {
+        const double ljj = sqrt(d);
+        B[j * ld + j] = ljj;
+        inv[j] = 1.0 / ljj;
+      }
+    }
+    __syncthreads();
+    if (*flag) return *flag;
+    if (t > j && t < 32) B[t * ld + j] *= inv[j];
+    __syncthreads();
+    const int i = j + 1 + (t >> 3);
+    if (i < 32) {
+      const double lij = B[i * ld + j];
+      for (int k = j + 1 + (t & 7); k <= i; k += 8) B[i * ld + k] = fma(-lij, B[k * ld + j], B[i * ld + k]);
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// Warp-level right-looking Cholesky of a 32 x 32 block whose row `lane` is held in registers r[0..32)
+// (lower part significant). col[32] is a smem column buffer; inv receives the reciprocal diagonal.
+// Statically indexed inner loops keep everything in registers. Returns 0 or the 1-based failing
+// column (same in every lane).
+__device__ __forceinline__ int warp_potrf32_regs(double (&r)[32], double* col, double* inv) {
+  const int i = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const double d = __shfl_sync(0xffffffffu, r[j], j);
+    if (!(d > 0.0)) return j + 1;  // uniform: every lane saw the same pivot (also catches NaN)
+    const double ljj = sqrt(d), ij = 1.0 / ljj;
+    if (i == j) {
+      r[j] = ljj;
+      inv[j] = ij;
+    }
+    if (i > j) r[j] *= ij;
+    col[i] = r[j];  // column j of L (rows > j significant)
+    __syncwarp();
+#pragma unroll
+    for (int k = j + 1; k < 32; ++k)
+      if (k <= i) r[k] = fma(-r[j], col[k], r[k]);
+    __syncwarp();
+  }
+  return 0;
+}
+
 // Unblocked Cholesky of the 32 x 32 diagonal block at A (in place, lower; upper zeroed), by warp 0
 // with lane i owning row i: right-looking column by column. Leaves the factor in s. Returns 0 or
 // the 1-based failing column (same value in every thread).
+// kRegs: rows in registers (warp_potrf32_regs; for kernels with registers to spare); otherwise the
+// rows stay in smem and lane i updates row i element by element (fits the 128-register FP64 kernel).
+template <bool kRegs>
 __device__ int cta_potrf32(double* A, int lda, Tri32& s, int* shared_flag) {
   const int t = threadIdx.x;
-  for (int e = t; e < 32 * 32; e += kThreads) {
-    const int i = e / 32, j = e % 32;
-    s.l[i][j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
-  }
+  __shared__ double col[32];
   if (t == 0) *shared_flag = 0;
-  __syncthreads();
-  if (t < 32) {
-    const int i = t;
-    int fail = 0;
-    for (int j = 0; j < 32; ++j) {
-      const double d = s.l[j][j];
-      if (!(d > 0.0)) {  // also catches NaN
-        fail = j + 1;
-        break;
-      }
-      const double ljj = sqrt(d);
-      const double inv = 1.0 / ljj;
-      __syncwarp();
-      if (i == j) {
-        s.l[j][j] = ljj;
-        s.inv[j] = inv;
-      }
-      if (i > j) s.l[i][j] *= inv;
-      __syncwarp();
-      if (i > j) {
-        const double lij = s.l[i][j];
-        for (int k = j + 1; k <= i; ++k) s.l[i][k] = fma(-lij, s.l[k][j], s.l[i][k]);
-      }
-      __syncwarp();
+  if constexpr (kRegs) {
+    (void)col;
+    for (int e = t; e < 32 * 32; e += kThreads) {
+      const int i = e / 32, j = e % 32;
+      s.l[i][j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
     }
-    if (i == 0) *shared_flag = fail;
+    __syncthreads();
+    cta_potrf32_par(&s.l[0][0], 33, s.inv, shared_flag);
+  } else {
+    for (int e = t; e < 32 * 32; e += kThreads) {
+      const int i = e / 32, j = e % 32;
+      s.l[i][j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
+    }
+    __syncthreads();
+    if (t < 32) {
+      const int i = t;
+      int fail = 0;
+      for (int j = 0; j < 32; ++j) {
+        const double d = s.l[j][j];
+        if (!(d > 0.0)) {
+          fail = j + 1;
+          break;
+        }
+        const double ljj = sqrt(d);
+        const double inv = 1.0 / ljj;
+        __syncwarp();
+        if (i == j) {
+          s.l[j][j] = ljj;
+          s.inv[j] = inv;
+        }
+        if (i > j) s.l[i][j] *= inv;
+        __syncwarp();
+        if (i > j) {
+          const double lij = s.l[i][j];
+          for (int k = j + 1; k <= i; ++k) s.l[i][k] = fma(-lij, s.l[k][j], s.l[i][k]);
+        }
+        __syncwarp();
+      }
+      if (i == 0) *shared_flag = fail;
+    }
   }
   __syncthreads();
   const int fail = *shared_flag;
@@ -218,11 +290,17 @@ __device__ void cta_trsm_rows32(const Tri32& s, double* B, int ldb, int rows) {
 #pragma unroll
     for (int c = 0; c < 32; ++c) x[c] = ldcg(row + c);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      double acc = x[c];
+    for (int c = 0; c < 32; ++c) {  // four independent chains: the FP64 FMA latency is long
+      double a0 = x[c], a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll
-      for (int k = 0; k < c; ++k) acc = fma(-x[k], s.l[c][k], acc);
-      x[c] = acc * s.inv[c];
+      for (int k = 0; k < c; ++k) {
+        const double v = -x[k];
+        if ((k & 3) == 0) a0 = fma(v, s.l[c][k], a0);
+        if ((k & 3) == 1) a1 = fma(v, s.l[c][k], a1);
+        if ((k & 3) == 2) a2 = fma(v, s.l[c][k], a2);
+        if ((k & 3) == 3) a3 = fma(v, s.l[c][k], a3);
+      }
+      x[c] = ((a0 + a1) + (a2 + a3)) * s.inv[c];
     }
 #pragma unroll
     for (int c = 0; c < 32; ++c) row[c] = x[c];
@@ -258,9 +336,10 @@ struct TileSmem {
 // POTRF of the nb x nb diagonal tile A (nb a multiple of 32), blocked right-looking with 32-wide
 // strips: factor the strip's diagonal block, TRSM the rows below it, SYRK-update the trailing
 // lower triangle. Upper triangle zeroed. Returns 0 or the 1-based failing column within the tile.
+template <bool kRegs>
 __device__ int cta_potrf(double* A, int lda, int nb, TileSmem& s) {
   for (int k0 = 0; k0 < nb; k0 += 32) {
-    const int fail = cta_potrf32(A + (size_t)k0 * lda + k0, lda, s.tri, &s.flag);
+    const int fail = cta_potrf32<kRegs>(A + (size_t)k0 * lda + k0, lda, s.tri, &s.flag);
     if (fail) return k0 + fail;
     const int rest = nb - k0 - 32;
     if (rest > 0) {
@@ -294,34 +373,10 @@ __device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* in
   if (t == 0) *flag = 0;
   __syncthreads();
   for (int k0 = 0; k0 < nb; k0 += 32) {
-    if (t < 32) {  // diagonal block, lane i = row k0 + i
-      const int i = t;
-      double* rowi = sm + (size_t)(k0 + i) * ld + k0;
-      int fail = 0;
-      for (int j = 0; j < 32; ++j) {
-        const double d = sm[(size_t)(k0 + j) * ld + k0 + j];
-        if (!(d > 0.0)) {
-          fail = j + 1;
-          break;
-        }
-        const double ljj = sqrt(d), ij = 1.0 / ljj;
-        __syncwarp();
-        if (i == j) {
-          rowi[j] = ljj;
-          inv[j] = ij;
-        }
-        if (i > j) rowi[j] *= ij;
-        __syncwarp();
-        if (i > j) {
-          const double lij = rowi[j];
-          for (int k = j + 1; k <= i; ++k) rowi[k] = fma(-lij, sm[(size_t)(k0 + k) * ld + k0 + j], rowi[k]);
-        }
-        __syncwarp();
-      }
-      if (i == 0) *flag = fail;
+    {
+      const int fail = cta_potrf32_par(sm + (size_t)k0 * ld + k0, ld, inv, flag);
+      if (fail) return k0 + fail;
     }
-    __syncthreads();
-    if (*flag) return k0 + *flag;
     for (int r = k0 + 32 + t; r < nb; r += kThreads) {  // rows below: x L_kk^T = row
       double* row = sm + (size_t)r * ld + k0;
       double x[32];
@@ -329,10 +384,16 @@ __device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* in
       for (int c = 0; c < 32; ++c) x[c] = row[c];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        double acc = x[c];
+        const double* lc = sm + (size_t)(k0 + c) * ld + k0;
+        double a0 = x[c], a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll
-        for (int k = 0; k < c; ++k) acc = fma(-x[k], sm[(size_t)(k0 + c) * ld + k0 + k], acc);
-        x[c] = acc * inv[c];
+        for (int k = 0; k < c; ++k) {
+          if ((k & 3) == 0) a0 = fma(-x[k], lc[k], a0);
+          if ((k & 3) == 1) a1 = fma(-x[k], lc[k], a1);
+          if ((k & 3) == 2) a2 = fma(-x[k], lc[k], a2);
+          if ((k & 3) == 3) a3 = fma(-x[k], lc[k], a3);
+        }
+        x[c] = ((a0 + a1) + (a2 + a3)) * inv[c];
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) row[c] = x[c];
@@ -344,10 +405,15 @@ __device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* in
       if (j > i) continue;
       const double* ri = sm + (size_t)(k0 + 32 + i) * ld + k0;
       const double* rj = sm + (size_t)(k0 + 32 + j) * ld + k0;
-      double acc = 0.0;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc = fma(ri[c], rj[c], acc);
-      sm[(size_t)(k0 + 32 + i) * ld + k0 + 32 + j] -= acc;
+      for (int c = 0; c < 32; c += 4) {
+        a0 = fma(ri[c], rj[c], a0);
+        a1 = fma(ri[c + 1], rj[c + 1], a1);
+        a2 = fma(ri[c + 2], rj[c + 2], a2);
+        a3 = fma(ri[c + 3], rj[c + 3], a3);
+      }
+      sm[(size_t)(k0 + 32 + i) * ld + k0 + 32 + j] -= (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
   }

@@ -144,17 +144,26 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
 // TF32 rounding (to nearest) of an FP32 value, on the integer pipe.
 __device__ __forceinline__ float tf32_rn(float f) { return __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u); }
 
-// Loads rows [r0, r0+128) x k [k0, k0+32) of the FP64 row-major operand P (ld), splits each value into
-// a TF32 high part and a TF32-rounded remainder and stores both swizzled. Coalesced: 16 lanes cover a
-// row's 32 values (256 B) with one double2 each, so a warp reads two whole row segments per pass.
-__device__ __forceinline__ void umma_stage_operand(uint8_t* hi_tile, uint8_t* lo_tile, const double* P, int ld, int r0,
-                                                   int k0) {
+// Staging of rows [r0, r0+128) x k [k0, k0+32) of an FP64 row-major operand: coalesced loads (16 lanes
+// cover a row's 32 values, 256 B, with one double2 each; a warp reads two whole row segments per pass)
+// into registers, then a split of each value into a TF32 high part and a TF32-rounded remainder,
+// stored 128-byte-swizzled. The two halves are separate so that the next chunk's loads can be in
+// flight while the current chunk is converted and multiplied.
+struct UmmaChunkRegs {
+  double2 a[8], b[8];
+};
+
+__device__ __forceinline__ void umma_load_operand(double2 (&d)[8], const double* P, int ld, int r0, int k0) {
   const int t = threadIdx.x;
-  const int kp = t & 15, rr = t >> 4;  // k pair 2kp, 2kp+1; row rr + 16 pass
-  double2 d[8];
+  const int kp = t & 15, rr = t >> 4;
 #pragma unroll
   for (int pass = 0; pass < 8; ++pass)
     d[pass] = __ldcg(reinterpret_cast<const double2*>(P + (size_t)(r0 + rr + 16 * pass) * ld + k0) + kp);
+}
+
+__device__ __forceinline__ void umma_store_operand(uint8_t* hi_tile, uint8_t* lo_tile, const double2 (&d)[8]) {
+  const int t = threadIdx.x;
+  const int kp = t & 15, rr = t >> 4;
 #pragma unroll
   for (int pass = 0; pass < 8; ++pass) {
     const float f0 = f64_to_f32_rn(d[pass].x), f1 = f64_to_f32_rn(d[pass].y);
@@ -168,17 +177,33 @@ __device__ __forceinline__ void umma_stage_operand(uint8_t* hi_tile, uint8_t* lo
 // C[128 x 128 block at (m0, n0)] (FP64, ldc) -= A[m0.., 0..K) B[n0.., 0..K)^T, A and B FP64 row-major
 // K-contiguous (K a multiple of 32). lower: write only entries with n <= m (diagonal blocks).
 // Returns false on a time-out (error already raised).
-__device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                               int m0, int n0, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
-  const int nk = K / kUmmaKChunk;
+// Up to kUmmaMaxPairs (A, B) operand pairs whose products are summed: C -= sum_p A_p B_p^T (K each).
+constexpr int kUmmaMaxPairs = 8;
+struct UmmaPairs {
+  const double* A[kUmmaMaxPairs];
+  const double* B[kUmmaMaxPairs];
+  int n;
+};
+
+__device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs& pr, int lda, int ldb, int m0,
+                               int n0, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
+  const int nkp = K / kUmmaKChunk, nk = nkp * pr.n;
+  UmmaChunkRegs rg;
+  umma_load_operand(rg.a, pr.A[0], lda, m0, 0);
+  umma_load_operand(rg.b, pr.B[0], ldb, n0, 0);
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc & 1;
     uint8_t* base = u.smem + s * kUmmaStageBytes;
     if (u.pending[s]) {  // the MMAs that read this stage two chunks ago must be done
       if (!umma_stage_wait(u, s, st, timeout_ns, where)) return false;
     }
-    umma_stage_operand(base, base + kUmmaTileBytes, A, lda, m0, kc * kUmmaKChunk);
-    umma_stage_operand(base + 2 * kUmmaTileBytes, base + 3 * kUmmaTileBytes, B, ldb, n0, kc * kUmmaKChunk);
+    umma_store_operand(base, base + kUmmaTileBytes, rg.a);
+    umma_store_operand(base + 2 * kUmmaTileBytes, base + 3 * kUmmaTileBytes, rg.b);
+    if (kc + 1 < nk) {  // next chunk's loads fly during the barrier, the MMA issue and the next wait
+      const int pi = (kc + 1) / nkp, kk = ((kc + 1) % nkp) * kUmmaKChunk;
+      umma_load_operand(rg.a, pr.A[pi], lda, m0, kk);
+      umma_load_operand(rg.b, pr.B[pi], ldb, n0, kk);
+    }
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -245,15 +270,14 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const double* A
   return true;
 }
 
-// C[M x N] -= A B^T on the tensor cores for M, N multiples of 128 and K a multiple of 32; lower skips
-// blocks above the diagonal and masks the diagonal blocks. Returns false on a time-out.
-__device__ bool umma_gemm_sub(UmmaState& u, double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                              int M, int N, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
+// C[M x N] -= sum_p A_p B_p^T on the tensor cores for M, N multiples of 128 and K a multiple of 32;
+// lower skips blocks above the diagonal and masks the diagonal blocks. Returns false on a time-out.
+__device__ bool umma_gemm_sub(UmmaState& u, double* C, int ldc, const UmmaPairs& pr, int lda, int ldb, int M, int N,
+                              int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
   for (int m0 = 0; m0 < M; m0 += kUmmaM)
     for (int n0 = 0; n0 < N; n0 += kUmmaN) {
       if (lower && n0 > m0) continue;
-      if (!umma_block_sub(u, C, ldc, A, lda, B, ldb, m0, n0, K, lower && n0 == m0, st, timeout_ns, where))
-        return false;
+      if (!umma_block_sub(u, C, ldc, pr, lda, ldb, m0, n0, K, lower && n0 == m0, st, timeout_ns, where)) return false;
     }
   return true;
 }

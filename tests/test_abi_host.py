@@ -59,8 +59,10 @@ def tasks(lib, graph, Mt, Mc, T, workers, mixed=0):
 def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
     """Every tile of the lower triangle receives POTRF/TRSM once and its updates J = 0..min-1 in order,
     and each task appears after the tasks whose tiles it reads (Fig. 1's dependencies)."""
-    t = tasks(lib, 0, Mt, 0, 64, workers, mixed)
-    assert len(t) == Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
+    T = 128 if mixed else 64  # mixed 128-tiles group their updates
+    t = tasks(lib, 0, Mt, 0, T, workers, mixed)
+    if not mixed:
+        assert len(t) == Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
     cnt = {}  # tile -> updates applied (+1 once final)
     for kind, p, q, r in t:
         if kind == 0:
@@ -69,10 +71,13 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
         elif kind == 1:
             assert cnt.get((q, q), 0) == q + 1 and cnt.get((p, q), 0) == q and p > q
             cnt[(p, q)] = q + 1
-        elif kind == 2:
-            assert p >= q > r
-            assert cnt.get((p, r), 0) == r + 1 and cnt.get((q, r), 0) == r + 1 and cnt.get((p, q), 0) == r
-            cnt[(p, q)] = r + 1
+        elif kind == 2:  # columns [J0, J1) of updates, r = J0 | J1 << 16
+            J0, J1 = r & 0xFFFF, (r >> 16) or (r & 0xFFFF) + 1
+            assert p >= q >= J1 > J0 >= 0 and J1 - J0 <= 8
+            for J in range(J0, J1):
+                assert cnt.get((p, J), 0) == J + 1 and cnt.get((q, J), 0) == J + 1
+            assert cnt.get((p, q), 0) == J0
+            cnt[(p, q)] = J1
         else:
             raise AssertionError(kind)
     assert all(cnt[(I, J)] == J + 1 for I in range(Mt) for J in range(I + 1))
