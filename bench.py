@@ -55,9 +55,10 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="solve", choices=["solve", "batch", "nlml"],
-                   help="solve: one large GP (the headline); batch: 512 uneven GPs in one graph launch; "
-                        "nlml: NLML gradient and Adam fitting at n = 16384")
+    p.add_argument("--workload", default="solve", choices=["solve", "large", "batch", "nlml"],
+                   help="solve: one large GP (the headline); large: n = 65536, m = 8192, D = 16 in mixed "
+                        "precision against one FP64 solve and cuSOLVER Dpotrf; batch: 512 uneven GPs in one "
+                        "graph launch; nlml: NLML gradient and Adam fitting at n = 16384")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--m", type=int, default=4096)
@@ -299,11 +300,25 @@ def run_ours(args):
             cov32 = torch.empty_like(cov)
             iters = [0]
 
-            def step32():
+            ph_ev = []
+
+            def step32(record=False):
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+                if record:
+                    evs[0].record(stream)
                 fac32[0] = api.gp_assemble(ctx32, Xd, h, fac32[0])
+                if record:
+                    evs[1].record(stream)
                 api.gp_cholesky(ctx32, fac32[0])
+                if record:
+                    evs[2].record(stream)
                 _, iters[0] = api.gp_predict_mean(ctx32, fac32[0], yd, Xsd, out=mean32, want_iters=True)
+                if record:
+                    evs[3].record(stream)
                 api.gp_predict_full_cov(ctx32, fac32[0], Xsd, out=cov32)
+                if record:
+                    evs[4].record(stream)
+                    ph_ev.append(evs)
 
             for _ in range(args.warmup):
                 step32()
@@ -313,11 +328,12 @@ def run_ours(args):
             m1 = torch.cuda.Event(enable_timing=True)
             m0.record(stream)
             for _ in range(args.steps):
-                step32()
+                step32(record=True)
             m1.record(stream)
             barrier()
             api.gp_sync(ctx32)
             ms32 = m0.elapsed_time(m1) / args.steps
+            phase32 = [sum(e[k].elapsed_time(e[k + 1]) for e in ph_ev) / len(ph_ev) / 1e3 for k in range(4)]
             logdet32 = api.gp_logdet(ctx32, fac32[0])
 
             def relerr(a, b):
@@ -325,6 +341,8 @@ def run_ours(args):
             mixed = {"precision": "fp32 trailing updates, FP64 POTRF/first-column TRSM/refinement",
                      "s_per_solve": ms32 / 1e3, "tflops": algorithmic_flops(n, m) / (ms32 / 1e3) / 1e12,
                      "speedup_vs_fp64": ms / ms32, "ir_iterations": iters[0],
+                     "phases_s": {"assemble": phase32[0], "cholesky": phase32[1], "mean_refined": phase32[2],
+                                  "full_cov": phase32[3]},
                      "mean_err_vs_fp64": relerr(mean32, mean64), "cov_err_vs_fp64": relerr(cov32, cov64),
                      "logdet_err_vs_fp64": abs(logdet32 - logdet64) / abs(logdet64)}
             fac32[0].free()
@@ -420,10 +438,114 @@ def ctx_tile(n, tile):
     return 256 if n >= 16384 else 128 if n >= 2048 else 64 if n >= 256 else 32
 
 
+def run_large(args):
+    """The largest single GP: n = 65536 training points (K is 34 GB in FP64, 17 GB in FP32), m = 8192
+    test points, D = 16 lags, in the mixed mode (FP32-class trailing updates on the tensor cores, FP64
+    POTRF / first-column TRSM / refinement of K^-1 y). Times the mixed solve (assembly + Cholesky +
+    refined mean + full covariance); then solves once in plain FP64 on the same GPU as the accuracy
+    reference (log-determinant, predictive-variance, mean and covariance errors of the mixed form), and
+    times cuSOLVER Dpotrf (64-bit API, one call) on an n x n FP64 matrix as a baseline."""
+    import torch
+    import nfir
+    from paper_2602_19683_gb300 import api
+    n, m, D = 65536, 8192, 16
+    dev = torch.device("cuda", 0)
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
+    Xd, yd, Xsd = (torch.from_numpy(a).to(dev) for a in (X, y, Xs))
+    h = api.Hyper(1.0, 1.0, 0.1)
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    outs = {}
+    with torch.cuda.stream(stream):
+        for prec in ("fp32", "fp64"):
+            ctx = api.Context(0, stream=stream, tile=args.tile, precision=prec, timeout_s=900.0)
+            mean = torch.empty(m, dtype=torch.float64, device=dev)
+            cov = torch.empty((m, m), dtype=torch.float64, device=dev)
+            fac = [None]
+            iters = [0]
+            ev = {}
+
+            def solve(record=False):
+                def mark(k):
+                    if record:
+                        ev[k] = torch.cuda.Event(enable_timing=True)
+                        ev[k].record(stream)
+                mark("t0")
+                fac[0] = api.gp_assemble(ctx, Xd, h, fac[0])
+                mark("t1")
+                api.gp_cholesky(ctx, fac[0])
+                mark("t2")
+                if prec == "fp32":
+                    _, iters[0] = api.gp_predict_mean(ctx, fac[0], yd, Xsd, out=mean, want_iters=True)
+                else:
+                    api.gp_predict_mean(ctx, fac[0], yd, Xsd, out=mean)
+                mark("t3")
+                api.gp_predict_full_cov(ctx, fac[0], Xsd, out=cov)
+                mark("t4")
+
+            reps = args.steps if prec == "fp32" else 1
+            for _ in range(args.warmup if prec == "fp32" else 0):
+                solve()
+            api.gp_sync(ctx)
+            phases = []
+            for _ in range(reps):
+                solve(record=True)
+                api.gp_sync(ctx)
+                phases.append([ev["t%d" % k].elapsed_time(ev["t%d" % (k + 1)]) for k in range(4)])
+            ph = [sum(p[k] for p in phases) / len(phases) / 1e3 for k in range(4)]
+            tot = sum(ph)
+            res[prec] = {"s_per_solve": tot, "tflops": algorithmic_flops(n, m) / tot / 1e12,
+                         "assemble_s": ph[0], "cholesky_s": ph[1], "mean_s": ph[2], "cov_s": ph[3],
+                         "cholesky_tflops": n ** 3 / 3 / ph[1] / 1e12, "timed_solves": reps}
+            if prec == "fp32":
+                res[prec]["ir_iterations"] = iters[0]
+            outs[prec] = (mean.clone(), cov.clone(), api.gp_logdet(ctx, fac[0]))
+            del mean, cov
+            fac[0].free()
+            ctx.close()
+            torch.cuda.synchronize(dev)
+            torch.cuda.empty_cache()
+    m32, c32, ld32 = outs["fp32"]
+    m64, c64, ld64 = outs["fp64"]
+
+    def relerr(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+    res["errors_mixed_vs_fp64"] = {"logdet_rel": abs(ld32 - ld64) / abs(ld64), "logdet_fp64": ld64,
+                                   "var_rel": relerr(torch.diagonal(c32), torch.diagonal(c64)),
+                                   "mean_rel": relerr(m32, m64), "cov_rel": relerr(c32, c64)}
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["s_per_solve"] / res["fp32"]["s_per_solve"]
+    del outs, m32, c32, m64, c64, Xd, yd, Xsd
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    if not args.no_vendor:
+        from paper_2602_19683_gb300 import baselines
+        try:
+            v = baselines.run(n, probes=False, spotrf=False, once=True, timeout=1200.0)
+            dp = v.get("cusolver_dpotrf", {})
+            res["vendor"] = {"cusolver_dpotrf_s": dp.get("ms", float("nan")) / 1e3, "api": dp.get("api"),
+                             "info": dp.get("info"),
+                             "cholesky_speedup_mixed_vs_cusolver": dp.get("ms", float("nan")) / 1e3 /
+                             res["fp32"]["cholesky_s"],
+                             "cholesky_speedup_fp64_vs_cusolver": dp.get("ms", float("nan")) / 1e3 /
+                             res["fp64"]["cholesky_s"]}
+        except Exception as e:  # the baseline leg must not hide the measured line
+            res["vendor"] = {"error": str(e)[:200]}
+    line = {"metric": "GP solve (assembly+Cholesky+mean+full cov) TFLOP/s, mixed precision, n=65536",
+            "value": res["fp32"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["fp32"]["s_per_solve"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic NFIR mass-spring-damper (seeded)",
+            "config": {"workload": f"exact GP solve n={n} m={m} D={D}, mixed vs FP64", "tile": ctx_tile(n, args.tile),
+                       "l2": "inputs larger than L2 (K is 17 GB)", "modes": res}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """512 independent GPs, n ~ U[128, 4096], m = 256, D in {4, 8, 16}: one CUDA-graph launch (batched
-    assembly + one persistent DAG launch + outputs) against a per-GP sequential loop over the single-GP
-    entry points. Metric: GPs per second (FP64 and FP32)."""
+    assembly + one persistent DAG launch + outputs). Per precision: the autotuner (gp_batch_autotune)
+    picks the tile edge per size class and the schedule; the tuned batch is timed against the same
+    batch under the library's built-in tile rule and against a per-GP sequential loop over the
+    single-GP entry points. Metric: GPs per second (FP64 and FP32)."""
     import torch
     import nfir
     from paper_2602_19683_gb300 import api
@@ -433,27 +555,36 @@ def run_batch(args):
     gps = [tuple(torch.from_numpy(a).to(dev) for a in (X, y, Xs)) + (api.Hyper(1.0, 1.0, 0.1),)
            for X, y, Xs, _ in data]
     res = {}
-    for prec in ("fp64", "fp32"):
-        ctx = api.Context(0, precision=prec)
-        b = api.Batch(ctx, gps, want_cov=True)
-        for _ in range(args.warmup):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def time_batch(ctx, entries):
+        b = api.Batch(ctx, entries, want_cov=True)
+        for _ in range(max(1, args.warmup)):
             b.run()
         api.gp_sync(ctx)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ctx.stream)
         for _ in range(args.steps):
             b.run()
         e1.record(ctx.stream)
         api.gp_sync(ctx)
-        t = e0.elapsed_time(e1) / args.steps / 1e3
-        means64 = [x.clone() for x in b.means] if prec == "fp64" else None
-        res[prec] = {"s_per_batch": t, "gps_per_s": B / t}
+        return b, e0.elapsed_time(e1) / args.steps / 1e3
+
+    ref_means = None
+    for prec in ("fp64", "fp32"):
+        ctx = api.Context(0, precision=prec)
+        tuned, rep = api.batch_autotune(ctx, gps, want_cov=True, reps=1)
+        b, t = time_batch(ctx, tuned)
+        res[prec] = {"s_per_batch": t, "gps_per_s": B / t, "autotune": rep}
         if prec == "fp64":
-            ref_means = means64
+            ref_means = [x.clone() for x in b.means]
         else:
             res[prec]["mean_err_vs_fp64"] = max(float((a - r).abs().max() / r.abs().max())
                                                 for a, r in zip(b.means, ref_means))
         b.free()
+        bd, td = time_batch(api.Context(0, precision=prec), gps)  # built-in tile rule, default schedule
+        bd.free()
+        res[prec]["default_rule_s_per_batch"] = td
+        res[prec]["speedup_tuned_vs_default_rule"] = td / t
         # per-GP sequential loop over the single-GP entry points (same kernels, one GP at a time)
         ctx2 = api.Context(0, precision=prec)
         outs = [(torch.empty(m, dtype=torch.float64, device=dev), torch.empty((m, m), dtype=torch.float64, device=dev))
@@ -536,6 +667,8 @@ def main():
         return run_batch(args)
     if args.workload == "nlml":
         return run_nlml(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

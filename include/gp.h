@@ -84,7 +84,13 @@ typedef struct {
   int32_t trace;          /* 1: the persistent kernel records, per task, the CTA and the %globaltimer
                              times at which the task was taken, became ready and finished (read with
                              gp_trace); 0 = off                                                       */
-  int32_t reserved[3];
+  int32_t batch_order;    /* dispatch order of gp_batch_create: 0 = every ready task ranked by its longest
+                             remaining cost path across all GPs; 1 = GPs ranked by total work (largest
+                             first), longest path within a GP. gp_batch_autotune stores its choice here. */
+  int32_t batch_ctas_per_sm; /* persistent-kernel CTAs per SM of batched launches (0 = library choice: two
+                             for GP_FP64, one for GP_FP32; capped by occupancy). gp_batch_autotune stores
+                             its choice here.                                                          */
+  int32_t reserved[1];
 } gp_config;
 
 typedef struct gp_ctx gp_ctx;
@@ -178,6 +184,45 @@ gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp
 gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
 gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
 
+/* Autotuner of the batched path (not in the paper, whose tile count is fixed per run): chooses each
+ * GP's tile edge and the batch's schedule by timing them on this GPU.
+ *   1. The GPs are split into `classes` size classes of equal count by n. For each class a sample of
+ *      up to `sample` GPs (evenly spaced in n) is run as a batch of its own with every candidate tile
+ *      edge (candidates more than twice the class's largest n are skipped); the fastest edge wins.
+ *   2. With those edges, the whole batch is run under every schedule (cfg.batch_order 0 and 1, and
+ *      for GP_FP64 one and two CTAs per SM); the fastest wins.
+ *   3. The batch under the library's own tile rule and schedule is timed too; if it is faster, it is
+ *      the choice (descs[g].tile = 0, order 0, residency 0).
+ * Each trial is one gp_batch_create, one untimed run and `reps` runs timed with CUDA events (the
+ * best is kept). On return descs[g].tile holds the chosen edge of GP g, the context's
+ * cfg.batch_order / cfg.batch_ctas_per_sm hold the chosen schedule (used by later gp_batch_create
+ * calls), and *result (host, may be NULL) reports the choices and timings. The trials write the
+ * outputs of the GPs they run (the caller's mean_out / cov_out arrays). Synchronous. */
+typedef struct {
+  int32_t tiles[6];  /* candidate tile edges (multiples of 32, <= 1024); all 0 = {32, 64, 128, 256} */
+  int32_t classes;   /* size classes, 1..8 (0 = 3)                                                  */
+  int32_t sample;    /* GPs timed per class (0 = 24)                                                */
+  int32_t reps;      /* timed runs per trial (0 = 2)                                                */
+  int32_t reserved;
+} gp_autotune_opts;
+
+typedef struct {
+  int32_t nclass;
+  int32_t class_tile[8];     /* chosen tile edge per class                                         */
+  int64_t class_nmax[8];     /* class k holds the GPs with class_nmax[k-1] < n <= class_nmax[k]       */
+  double class_seconds[8];   /* best time of the class's sample (s)                                */
+  int32_t order;             /* chosen cfg.batch_order                                             */
+  int32_t ctas_per_sm;       /* chosen cfg.batch_ctas_per_sm                                       */
+  int32_t trials;            /* batches built and timed                                            */
+  int32_t reserved;
+  double seconds_tuned;      /* the whole batch with the chosen tiles and schedule (s, best run)    */
+  double seconds_default;    /* the whole batch with the library's own tile rule and schedule (s)   */
+  double seconds_spent;      /* wall time of the whole search (s)                                  */
+} gp_autotune_result;
+
+gp_status gp_batch_autotune(gp_ctx* ctx, int32_t B, gp_batch_desc* descs, const gp_autotune_opts* opts,
+                            gp_autotune_result* result);
+
 /* Predictive mean (Eq. 2) of a small GP, end to end, without allocating anything -- no
  * counterpart in the paper; it exists for callers that cannot call cudaMalloc (a real-time loop that
  * must not touch the device allocator, a process whose device memory is fixed up front, or a host
@@ -202,7 +247,8 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * 1 = GP_FP32) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
- * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J)) into out (host, room
+ * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J), 14 TRTRI(J): the FP64 inverse of the factored diagonal tile
+ * J, which the vector solves of gp_predict_mean apply as a matrix-vector product) into out (host, room
  * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap);

@@ -26,13 +26,26 @@ class gp_config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("precision", ctypes.c_int32), ("ir_tol", ctypes.c_double),
                 ("ir_maxit", ctypes.c_int32), ("noisy_prior", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("withhold_task", ctypes.c_int32), ("withhold_enable", ctypes.c_int32),
-                ("tensor_cores", ctypes.c_int32), ("trace", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tensor_cores", ctypes.c_int32), ("trace", ctypes.c_int32), ("batch_order", ctypes.c_int32),
+                ("batch_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class gp_batch_desc(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("Xs", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("m", ctypes.c_int64), ("D", ctypes.c_int32), ("tile", ctypes.c_int32), ("h", gp_hyper),
                 ("mean_out", ctypes.c_void_p), ("cov_out", ctypes.c_void_p)]
+
+
+class gp_autotune_opts(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int32 * 6), ("classes", ctypes.c_int32), ("sample", ctypes.c_int32),
+                ("reps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class gp_autotune_result(ctypes.Structure):
+    _fields_ = [("nclass", ctypes.c_int32), ("class_tile", ctypes.c_int32 * 8), ("class_nmax", ctypes.c_int64 * 8),
+                ("class_seconds", ctypes.c_double * 8), ("order", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seconds_tuned", ctypes.c_double),
+                ("seconds_default", ctypes.c_double), ("seconds_spent", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -49,6 +62,8 @@ SIGNATURES = {
     "gp_batch_create": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(_P)], _I32),
     "gp_batch_run": ([_P, _P], _I32),
     "gp_batch_free": ([_P, _P], _I32),
+    "gp_batch_autotune": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(gp_autotune_opts),
+                           ctypes.POINTER(gp_autotune_result)], _I32),
     "gp_factor_rows": ([_P, _P, _I64, _I64, _P], _I32),
     "gp_alpha": ([_P, _P, _P], _I32),
     "gp_factor_free": ([_P, _P], _I32),

@@ -55,7 +55,7 @@ class Context:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, tile: int = 0,
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
-                 tensor_cores: bool = True, trace: bool = False):
+                 tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0):
         self.lib = N.load()
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -69,6 +69,8 @@ class Context:
         cfg.grid = grid
         cfg.tensor_cores = 0 if tensor_cores else -1
         cfg.trace = int(trace)
+        cfg.batch_order = batch_order
+        cfg.batch_ctas_per_sm = batch_ctas_per_sm
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1
@@ -118,7 +120,7 @@ class Factor:
 
 
 TASK_NAMES = ["POTRF", "TRSM", "UPDATE", "VTRSM", "VGEMM", "WSYRK", "FSOLVE", "FGEMV", "BSOLVE", "BGEMV",
-              "RUPD", "RTRSM", "RDIAG", "RPOTRF"]
+              "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI"]
 
 
 def gp_trace(ctx: Context):
@@ -254,6 +256,52 @@ def gp_predict_mean_noalloc(X: torch.Tensor, y: torch.Tensor, Xs: torch.Tensor, 
     return out
 
 
+def _batch_descs(gps, want_cov: bool):
+    """gp_batch_desc array for entries (X, y, Xs, hyper[, tile]), with freshly allocated outputs."""
+    descs = (N.gp_batch_desc * len(gps))()
+    inputs, means, covs = [], [], []
+    for g, e in enumerate(gps):
+        X, y, Xs, hyper = e[:4]
+        tile = e[4] if len(e) > 4 else 0
+        n, D = X.shape
+        m = Xs.shape[0]
+        _dev(X, "X")
+        _dev(y, "y", (n,))
+        _dev(Xs, "Xs", (m, D))
+        mean = torch.empty(m, dtype=torch.float64, device=X.device)
+        cov = torch.empty((m, m), dtype=torch.float64, device=X.device) if want_cov else None
+        inputs.append((X, y, Xs))
+        means.append(mean)
+        covs.append(cov)
+        d = descs[g]
+        d.X, d.y, d.Xs, d.n, d.m, d.D, d.tile = X.data_ptr(), y.data_ptr(), Xs.data_ptr(), n, m, D, tile
+        d.h = Hyper(*hyper).c
+        d.mean_out = mean.data_ptr()
+        d.cov_out = cov.data_ptr() if cov is not None else None
+    return descs, inputs, means, covs
+
+
+def batch_autotune(ctx: Context, gps, want_cov: bool = True, tiles=(), classes: int = 0, sample: int = 0,
+                   reps: int = 0):
+    """Runs gp_batch_autotune on entries (X, y, Xs, hyper[, tile]). Returns (entries with the chosen
+    tile edge appended, report dict); the chosen schedule stays in the context for later Batch()es."""
+    descs, inputs, means, covs = _batch_descs(gps, want_cov)
+    o = N.gp_autotune_opts()
+    for k, t in enumerate(list(tiles)[:6]):
+        o.tiles[k] = int(t)
+    o.classes, o.sample, o.reps = classes, sample, reps
+    r = N.gp_autotune_result()
+    _check(ctx.lib.gp_batch_autotune(ctx.h, len(gps), descs, ctypes.byref(o), ctypes.byref(r)), "gp_batch_autotune")
+    tuned = [tuple(e[:4]) + (int(descs[g].tile),) for g, e in enumerate(gps)]
+    rep = {"classes": [{"n_max": int(r.class_nmax[k]), "tile": int(r.class_tile[k]),
+                        "sample_s": float(r.class_seconds[k])} for k in range(r.nclass)],
+           "order": int(r.order), "ctas_per_sm": int(r.ctas_per_sm), "trials": int(r.trials),
+           "seconds_tuned": float(r.seconds_tuned), "seconds_default": float(r.seconds_default),
+           "seconds_spent": float(r.seconds_spent)}
+    del inputs, means, covs
+    return tuned, rep
+
+
 class Batch:
     """A gp_batch: many independent GPs assembled, factored and predicted by one captured CUDA graph
     (batched assembly, one persistent task-DAG launch, outputs). Entries are (X, y, Xs, hyper) or
@@ -261,27 +309,7 @@ class Batch:
 
     def __init__(self, ctx: Context, gps, want_cov: bool = True):
         self.ctx = ctx
-        self.inputs = []
-        self.means, self.covs = [], []
-        descs = (N.gp_batch_desc * len(gps))()
-        for g, e in enumerate(gps):
-            X, y, Xs, hyper = e[:4]
-            tile = e[4] if len(e) > 4 else 0
-            n, D = X.shape
-            m = Xs.shape[0]
-            _dev(X, "X")
-            _dev(y, "y", (n,))
-            _dev(Xs, "Xs", (m, D))
-            mean = torch.empty(m, dtype=torch.float64, device=X.device)
-            cov = torch.empty((m, m), dtype=torch.float64, device=X.device) if want_cov else None
-            self.inputs.append((X, y, Xs))
-            self.means.append(mean)
-            self.covs.append(cov)
-            d = descs[g]
-            d.X, d.y, d.Xs, d.n, d.m, d.D, d.tile = X.data_ptr(), y.data_ptr(), Xs.data_ptr(), n, m, D, tile
-            d.h = Hyper(*hyper).c
-            d.mean_out = mean.data_ptr()
-            d.cov_out = cov.data_ptr() if cov is not None else None
+        descs, self.inputs, self.means, self.covs = _batch_descs(gps, want_cov)
         self.h = ctypes.c_void_p()
         _check(ctx.lib.gp_batch_create(ctx.h, len(gps), descs, ctypes.byref(self.h)), "gp_batch_create")
 

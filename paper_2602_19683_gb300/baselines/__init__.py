@@ -18,9 +18,11 @@ def build() -> str:
     return EXE
 
 
-def run(n: int = 32768, potrf: bool = True, timeout: float = 600.0) -> dict:
-    """Runs the probes; returns {probe name: record}."""
-    args = [build(), str(n)] + ([] if potrf else ["--no-potrf"])
+def run(n: int = 32768, potrf: bool = True, timeout: float = 600.0, probes: bool = True, spotrf: bool = True,
+        once: bool = False) -> dict:
+    """Runs the probes; returns {probe name: record}. once: time the first Dpotrf call (no warm-up)."""
+    args = [build(), str(n)] + ([] if potrf else ["--no-potrf"]) + ([] if probes else ["--no-probes"]) + \
+        ([] if spotrf else ["--no-spotrf"]) + (["--once"] if once else [])
     out = subprocess.run(args, capture_output=True, text=True, timeout=timeout, check=True).stdout
     res = {}
     for line in out.splitlines():

@@ -2,7 +2,10 @@
 //   cuSOLVER Dpotrf / Spotrf on an n x n SPD matrix (the single-call factorisation the paper's
 //   tiled approach is compared with in Sec. 4.1), cuBLAS DGEMM, and register-only FP64 FFMA,
 //   FP64 mma.sync (DMMA) and FP32 FFMA loops that bound what FMA-issue-bound kernels can reach.
-// Prints one JSON object per measurement. Usage: vendor_baselines [n] [--no-potrf]
+// Prints one JSON object per measurement.
+// Usage: vendor_baselines [n] [--no-potrf] [--no-spotrf] [--no-probes] [--once]
+//   --once: time the first Dpotrf call (no warm-up call; for sizes where one call takes a minute).
+// Above n = 46340 (n^2 > 2^31 entries) Dpotrf goes through the 64-bit generic API (cusolverDnXpotrf).
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -97,27 +100,31 @@ float best_ms(F f, int reps) {
 
 int main(int argc, char** argv) {
   long long n = 32768;
-  bool potrf = true;
+  bool potrf = true, spotrf = true, probes = true, once = false;
   for (int i = 1; i < argc; ++i) {
     if (!strcmp(argv[i], "--no-potrf")) potrf = false;
+    else if (!strcmp(argv[i], "--no-spotrf")) spotrf = false;
+    else if (!strcmp(argv[i], "--no-probes")) probes = false;
+    else if (!strcmp(argv[i], "--once")) once = true;
     else n = atoll(argv[i]);
   }
+  const bool big = n * n > 2147483647LL;
   cudaDeviceProp p;
   CK(cudaGetDeviceProperties(&p, 0));
   const int sms = p.multiProcessorCount;
   double* out;
   CK(cudaMalloc(&out, sizeof(double) * sms * 2048));
-  {
+  if (probes) {
     const int grid = sms * 8, iters = 4000;
     float ms = best_ms([&] { ffma64_loop<<<grid, 256>>>(out, iters, 0.999, 1e-3); }, 3);
     printf("{\"probe\": \"ffma64\", \"tflops\": %.4f}\n", 2.0 * 16 * iters * (double)grid * 256 / ms / 1e9);
   }
-  {
+  if (probes) {
     const int grid = sms * 8, iters = 2000;
     float ms = best_ms([&] { ffma32_loop<<<grid, 256>>>((float*)out, iters, 0.999f, 1e-3f); }, 3);
     printf("{\"probe\": \"ffma32\", \"tflops\": %.4f}\n", 2.0 * 128 * iters * (double)grid * 256 / ms / 1e9);
   }
-  {
+  if (probes) {
     const int grid = sms * 4, iters = 400;
     float ms = best_ms([&] { dmma_loop<<<grid, 256>>>(out, iters); }, 3);
     printf("{\"probe\": \"dmma_m8n8k4\", \"tflops\": %.4f}\n", 2.0 * 256 * 8 * iters * (double)grid * 8 / ms / 1e9);
@@ -127,7 +134,7 @@ int main(int argc, char** argv) {
   CK(cudaMalloc(&A, sizeof(double) * n * n));
   cublasHandle_t bh;
   cublasCreate(&bh);
-  {
+  if (probes) {
     const int N = 8192;
     double *B, *C;
     CK(cudaMalloc(&B, sizeof(double) * N * N));
@@ -145,30 +152,65 @@ int main(int argc, char** argv) {
     cusolverDnCreate(&sh);
     int* info;
     CK(cudaMalloc(&info, sizeof(int)));
-    int lw = 0;
-    cusolverDnDpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, &lw);
-    double* W;
-    CK(cudaMalloc(&W, sizeof(double) * (lw + 1)));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    for (int r = 0; r < 2; ++r) {  // first call warms up
-      fill_spd<<<4096, 256>>>(A, n);
-      CK(cudaDeviceSynchronize());
-      cudaEventRecord(e0);
-      cusolverDnDpotrf(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, W, lw, info);
-      cudaEventRecord(e1);
-      CK(cudaEventSynchronize(e1));
-      float ms;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (r > 0) best = ms;
+    if (!big) {
+      int lw = 0;
+      cusolverDnDpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, &lw);
+      double* W;
+      CK(cudaMalloc(&W, sizeof(double) * (lw + 1)));
+      for (int r = once ? 1 : 0; r < 2; ++r) {  // r = 0 warms up
+        fill_spd<<<4096, 256>>>(A, n);
+        CK(cudaDeviceSynchronize());
+        cudaEventRecord(e0);
+        cusolverDnDpotrf(sh, CUBLAS_FILL_MODE_LOWER, (int)n, A, (int)n, W, lw, info);
+        cudaEventRecord(e1);
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = ms;
+      }
+      cudaFree(W);
+    } else {
+      cusolverDnParams_t prm;
+      cusolverDnCreateParams(&prm);
+      size_t wd = 0, wh = 0;
+      cusolverDnXpotrf_bufferSize(sh, prm, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, A, n, CUDA_R_64F, &wd, &wh);
+      void* Wd = nullptr;
+      CK(cudaMalloc(&Wd, wd + 16));
+      void* Wh = malloc(wh + 16);
+      for (int r = once ? 1 : 0; r < 2; ++r) {
+        fill_spd<<<4096, 256>>>(A, n);
+        CK(cudaDeviceSynchronize());
+        cudaEventRecord(e0);
+        cusolverDnXpotrf(sh, prm, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, A, n, CUDA_R_64F, Wd, wd, Wh, wh, info);
+        cudaEventRecord(e1);
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = ms;
+      }
+      cudaFree(Wd);
+      free(Wh);
+      cusolverDnDestroyParams(prm);
     }
     int hinfo = -1;
     cudaMemcpy(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost);
-    printf("{\"probe\": \"cusolver_dpotrf\", \"n\": %lld, \"ms\": %.3f, \"tflops\": %.4f, \"info\": %d}\n", n, best,
-           (double)n * n * (double)n / 3.0 / best / 1e9, hinfo);
+    printf("{\"probe\": \"cusolver_dpotrf\", \"n\": %lld, \"ms\": %.3f, \"tflops\": %.4f, \"info\": %d, \"api\": \"%s\"}\n",
+           n, best, (double)n * n * (double)n / 3.0 / best / 1e9, hinfo, big ? "Xpotrf" : "Dpotrf");
     fflush(stdout);
+  }
+  if (potrf && spotrf && !big) {
+    cusolverDnHandle_t sh;
+    cusolverDnCreate(&sh);
+    int* info;
+    CK(cudaMalloc(&info, sizeof(int)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
     float* Af;
     CK(cudaMalloc(&Af, sizeof(float) * n * n));
     int lwf = 0;

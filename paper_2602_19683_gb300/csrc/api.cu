@@ -1,6 +1,7 @@
 // C ABI of libgp (declared in include/gp.h): contexts, factor objects, workspace and the entry
 // points of the hot path (assembly, tiled Cholesky, mean and covariance prediction).
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -96,6 +97,7 @@ struct gp_factor {
   DevBuf Kt, cK;              // packed lower tiles and their counters
   DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
+  DevBuf Linv;                // inverses of the diagonal tiles of L (written by the Cholesky launch)
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
   DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
                                   // sums, counters, L^{-1} y
@@ -194,6 +196,7 @@ gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
   GP_TRY(get_tasks(c, 2, Mt, 0, T, false, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.bvec = (double*)f->bvec.p;
+  a.Linv = (double*)f->Linv.p;  // diagonal-block solves as products with the stored inverses
   int* cm = (int*)f->cMean.p;
   a.cF = cm;
   a.cB = cm + (size_t)Mt * nch;
@@ -243,6 +246,8 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   if (c.ir_tol <= 0) c.ir_tol = 1e-15;
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
+  if (c.batch_order < 0 || c.batch_order > 1 || c.batch_ctas_per_sm < 0 || c.batch_ctas_per_sm > 2)
+    return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(device));
   gp_ctx* ctx = new (std::nothrow) gp_ctx();
   if (!ctx) return GP_ERR_OOM;
@@ -379,6 +384,7 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->beta);
   release(f->bvec);
   release(f->cMean);
+  release(f->Linv);
   release(f->V);
   release(f->S);
   release(f->cCov);
@@ -432,8 +438,11 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   const TaskBuf* tb;
   GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, mixed, &tb));
   const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
+  GP_TRY(grow(f->Linv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
   GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
-  GP_TRY(run_dag(c, base_args(c, f), tb, mixed));
+  gpk::DagArgs a = base_args(c, f);
+  a.Linv = (double*)f->Linv.p;
+  GP_TRY(run_dag(c, a, tb, mixed));
   f->factored = true;
   return GP_OK;
 }
@@ -751,9 +760,14 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     pre.push_back(make_int4(3, g, 0, 0));
     for (long long r = 0; r < e.m; r += 8) post.push_back(make_int4(0, g, (int)r, 0));
   }
-  // task order over all GPs (cached per batch: the plan owns it)
-  const int workers = c->grid[mixed ? 1 : 0];
-  std::vector<gpk::Task4> tasks = gpk::batch_tasks(shapes, want_cov, workers, cost_model(c, mixed));
+  // persistent-kernel residency, then the task order over all GPs for that many workers
+  const int occ = gpk::dag_max_ctas_per_sm_batch(mixed);
+  int per_sm = c->cfg.batch_ctas_per_sm > 0 ? c->cfg.batch_ctas_per_sm : (mixed ? 1 : 2);
+  if (per_sm > occ) per_sm = occ > 0 ? occ : 1;
+  const int grid = c->sms * per_sm;
+  gpk::CostModel cm = cost_model(c, mixed);
+  cm.sec_per_flop = (double)per_sm / 7.8e9;
+  std::vector<gpk::Task4> tasks = gpk::batch_tasks(shapes, want_cov, grid, cm, c->cfg.batch_order);
   st = grow(b->tasks, tasks.size() * sizeof(gpk::Task4));
   if (st == GP_OK) st = grow(b->items, (pre.size() + post.size()) * sizeof(int4));
   if (st != GP_OK) {
@@ -790,9 +804,6 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     a.timeout_ns = c->cfg.timeout_ns;
     a.withhold_task = -1;
     a.use_umma = (mixed && c->cfg.tensor_cores >= 0) ? 1 : 0;
-    const int occ = gpk::dag_max_ctas_per_sm_batch(mixed);
-    const int cap = mixed ? 1 : 2;
-    const int grid = c->sms * (occ >= cap ? cap : (occ > 0 ? occ : 1));
     gpk::launch_dag(a, grid < b->ntasks ? grid : b->ntasks, mixed, cs, false, true);
     gpk::launch_batch_post((const int4*)b->items.p + b->npre, b->npost, (const gpk::GpDesc*)b->descs.p, cs);
     cudaGraph_t graph = nullptr;
@@ -828,6 +839,149 @@ gp_status gp_batch_free(gp_ctx* c, gp_batch* b) {
   release(b->tasks);
   release(b->items);
   delete b;
+  return GP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One autotuner trial: builds the batch from descs, runs it once untimed and `reps` times timed
+// (CUDA events on the context's stream), frees it. *best_s receives the fastest timed run.
+gp_status autotune_trial(gp_ctx* c, const std::vector<gp_batch_desc>& descs, int reps, double* best_s) {
+  gp_batch* b = nullptr;
+  GP_TRY(gp_batch_create(c, (int32_t)descs.size(), descs.data(), &b));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gp_status st = cuda_status(cudaEventCreate(&e0));
+  if (st == GP_OK) st = cuda_status(cudaEventCreate(&e1));
+  if (st == GP_OK) st = gp_batch_run(c, b);
+  if (st == GP_OK) st = gp_sync(c, nullptr);
+  double best = 1e300;
+  for (int r = 0; r < reps && st == GP_OK; ++r) {
+    cudaEventRecord(e0, c->stream);
+    st = gp_batch_run(c, b);
+    cudaEventRecord(e1, c->stream);
+    if (st == GP_OK) st = gp_sync(c, nullptr);
+    float ms = 0.f;
+    if (st == GP_OK) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+    if (st == GP_OK) best = std::min(best, (double)ms / 1e3);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  gp_batch_free(c, b);
+  *best_s = best;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_batch_autotune(gp_ctx* c, int32_t B, gp_batch_desc* descs, const gp_autotune_opts* opts,
+                            gp_autotune_result* result) {
+  if (!c || !descs || B < 1) return GP_ERR_INVALID_ARG;
+  gp_autotune_opts o{};
+  if (opts) o = *opts;
+  std::vector<int> cand;
+  for (int k = 0; k < 6; ++k) {
+    const int t = o.tiles[k];
+    if (t == 0) continue;
+    if (t < 32 || t > 1024 || t % 32) return GP_ERR_INVALID_ARG;
+    if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
+  }
+  if (cand.empty()) cand = {32, 64, 128, 256};
+  const int nclass = o.classes > 0 ? std::min(o.classes, 8) : 3;
+  const int sample = o.sample > 0 ? o.sample : 24;
+  const int reps = o.reps > 0 ? o.reps : 2;
+  if (o.classes < 0 || o.sample < 0 || o.reps < 0) return GP_ERR_INVALID_ARG;
+  for (int g = 0; g < B; ++g)
+    if (descs[g].n < 1) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const auto t_start = std::chrono::steady_clock::now();
+  const gp_config saved = c->cfg;
+  gp_autotune_result r{};
+  // GPs in increasing n; class k = ranks [k B / nclass, (k+1) B / nclass)
+  std::vector<int> idx(B);
+  for (int g = 0; g < B; ++g) idx[g] = g;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return descs[a].n < descs[b].n; });
+  const int nc = std::min(nclass, B);
+  std::vector<int> chosen(B, 0);
+  gp_status st = GP_OK;
+  c->cfg.batch_order = 0;
+  c->cfg.batch_ctas_per_sm = 0;
+  for (int k = 0; k < nc && st == GP_OK; ++k) {
+    const int lo = (int)((long long)k * B / nc), hi = (int)((long long)(k + 1) * B / nc);
+    const long long nmax = descs[idx[hi - 1]].n;
+    std::vector<gp_batch_desc> sub;
+    const int cnt = std::min(sample, hi - lo);
+    for (int s2 = 0; s2 < cnt; ++s2) {
+      const int pos = lo + (int)((long long)s2 * (hi - lo) / cnt);
+      sub.push_back(descs[idx[pos]]);
+    }
+    int best_t = 0;
+    double best = 1e300;
+    for (int t : cand) {
+      if (t > 2 * nmax && best_t != 0) continue;  // mostly padding: skip once some edge has a time
+      for (auto& d : sub) d.tile = t;
+      double sec = 0.0;
+      st = autotune_trial(c, sub, reps, &sec);
+      ++r.trials;
+      if (st != GP_OK) break;
+      if (sec < best) {
+        best = sec;
+        best_t = t;
+      }
+    }
+    for (int p = lo; p < hi; ++p) chosen[idx[p]] = best_t;
+    r.class_tile[k] = best_t;
+    r.class_nmax[k] = nmax;
+    r.class_seconds[k] = best;
+  }
+  r.nclass = nc;
+  // schedule search on the whole batch with the chosen edges
+  std::vector<gp_batch_desc> all(descs, descs + B);
+  for (int g = 0; g < B && st == GP_OK; ++g) all[g].tile = chosen[g];
+  const bool mixed = c->cfg.precision == GP_FP32;
+  double best = 1e300;
+  int best_order = 0, best_ctas = 0;
+  for (int order = 0; order < 2 && st == GP_OK; ++order)
+    for (int ctas = 1; ctas <= (mixed ? 1 : 2) && st == GP_OK; ++ctas) {
+      c->cfg.batch_order = order;
+      c->cfg.batch_ctas_per_sm = ctas;
+      double sec = 0.0;
+      st = autotune_trial(c, all, reps, &sec);
+      ++r.trials;
+      if (st == GP_OK && sec < best) {
+        best = sec;
+        best_order = order;
+        best_ctas = ctas;
+      }
+    }
+  // the library's own rule, for the report
+  if (st == GP_OK) {
+    std::vector<gp_batch_desc> def(descs, descs + B);
+    for (auto& d : def) d.tile = 0;
+    c->cfg.batch_order = 0;
+    c->cfg.batch_ctas_per_sm = 0;
+    st = autotune_trial(c, def, reps, &r.seconds_default);
+    ++r.trials;
+  }
+  c->cfg = saved;
+  if (st != GP_OK) return st;
+  if (r.seconds_default < best) {  // the built-in rule won the final comparison: keep it
+    best = r.seconds_default;
+    std::fill(chosen.begin(), chosen.end(), 0);
+    best_order = 0;
+    best_ctas = 0;
+  }
+  for (int g = 0; g < B; ++g) descs[g].tile = chosen[g];
+  c->cfg.batch_order = best_order;
+  c->cfg.batch_ctas_per_sm = best_ctas;
+  r.order = best_order;
+  r.ctas_per_sm = best_ctas;
+  r.seconds_tuned = best;
+  r.seconds_spent = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (result) *result = r;
   return GP_OK;
 }
 

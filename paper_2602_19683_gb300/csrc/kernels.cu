@@ -179,6 +179,8 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
       const int part = (p - q - 1) % kAdjParts, k = (p - q - 1) / kAdjParts;
       return wait_ge(a.fa + tri(p, q), 1, st, to, ti) && wait_ge(a.rd + (size_t)q * kAdjParts + part, k, st, to, ti);
     }
+    case TASK_TRTRI:  // (J=p): the factored diagonal tile
+      return wait_ge(a.cK + tri(p, p), p + 1, st, to, ti);
     case TASK_RPOTRF: {  // (J=p): every part complete
       for (int part = 0; part < kAdjParts; ++part) {
         const int cnt = (a.Mt - 1 - p - part + kAdjParts - 1) / kAdjParts;
@@ -359,7 +361,10 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         break;
       }
       case TASK_FSOLVE:
-        cta_trsv_lower(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
+        if (a.Linv)
+          cta_trsv_inv(a.Linv + (size_t)p * TT, T, a.bvec + (size_t)p * T, T, &s.g.a[0][0][0]);
+        else
+          cta_trsv_lower(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
         cta_publish(a.dF + p, 1);
         break;
       case TASK_FGEMV:
@@ -368,8 +373,14 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         cta_publish(a.cF + (size_t)p * a.nch + r, q + 1);
         break;
       case TASK_BSOLVE:
-        cta_trsv_lower_T(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
+        if (a.Linv)
+          cta_trsv_inv_T(a.Linv + (size_t)p * TT, T, a.bvec + (size_t)p * T, T, &s.g.a[0][0][0], s_red);
+        else
+          cta_trsv_lower_T(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
         cta_publish(a.dB + p, 1);
+        break;
+      case TASK_TRTRI:  // read by later launches only: nothing to publish
+        cta_trtri(a.Kt + tri(p, p) * TT, T, a.Linv + (size_t)p * TT, T, s);
         break;
       case TASK_BGEMV:
         cta_gemv_T_sub(a.Kt + tri(q, p) * TT + (size_t)r * 32, T, a.bvec + (size_t)q * T,

@@ -25,7 +25,10 @@ enum TaskKind {
   TASK_RUPD = 10,   // (P, K, J)  Lbar_PJ -= Abar~_PK L_KJ    (reverse of step J's SYRK/GEMM updates)
   TASK_RTRSM = 11,  // (P, J)     Abar_PJ = Lbar_PJ L_JJ^{-1} (reverse of TRSM(P, J))
   TASK_RDIAG = 12,  // (P, J)     Lbar_JJ -= tril(Abar_PJ^T L_PJ)
-  TASK_RPOTRF = 13  // (J)        Abar_JJ = sym(L^{-T} Phi(L^T Lbar_JJ) L^{-1})  (reverse of POTRF(J))
+  TASK_RPOTRF = 13,  // (J)       Abar_JJ = sym(L^{-T} Phi(L^T Lbar_JJ) L^{-1})  (reverse of POTRF(J))
+  // Inverse of a factored diagonal tile, kept for the vector solves of Eq. (2) (each diagonal-block
+  // solve becomes a matrix-vector product; not a step of the paper, which solves by substitution).
+  TASK_TRTRI = 14    // (J)        Linv_J = L_JJ^{-1} (FP64)
 };
 
 // One GP of a batch: its inputs, outputs, hyperparameters and workspace (all device pointers).
@@ -67,6 +70,7 @@ struct DagArgs {
   double* S;        // Mc*T x lds row-major, lower tiles hold K_{Xs,Xs} - V^T V on exit
   long long lds;
   double* bvec;     // Mt*T vector: y on entry, beta then alpha
+  double* Linv;     // Mt x T x T: inverses of the diagonal tiles of L (null: solves by substitution)
   int nch;          // T / 32 (row chunks of the vector tasks)
   int* cK;          // per lower K tile: updates applied (J+1 once final)
   int* cV;          // per V tile

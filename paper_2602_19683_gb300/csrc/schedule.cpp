@@ -13,7 +13,7 @@
 namespace gpk {
 
 std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
-                               int workers) {
+                               int workers, const std::vector<double>* group_key) {
   const int n = (int)cost.size();
   std::vector<std::vector<int>> succ(n);
   std::vector<int> indeg(n, 0);
@@ -29,7 +29,10 @@ std::vector<int> list_schedule(const std::vector<double>& cost, const std::vecto
     for (int s : succ[t]) m = std::max(m, bl[s]);
     bl[t] = cost[t] + m;
   }
-  auto cmp = [&](int a, int b) { return bl[a] < bl[b] || (bl[a] == bl[b] && a > b); };
+  auto cmp = [&](int a, int b) {
+    if (group_key && (*group_key)[a] != (*group_key)[b]) return (*group_key)[a] < (*group_key)[b];
+    return bl[a] < bl[b] || (bl[a] == bl[b] && a > b);
+  };
   std::priority_queue<int, std::vector<int>, decltype(cmp)> ready(cmp);
   for (int t = 0; t < n; ++t)
     if (indeg[t] == 0) ready.push(t);
@@ -76,8 +79,8 @@ struct Builder {
     preds.push_back(std::move(d));
     return (int)tasks.size() - 1;
   }
-  std::vector<Task4> ordered(int workers) const {
-    std::vector<int> ord = list_schedule(cost, preds, workers);
+  std::vector<Task4> ordered(int workers, const std::vector<double>* group_key = nullptr) const {
+    std::vector<int> ord = list_schedule(cost, preds, workers, group_key);
     std::vector<Task4> out;
     out.reserve(ord.size());
     for (int t : ord) out.push_back(tasks[t]);
@@ -109,6 +112,7 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   for (int J = 0; J < Mt; ++J) {
     const int po = b.add(TASK_POTRF, J, 0, 0, c_potrf, {last[tri(J, J)]});
     last[tri(J, J)] = po;
+    b.add(TASK_TRTRI, J, 0, 0, c_trsm0, {po});  // inverse of L_JJ for the vector solves; nothing waits on it
     for (int I = J + 1; I < Mt; ++I) {
       last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, J == 0 ? c_trsm0 : c_trsm, {po, last[tri(I, J)]});
       trsm_of[tri(I, J)] = last[tri(I, J)];
@@ -275,10 +279,23 @@ void append_gp(Builder& b, int g, const BatchGp& gp, bool want_cov, const CostMo
 
 }  // namespace
 
-std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm) {
+std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm,
+                               int order) {
   Builder b;
-  for (size_t g = 0; g < gps.size(); ++g) append_gp(b, (int)g, gps[g], want_cov, cm);
-  return b.ordered(workers);
+  std::vector<size_t> first(gps.size() + 1, 0);
+  for (size_t g = 0; g < gps.size(); ++g) {
+    first[g] = b.tasks.size();
+    append_gp(b, (int)g, gps[g], want_cov, cm);
+  }
+  first[gps.size()] = b.tasks.size();
+  if (order != 1) return b.ordered(workers);
+  std::vector<double> key(b.tasks.size(), 0.0);  // each task carries its GP's total modelled work
+  for (size_t g = 0; g < gps.size(); ++g) {
+    double w = 0.0;
+    for (size_t t = first[g]; t < first[g + 1]; ++t) w += b.cost[t];
+    for (size_t t = first[g]; t < first[g + 1]; ++t) key[t] = w;
+  }
+  return b.ordered(workers, &key);
 }
 
 std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm) {

@@ -36,11 +36,15 @@ std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm);
 struct BatchGp {
   int Mt, Mc, T;
 };
-std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm);
+// order 0: every ready task ranked by its bottom level (longest remaining cost path) across all GPs;
+// order 1: GPs ranked by their total work (largest first), bottom level within a GP.
+std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, int workers, const CostModel& cm,
+                               int order = 0);
 
 // Generic list scheduling: returns the start order of tasks with the given costs and
-// predecessor lists, simulated on `workers` identical workers.
+// predecessor lists, simulated on `workers` identical workers. Ready tasks are ranked by
+// (group_key, bottom level) when group_key is given, else by bottom level alone.
 std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
-                               int workers);
+                               int workers, const std::vector<double>* group_key = nullptr);
 
 }  // namespace gpk

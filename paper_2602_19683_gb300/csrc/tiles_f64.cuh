@@ -559,6 +559,73 @@ __device__ void cta_trsv_lower_T(const double* L, int ldl, double* b, int nb, do
   }
 }
 
+// b[0..nb) <- Linv b, Linv the lower-triangular inverse of a diagonal tile (upper triangle zero): the
+// diagonal-block solve as a matrix-vector product, without the substitution's serial chain. b is
+// staged in smem (xs, nb doubles). Each warp takes four rows at a time; lanes stride the columns
+// (coalesced row segments), so 4 x (nb / 32) loads per lane are independent.
+__device__ void cta_trsv_inv(const double* Linv, int ld, double* b, int nb, double* xs) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  for (int i = t; i < nb; i += kThreads) xs[i] = ldcg(b + i);
+  __syncthreads();
+  for (int r0 = 4 * w; r0 < nb; r0 += 4 * (kThreads / 32)) {
+    const double* L0 = Linv + (size_t)r0 * ld;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 4
+    for (int c = lane; c <= r0 + 3; c += 32) {
+      const double x = xs[c];
+      a0 = fma(ldcg(L0 + c), x, a0);
+      a1 = fma(ldcg(L0 + ld + c), x, a1);
+      a2 = fma(ldcg(L0 + 2 * (size_t)ld + c), x, a2);
+      a3 = fma(ldcg(L0 + 3 * (size_t)ld + c), x, a3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+    }
+    if (lane == 0) {
+      b[r0] = a0;
+      b[r0 + 1] = a1;
+      b[r0 + 2] = a2;
+      b[r0 + 3] = a3;
+    }
+  }
+  __syncthreads();
+}
+
+// b[0..nb) <- Linv^T b (the diagonal-block solve of L^T x = b). Per 32-column strip: warps split the
+// rows at or below the strip, lanes own its columns; partial sums are reduced through red[8][32].
+__device__ void cta_trsv_inv_T(const double* Linv, int ld, double* b, int nb, double* xs, double (*red)[32]) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  for (int i = t; i < nb; i += kThreads) xs[i] = ldcg(b + i);
+  __syncthreads();
+  for (int c0 = 0; c0 < nb; c0 += 32) {
+    double a0 = 0.0, a1 = 0.0;
+    int r = c0 + w;
+#pragma unroll 2
+    for (; r + kThreads / 32 < nb; r += 2 * (kThreads / 32)) {
+      a0 = fma(ldcg(Linv + (size_t)r * ld + c0 + lane), xs[r], a0);
+      a1 = fma(ldcg(Linv + (size_t)(r + kThreads / 32) * ld + c0 + lane), xs[r + kThreads / 32], a1);
+    }
+    if (r < nb) a0 = fma(ldcg(Linv + (size_t)r * ld + c0 + lane), xs[r], a0);
+    red[w][lane] = a0 + a1;
+    __syncthreads();
+    if (t < 32) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < kThreads / 32; ++q) acc += red[q][t];
+      b[c0 + t] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Linv <- L^{-1} for a factored nb x nb diagonal tile: the identity solved in place from the left.
+// Entries above the diagonal stay exactly zero.
+__device__ void cta_trtri(const double* L, int ldl, double* Linv, int nb, TileSmem& s);
+
 // b[r] -= sum_c A[r][c] x[c] for r in [0, rows): one warp per row, lanes over columns.
 __device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* b, int rows, int cols) {
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -590,6 +657,13 @@ __device__ void cta_gemv_T_sub(const double* A, int lda, const double* x, double
     b[threadIdx.x] = ldcg(b + threadIdx.x) - s;
   }
   __syncthreads();
+}
+
+__device__ void cta_trtri(const double* L, int ldl, double* Linv, int nb, TileSmem& s) {
+  const size_t nn = (size_t)nb * nb;
+  for (size_t e = threadIdx.x; e < nn; e += kThreads) Linv[e] = (e / nb == e % nb) ? 1.0 : 0.0;
+  __syncthreads();
+  cta_trsm_left(L, ldl, Linv, nb, nb, nb, s);
 }
 
 }  // namespace gpk

@@ -62,12 +62,16 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
     T = 128 if mixed else 64  # mixed 128-tiles group their updates
     t = tasks(lib, 0, Mt, 0, T, workers, mixed)
     if not mixed:
-        assert len(t) == Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
+        assert len(t) == 2 * Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
     cnt = {}  # tile -> updates applied (+1 once final)
+    inverted = set()
     for kind, p, q, r in t:
         if kind == 0:
             assert cnt.get((p, p), 0) == p
             cnt[(p, p)] = p + 1
+        elif kind == 14:  # TRTRI(J): after POTRF(J), once
+            assert cnt.get((p, p), 0) == p + 1 and p not in inverted
+            inverted.add(p)
         elif kind == 1:
             assert cnt.get((q, q), 0) == q + 1 and cnt.get((p, q), 0) == q and p > q
             cnt[(p, q)] = q + 1
@@ -81,6 +85,7 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
         else:
             raise AssertionError(kind)
     assert all(cnt[(I, J)] == J + 1 for I in range(Mt) for J in range(I + 1))
+    assert inverted == set(range(Mt))
 
 
 @pytest.mark.parametrize("Mt,Mc,workers", [(1, 1, 2), (4, 3, 5), (7, 2, 304)])

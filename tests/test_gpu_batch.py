@@ -70,3 +70,61 @@ def test_batch_tiles_and_errors(api):
         api.gp_sync(ctx)
     assert e.value.status == 2 and (e.value.info >> 32) == 1 and (e.value.info & 0xFFFFFFFF) == 3
     b.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotuner_choices_and_tuned_batch(api, precision):
+    """gp_batch_autotune picks one candidate edge per size class and a schedule; the batch built with
+    its choices (and the schedule it leaves in the context) still matches the oracle."""
+    gps = make_gps(12, 40, seed0=3000)
+    dev = [(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(Xs).cuda(), h)
+           for X, y, Xs, h in gps]
+    ctx = api.Context(0, precision=precision)
+    tuned, rep = api.batch_autotune(ctx, dev, want_cov=True, tiles=(32, 64, 128), classes=2, sample=4, reps=1)
+    assert len(rep["classes"]) == 2 and rep["trials"] >= 2 + 2
+    ns = sorted(X.shape[0] for X, _, _, _ in gps)
+    assert rep["classes"][0]["n_max"] == ns[5] and rep["classes"][1]["n_max"] == ns[11]
+    for c in rep["classes"]:
+        assert c["tile"] in (32, 64, 128) and c["sample_s"] > 0
+    assert rep["seconds_tuned"] > 0 and rep["seconds_default"] > 0
+    assert rep["seconds_tuned"] <= rep["seconds_default"]
+    builtin = all(t == 0 for *_, t in tuned)  # the library's own rule won the final comparison
+    for (X, _, _, _, t) in tuned:  # otherwise every GP carries its class's edge
+        k = 0 if X.shape[0] <= rep["classes"][0]["n_max"] else 1
+        assert t == (0 if builtin else rep["classes"][k]["tile"])
+    if builtin:
+        assert rep["order"] == 0 and rep["ctas_per_sm"] == 0
+    else:
+        assert rep["order"] in (0, 1) and rep["ctas_per_sm"] in ((1,) if precision == "fp32" else (1, 2))
+    batch = api.Batch(ctx, tuned, want_cov=True)
+    batch.run()
+    api.gp_sync(ctx)
+    for g, (X, y, Xs, h) in enumerate(gps):
+        ref = oracle.gp_predict(X, y, Xs, h)
+        em = rel(batch.means[g].cpu().numpy(), ref["mean"])
+        ec = rel(batch.covs[g].cpu().numpy(), ref["cov"])
+        if precision == "fp64":
+            assert em <= 1e-10 and ec <= 1e-9, (g, em, ec)
+        else:
+            assert em <= 1e-3 and ec <= 2e-4, (g, em, ec)
+    batch.free()
+
+
+@pytest.mark.parametrize("order,ctas", [(1, 1), (0, 1), (1, 2)])
+def test_batch_schedule_options(api, order, ctas):
+    """Both dispatch orders and both residencies give the same FP64 results (bit-identical: updates
+    into a tile are applied in a fixed order whatever the schedule)."""
+    gps = make_gps(6, 32, seed0=4000)
+    dev = [(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(Xs).cuda(), h)
+           for X, y, Xs, h in gps]
+    base = api.Batch(api.Context(0), dev, want_cov=True)
+    base.run()
+    ctx = api.Context(0, batch_order=order, batch_ctas_per_sm=ctas)
+    b = api.Batch(ctx, dev, want_cov=True)
+    b.run()
+    api.gp_sync(ctx)
+    torch.cuda.synchronize()
+    for g in range(len(gps)):
+        assert torch.equal(b.means[g], base.means[g]) and torch.equal(b.covs[g], base.covs[g])
+    b.free()
+    base.free()
