@@ -98,6 +98,7 @@ struct gp_factor {
   DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
   DevBuf Linv;                // inverses of the diagonal tiles of L (written by the Cholesky launch)
+  DevBuf Pk, PV;              // mixed mode with tensor cores: packed operands of the panel tiles and of V
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
   DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
                                   // sums, counters, L^{-1} y
@@ -166,6 +167,11 @@ gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
   a.withhold_task = c->cfg.withhold_enable ? c->cfg.withhold_task : -1;
   a.use_umma = (f->precision == GP_FP32 && c->cfg.tensor_cores >= 0) ? 1 : 0;
   return a;
+}
+
+// Mixed mode on the tensor cores keeps packed operands (tile edge a multiple of 128).
+bool packed_operands(const gp_ctx* c, const gp_factor* f) {
+  return f->precision == GP_FP32 && c->cfg.tensor_cores >= 0 && f->T % 128 == 0;
 }
 
 gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb, bool mixed) {
@@ -385,6 +391,8 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->bvec);
   release(f->cMean);
   release(f->Linv);
+  release(f->Pk);
+  release(f->PV);
   release(f->V);
   release(f->S);
   release(f->cCov);
@@ -439,9 +447,11 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, mixed, &tb));
   const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
   GP_TRY(grow(f->Linv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
+  if (packed_operands(c, f)) GP_TRY(grow(f->Pk, ntiles * f->T * f->T * sizeof(double)));
   GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
   gpk::DagArgs a = base_args(c, f);
   a.Linv = (double*)f->Linv.p;
+  if (packed_operands(c, f)) a.Pk = (uint8_t*)f->Pk.p;
   GP_TRY(run_dag(c, a, tb, mixed));
   f->factored = true;
   return GP_OK;
@@ -541,6 +551,11 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   a.lds = (long long)ldv;
   a.cV = (int*)f->cCov.p;
   a.cS = a.cV + (size_t)Mt * Mc;
+  if (packed_operands(c, f) && f->Pk.p) {
+    GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
+    a.Pk = (uint8_t*)f->Pk.p;
+    a.PV = (uint8_t*)f->PV.p;
+  }
   GP_TRY(run_dag(c, a, tb, mixed));
   GP_CUDA(gpk::launch_cov_copy((const double*)f->S.p, (long long)ldv, cov_out, m, c->stream));
   count_launch(c);
@@ -570,6 +585,11 @@ gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, d
   a.ldv = (long long)ldv;
   a.Mc = (int)Mc;
   a.cV = (int*)f->cCov.p;
+  if (packed_operands(c, f) && f->Pk.p) {
+    GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
+    a.Pk = (uint8_t*)f->Pk.p;
+    a.PV = (uint8_t*)f->PV.p;
+  }
   GP_TRY(run_dag(c, a, tb, mixed));
   GP_CUDA(gpk::launch_var_from_v((const double*)f->V.p, (long long)ldv, (long long)npad, f->h.v,
                                  c->cfg.noisy_prior ? f->h.s2 : 0.0, var_out, m, c->stream));

@@ -4,7 +4,7 @@
 #include <climits>
 
 #include "kernels.h"
-#include "umma.cuh"
+#include "umma_packed.cuh"
 
 namespace gpk {
 
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
   // Tensor-core path of the mixed trailing updates: TMEM accumulator and two mbarriers per CTA.
   constexpr bool kUmma = kMixed && !kRev;
   extern __shared__ __align__(1024) uint8_t dyn_smem[];
-  __shared__ uint64_t s_bar[2];
+  __shared__ uint64_t s_bar[2 + 2 * kPkStages];
   __shared__ uint32_t s_tmem;
   UmmaState um;
   const bool use_umma = kUmma && a0.use_umma;
@@ -221,8 +221,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       tmem_relinquish();
     }
     if (threadIdx.x == 0) {
-      mbar_init(&s_bar[0], 1);
-      mbar_init(&s_bar[1], 1);
+      for (int b = 0; b < 2 + 2 * kPkStages; ++b) mbar_init(&s_bar[b], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     umma_fence_before();
@@ -233,6 +232,9 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     um.tmem = s_tmem;
     um.phase[0] = um.phase[1] = 0;
     um.pending[0] = um.pending[1] = 0;
+    um.pfull = s_bar + 2;
+    um.pempty = s_bar + 2 + kPkStages;
+    for (int b = 0; b < kPkStages; ++b) um.fph[b] = um.eph[b] = um.fpend[b] = um.epend[b] = 0;
   }
   while (true) {
     if (threadIdx.x == 0) s_task = ld_relaxed(&a0.st->abort) ? INT_MAX : (int)atomicAdd(&a0.st->next_task, 1ull);
@@ -302,12 +304,27 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsm_right_f32(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, u.f);
         else
           cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
+        if (kUmma && a.Pk && T % kUmmaM == 0) {  // the panel tile in the operand format of its readers
+          __syncthreads();
+          cta_pack_operand(a.Kt + tri(p, q) * TT, T, false, T, T, a.Pk + tri(p, q) * TT * 8);
+        }
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
       case TASK_UPD: {  // K_IK -= sum_{J0 <= J < J1} L_IJ L_KJ^T (SYRK when I == K), J in increasing order
         const int J0 = r & 0xFFFF, J1 = (r >> 16) ? (r >> 16) : J0 + 1;
         double* C = a.Kt + tri(p, q) * TT;
-        if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
+        if (kUmma && use_umma && a.Pk && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
+          PkPairs pr;
+          pr.n = J1 - J0;
+          for (int J = J0; J < J1; ++J) {
+            pr.A[J - J0] = a.Pk + tri(p, J) * TT * 8;
+            pr.B[J - J0] = a.Pk + tri(q, J) * TT * 8;
+          }
+          if (!umma_pk_gemm_sub(um, C, T, pr, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
           UmmaPairs pr;
           pr.n = J1 - J0;
           for (int J = J0; J < J1; ++J) {
@@ -336,13 +353,26 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsm_left_f32(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, u.f);
         else
           cta_trsm_left(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, s);
+        if (kUmma && a.PV && T % kUmmaM == 0) {  // V_Jc is final: its transposed operand for V and W
+          __syncthreads();
+          cta_pack_operand(B, (int)a.ldv, true, T, T, a.PV + ((size_t)p * a.Mc + q) * TT * 8);
+        }
         cta_publish(a.cV + (size_t)p * a.Mc + q, p + 1);
         break;
       }
       case TASK_VGEMM: {
         double* C = a.V + (size_t)p * T * a.ldv + (size_t)r * T;
         const double* B = a.V + (size_t)q * T * a.ldv + (size_t)r * T;
-        if (kMixed)
+        if (kUmma && use_umma && a.Pk && a.PV && T % kUmmaM == 0) {  // V_Ic -= L_IJ V_Jc, packed operands
+          PkPairs pr;
+          pr.n = 1;
+          pr.A[0] = a.Pk + tri(p, q) * TT * 8;
+          pr.B[0] = a.PV + ((size_t)q * a.Mc + r) * TT * 8;
+          if (!umma_pk_gemm_sub(um, C, (int)a.ldv, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kMixed)
           cta_gemm_sub_f32<0, 1>(C, (int)a.ldv, a.Kt + tri(p, q) * TT, T, B, (int)a.ldv, T, T, T, false, u.f.g);
         else
           cta_gemm_sub<A_MK, B_KN>(C, (int)a.ldv, a.Kt + tri(p, q) * TT, T, B, (int)a.ldv, T, T, T, false, 0, s.g);
@@ -353,7 +383,16 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         double* C = a.S + (size_t)p * T * a.lds + (size_t)q * T;
         const double* Va = a.V + (size_t)r * T * a.ldv + (size_t)p * T;
         const double* Vb = a.V + (size_t)r * T * a.ldv + (size_t)q * T;
-        if (kMixed)
+        if (kUmma && use_umma && a.PV && T % kUmmaM == 0) {  // S_ab -= V_Ja^T V_Jb, packed operands
+          PkPairs pr;
+          pr.n = 1;
+          pr.A[0] = a.PV + ((size_t)r * a.Mc + p) * TT * 8;
+          pr.B[0] = a.PV + ((size_t)r * a.Mc + q) * TT * 8;
+          if (!umma_pk_gemm_sub(um, C, (int)a.lds, pr, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kMixed)
           cta_gemm_sub_f32<1, 1>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, u.f.g);
         else
           cta_gemm_sub<A_KM, B_KN>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, 0, s.g);

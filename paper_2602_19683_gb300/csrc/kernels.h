@@ -71,6 +71,9 @@ struct DagArgs {
   long long lds;
   double* bvec;     // Mt*T vector: y on entry, beta then alpha
   double* Linv;     // Mt x T x T: inverses of the diagonal tiles of L (null: solves by substitution)
+  uint8_t* Pk;      // mixed mode: packed tensor-core operands of the panel tiles L_IJ (I > J), same tile
+                    // index as Kt, T*T*8 bytes each (null: operands staged from FP64 per update)
+  uint8_t* PV;      // mixed mode: packed operands of the blocks V_Jc (transposed), (J*Mc + c)*T*T*8 bytes
   int nch;          // T / 32 (row chunks of the vector tasks)
   int* cK;          // per lower K tile: updates applied (J+1 once final)
   int* cV;          // per V tile

@@ -114,6 +114,12 @@ struct UmmaState {
   uint32_t tmem;       // TMEM base address (128 columns)
   uint32_t phase[2];   // next parity to wait for, per stage
   uint32_t pending[2]; // stage has an uncompleted commit
+  // packed-operand pipeline (umma_packed.cuh): per stage, a "full" barrier completed by the bulk
+  // copies' transaction bytes and an "empty" barrier completed by the MMA commit
+  uint64_t* pfull;
+  uint64_t* pempty;
+  uint32_t fph[2], eph[2];      // next parity to wait for
+  uint32_t fpend[2], epend[2];  // a copy / a commit is outstanding on the stage
 };
 
 // Waits (thread 0, bounded) until the MMAs committed to stage s have completed; the outcome is made
@@ -185,6 +191,8 @@ struct UmmaPairs {
   int n;
 };
 
+__device__ void umma_epilogue_sub(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower);
+
 __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs& pr, int lda, int ldb, int m0,
                                int n0, int K, bool lower, DevStatus* st, long long timeout_ns, long long where) {
   const int nkp = K / kUmmaKChunk, nk = nkp * pr.n;
@@ -227,9 +235,15 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs
     if (u.pending[s]) {
       if (!umma_stage_wait(u, s, st, timeout_ns, where)) return false;
     }
-  // epilogue: TMEM -> registers (warp w: lanes 32(w%4).., a 64-column half) -> smem (row-major, the
-  // operand stages are free now) -> coalesced FP64 read-modify-write of C (a warp per row, 4 columns
-  // per lane).
+  umma_epilogue_sub(u, C, ldc, m0, n0, lower);
+  return true;
+}
+
+// Epilogue of a 128 x 128 block whose MMAs are all complete: TMEM -> registers (warp w: lanes
+// 32(w%4).., a 64-column half) -> smem (row-major, the operand stages are free now) -> coalesced
+// FP64 read-modify-write of C (a warp per row, 4 columns per lane): C -= acc, only n <= m when lower.
+// Ends with __syncthreads().
+__device__ void umma_epilogue_sub(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower) {
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* acc_s = reinterpret_cast<float*>(u.smem);  // 128 x (128 + 4) floats
@@ -267,7 +281,6 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs
     c2[1] = c23;
   }
   __syncthreads();  // smem and TMEM are reused by the next block
-  return true;
 }
 
 // C[M x N] -= sum_p A_p B_p^T on the tensor cores for M, N multiples of 128 and K a multiple of 32;

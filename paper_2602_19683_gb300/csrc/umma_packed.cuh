@@ -1,0 +1,213 @@
+// Packed tensor-core operands of the mixed-precision mode, and the products fed from them by bulk
+// tensor-memory-access (TMA) copies.
+//
+// A tile that many trailing updates read (a panel tile L_IJ after its TRSM, a block V_Jc of the
+// covariance solve after its triangular solve) is converted ONCE into the operand format of the
+// tcgen05 3xTF32 product: each FP64 value is split into a TF32 high part and a TF32-rounded remainder,
+// and the halves are stored exactly as the MMA reads them from shared memory (K-major, 128-byte
+// swizzle, 8-row groups 1024 bytes apart). A packed R x Kd operand is a sequence of chunks, one per
+// (128-row block rb, 32-wide k block kc) in the order rb * (Kd / 32) + kc; a chunk is the 16 KB high
+// tile followed by the 16 KB low tile (32 KB, the same bytes per value as the FP64 source).
+//
+// A consumer then moves each 32 KB chunk into shared memory with one cp.async.bulk (no registers, no
+// conversion), completion counted on an mbarrier by bytes, and one thread issues the 12 MMAs of the
+// chunk as soon as its A and B halves have landed. Stages alternate so that the copies of the next
+// chunk fly while the tensor cores work on the current one. The accumulator (FP32 in TMEM) leaves
+// through the same epilogue as the register-staged path: subtracted from the FP64 C tile.
+//
+// Every wait is bounded; after a time-out the thread waits (bounded) for its own copies and MMAs in
+// flight so that shared memory and TMEM are quiet when the CTA leaves.
+#pragma once
+#include "umma.cuh"
+
+namespace gpk {
+
+constexpr int kPkChunkBytes = 2 * kUmmaTileBytes;  // high + low tile of one 128-row x 32-k chunk
+constexpr int kPkStages = 2;                        // each stage: A chunk + B chunk (64 KB)
+static_assert(kPkStages * 2 * kPkChunkBytes <= 2 * kUmmaStageBytes, "stages must fit the dynamic smem");
+
+__device__ __forceinline__ size_t pk_chunk_off(int rb, int kc, int Kd) {
+  return ((size_t)rb * (Kd / kUmmaKChunk) + kc) * kPkChunkBytes;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One bulk copy global -> shared (this CTA), completion signalled on bar as transaction bytes. Both
+// addresses 16-byte aligned, bytes a multiple of 16 (chunks are 32 KB at 32 KB offsets).
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Writes the packed operand of an R x Kd FP64 block: Op[r][k] = src[r * ld + k] (trans = false) or
+// src[k * ld + r] (trans = true). R a multiple of 128, Kd of 32. Loads are coalesced in both forms;
+// stores of the transposed form are one 128-byte packed row per warp instruction.
+__device__ void cta_pack_operand(const double* src, int ld, bool trans, int R, int Kd, uint8_t* dst) {
+  const int t = threadIdx.x;
+  for (int rb = 0; rb < R / kUmmaM; ++rb)
+    for (int kc = 0; kc < Kd / kUmmaKChunk; ++kc) {
+      uint8_t* hi = dst + pk_chunk_off(rb, kc, Kd);
+      uint8_t* lo = hi + kUmmaTileBytes;
+      if (!trans) {
+        const int kp = t & 15, rr = t >> 4;
+        double2 d[8];
+#pragma unroll
+        for (int pass = 0; pass < 8; ++pass)
+          d[pass] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(rb * kUmmaM + rr + 16 * pass) * ld +
+                                                            kc * kUmmaKChunk) + kp);
+#pragma unroll
+        for (int pass = 0; pass < 8; ++pass) {
+          const float f0 = f64_to_f32_rn(d[pass].x), f1 = f64_to_f32_rn(d[pass].y);
+          const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
+          const uint32_t off = sw128_offset(rr + 16 * pass, 2 * kp);
+          *reinterpret_cast<float2*>(hi + off) = make_float2(h0, h1);
+          *reinterpret_cast<float2*>(lo + off) = make_float2(tf32_rn(f0 - h0), tf32_rn(f1 - h1));
+        }
+      } else {
+        const int k = t & 31, w = t >> 5;  // lane: k row of the source; warp: 16 consecutive r
+        double2 d[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          d[q] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(kc * kUmmaKChunk + k) * ld + rb * kUmmaM +
+                                                         w * 16) + q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float f = f64_to_f32_rn(e ? d[q].y : d[q].x), h = tf32_rn(f);
+            const uint32_t off = sw128_offset(w * 16 + 2 * q + e, k);
+            *reinterpret_cast<float*>(hi + off) = h;
+            *reinterpret_cast<float*>(lo + off) = tf32_rn(f - h);
+          }
+        }
+      }
+    }
+  fence_proxy_async_global();  // the bytes are read later by bulk copies (async proxy)
+  __syncthreads();
+}
+
+// Operand pairs of a packed product: C -= sum_p A_p B_p^T, each A_p / B_p a packed T-row operand.
+struct PkPairs {
+  const uint8_t* A[kUmmaMaxPairs];
+  const uint8_t* B[kUmmaMaxPairs];
+  int n;
+};
+
+// Thread 0: bounded wait without raising an error (used while draining after a time-out).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long long timeout_ns) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity) && (long long)(globaltimer() - t0) < timeout_ns) {
+  }
+}
+
+// C[128 x 128 block at (m0, n0)] (FP64, ldc) -= sum_p A_p[m0..] B_p[n0..]^T over Kd, from packed
+// operands. Thread 0 runs the copy/MMA pipeline; all threads run the epilogue. Returns false (error
+// raised, copies and MMAs drained) on a time-out.
+__device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int m0, int n0,
+                                  bool lower, DevStatus* st, long long timeout_ns, long long where) {
+  const int nkp = Kd / kUmmaKChunk, nk = nkp * pr.n;
+  const int rbA = m0 / kUmmaM, rbB = n0 / kUmmaN;
+  bool ok = true;
+  fence_async_smem();  // earlier generic use of the stage memory (other tile routines) before the copies
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();  // tiles acquired through the dependency counters feed bulk copies
+    auto load = [&](int i) {
+      const int s = i % kPkStages, p = i / nkp, kc = i % nkp;
+      uint8_t* base = u.smem + s * 2 * kPkChunkBytes;
+      mbar_expect_tx(&u.pfull[s], 2 * kPkChunkBytes);
+      tma_bulk_g2s(base, pr.A[p] + pk_chunk_off(rbA, kc, Kd), kPkChunkBytes, &u.pfull[s]);
+      tma_bulk_g2s(base + kPkChunkBytes, pr.B[p] + pk_chunk_off(rbB, kc, Kd), kPkChunkBytes, &u.pfull[s]);
+      u.fpend[s] = 1;
+    };
+    for (int i = 0; i < nk && i < kPkStages; ++i) load(i);
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % kPkStages;
+      if (!mbar_wait(&u.pfull[s], u.fph[s], st, timeout_ns, where)) {
+        ok = false;
+        break;
+      }
+      u.fph[s] ^= 1u;
+      u.fpend[s] = 0;
+      umma_fence_after();
+      const uint32_t a_hi = smem_u32(u.smem + s * 2 * kPkChunkBytes), a_lo = a_hi + kUmmaTileBytes;
+      const uint32_t b_hi = a_hi + kPkChunkBytes, b_lo = b_hi + kUmmaTileBytes;
+#pragma unroll
+      for (int ks = 0; ks < kUmmaKChunk / 8; ++ks) {
+        const uint32_t o = ks * 32;
+        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_hi + o), (i > 0 || ks > 0) ? 1u : 0u);
+        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
+        umma_tf32(u.tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
+      }
+      umma_commit(&u.pempty[s]);
+      u.epend[s] = 1;
+      if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
+        const int sp = (i - 1) % kPkStages, j = i - 1 + kPkStages;
+        if (j < nk) {
+          if (!mbar_wait(&u.pempty[sp], u.eph[sp], st, timeout_ns, where)) {
+            ok = false;
+            break;
+          }
+          u.eph[sp] ^= 1u;
+          u.epend[sp] = 0;
+          load(j);
+        }
+      }
+    }
+    // every MMA of the block must be complete before TMEM is read (and before the stages are reused)
+    for (int i = 0; i < kPkStages; ++i) {
+      const int s = (nk + i) % kPkStages;  // oldest outstanding commit first
+      if (u.epend[s]) {
+        if (ok) {
+          ok = mbar_wait(&u.pempty[s], u.eph[s], st, timeout_ns, where);
+        } else {
+          mbar_drain(&u.pempty[s], u.eph[s], timeout_ns);
+        }
+        u.eph[s] ^= 1u;
+        u.epend[s] = 0;
+      }
+    }
+    if (!ok) {
+      for (int s = 0; s < kPkStages; ++s)
+        if (u.fpend[s]) {
+          mbar_drain(&u.pfull[s], u.fph[s], timeout_ns);
+          u.fph[s] ^= 1u;
+          u.fpend[s] = 0;
+        }
+      for (int s = 0; s < kPkStages; ++s)
+        if (u.epend[s]) {
+          mbar_drain(&u.pempty[s], u.eph[s], timeout_ns);
+          u.eph[s] ^= 1u;
+          u.epend[s] = 0;
+        }
+    }
+  }
+  if (__syncthreads_or(!ok)) return false;
+  umma_epilogue_sub(u, C, ldc, m0, n0, lower);
+  fence_async_smem();  // generic smem traffic of the epilogue before the next bulk copies
+  __syncthreads();
+  return true;
+}
+
+// C[M x N] -= sum_p A_p B_p^T from packed operands (M, N multiples of 128; Kd of 32); lower skips the
+// blocks above the diagonal and masks the diagonal blocks. False on a time-out.
+__device__ bool umma_pk_gemm_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int M, int N, bool lower,
+                                 DevStatus* st, long long timeout_ns, long long where) {
+  for (int m0 = 0; m0 < M; m0 += kUmmaM)
+    for (int n0 = 0; n0 < N; n0 += kUmmaN) {
+      if (lower && n0 > m0) continue;
+      if (!umma_pk_block_sub(u, C, ldc, pr, Kd, m0, n0, lower && n0 == m0, st, timeout_ns, where)) return false;
+    }
+  return true;
+}
+
+}  // namespace gpk
