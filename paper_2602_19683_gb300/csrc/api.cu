@@ -99,6 +99,7 @@ struct gp_factor {
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
   DevBuf Linv;                // inverses of the diagonal tiles of L (written by the Cholesky launch)
   DevBuf Pk, PV;              // mixed mode with tensor cores: packed operands of the panel tiles and of V
+  DevBuf PLinv;               // mixed mode, T = 128: packed FP32 inverses of the diagonal tiles
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
   DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
                                   // sums, counters, L^{-1} y
@@ -111,8 +112,11 @@ namespace {
 
 void count_launch(gp_ctx* c, int k = 1) { c->launches += k; }
 
-int auto_tile(long long n) {
-  if (n >= 16384) return 256;
+// Default tile edge. FP64: 256 from n = 16384 (the FP64 pipe, not the critical path, bounds the
+// factorisation there). Mixed mode on the tensor cores: 128 from n = 2048, where the FP64 POTRF of a
+// diagonal tile (its cost grows as T^3 per step, T^2 over the whole critical path) dominates.
+int auto_tile(long long n, bool mixed_tc) {
+  if (n >= 16384 && !mixed_tc) return 256;
   if (n >= 2048) return 128;
   if (n >= 256) return 64;
   return 32;
@@ -393,6 +397,7 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->Linv);
   release(f->Pk);
   release(f->PV);
+  release(f->PLinv);
   release(f->V);
   release(f->S);
   release(f->cCov);
@@ -403,7 +408,7 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
 gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper h, gp_factor** K_out) {
   if (!c || !K_out || !X || n < 1 || D < 1 || D > 4096 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
-  const int T = c->cfg.tile ? c->cfg.tile : auto_tile(n);
+  const int T = c->cfg.tile ? c->cfg.tile : auto_tile(n, c->cfg.precision == GP_FP32 && c->cfg.tensor_cores >= 0);
   const long long Mt = (n + T - 1) / T;
   if (Mt > 46340) return GP_ERR_INVALID_ARG;  // packed tile index must fit int arithmetic
   gp_factor* f = *K_out;
@@ -448,10 +453,12 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
   GP_TRY(grow(f->Linv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
   if (packed_operands(c, f)) GP_TRY(grow(f->Pk, ntiles * f->T * f->T * sizeof(double)));
+  if (packed_operands(c, f) && f->T == 128) GP_TRY(grow(f->PLinv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
   GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
   gpk::DagArgs a = base_args(c, f);
   a.Linv = (double*)f->Linv.p;
   if (packed_operands(c, f)) a.Pk = (uint8_t*)f->Pk.p;
+  if (packed_operands(c, f) && f->T == 128) a.PLinv = (uint8_t*)f->PLinv.p;
   GP_TRY(run_dag(c, a, tb, mixed));
   f->factored = true;
   return GP_OK;
@@ -555,6 +562,7 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
     GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
     a.Pk = (uint8_t*)f->Pk.p;
     a.PV = (uint8_t*)f->PV.p;
+    a.PLinv = f->T == 128 ? (uint8_t*)f->PLinv.p : nullptr;
   }
   GP_TRY(run_dag(c, a, tb, mixed));
   GP_CUDA(gpk::launch_cov_copy((const double*)f->S.p, (long long)ldv, cov_out, m, c->stream));
@@ -589,6 +597,7 @@ gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, d
     GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
     a.Pk = (uint8_t*)f->Pk.p;
     a.PV = (uint8_t*)f->PV.p;
+    a.PLinv = f->T == 128 ? (uint8_t*)f->PLinv.p : nullptr;
   }
   GP_TRY(run_dag(c, a, tb, mixed));
   GP_CUDA(gpk::launch_var_from_v((const double*)f->V.p, (long long)ldv, (long long)npad, f->h.v,

@@ -296,11 +296,27 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           aborted = true;
           break;
         }
+        if (kUmma && use_umma && a.PLinv && T == kUmmaM)  // FP32 inverse for the column's TRSMs and V solves
+          cta_inverse_pack(a.Kt + tri(p, p) * TT, T, T, reinterpret_cast<float*>(um.smem), a.PLinv + p * TT * 8);
         cta_publish(a.cK + tri(p, p), p + 1);
         break;
       }
       case TASK_TRSM:
-        if (kMixed && q > 0)
+        if (kUmma && use_umma && q > 0 && a.PLinv && a.Pk && T == kUmmaM) {
+          // L_IJ = K_IJ X_J^T on the tensor cores, X_J the packed inverse of L_JJ (K_IJ packed first,
+          // in the slot that then receives L_IJ)
+          double* Kij = a.Kt + tri(p, q) * TT;
+          uint8_t* Pij = a.Pk + tri(p, q) * TT * 8;
+          cta_pack_operand(Kij, T, false, T, T, Pij);
+          PkPairs pr;
+          pr.n = 1;
+          pr.A[0] = Pij;
+          pr.B[0] = a.PLinv + (size_t)q * TT * 8;
+          if (!umma_pk_gemm_sub<true>(um, Kij, T, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kMixed && q > 0)
           cta_trsm_right_f32(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, u.f);
         else
           cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
@@ -349,7 +365,20 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       }
       case TASK_VTRSM: {
         double* B = a.V + (size_t)p * T * a.ldv + (size_t)q * T;
-        if (kMixed)
+        if (kUmma && use_umma && a.PLinv && a.PV && T == kUmmaM) {
+          // V_Jc = X_J V_Jc on the tensor cores (V_Jc packed transposed first, in the slot that then
+          // receives the solved block)
+          uint8_t* Pjc = a.PV + ((size_t)p * a.Mc + q) * TT * 8;
+          cta_pack_operand(B, (int)a.ldv, true, T, T, Pjc);
+          PkPairs pr;
+          pr.n = 1;
+          pr.A[0] = a.PLinv + (size_t)p * TT * 8;
+          pr.B[0] = Pjc;
+          if (!umma_pk_gemm_sub<true>(um, B, (int)a.ldv, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+            aborted = true;
+            break;
+          }
+        } else if (kMixed)
           cta_trsm_left_f32(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, u.f);
         else
           cta_trsm_left(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, s);

@@ -74,6 +74,8 @@ struct DagArgs {
   uint8_t* Pk;      // mixed mode: packed tensor-core operands of the panel tiles L_IJ (I > J), same tile
                     // index as Kt, T*T*8 bytes each (null: operands staged from FP64 per update)
   uint8_t* PV;      // mixed mode: packed operands of the blocks V_Jc (transposed), (J*Mc + c)*T*T*8 bytes
+  uint8_t* PLinv;   // mixed mode, T = 128: packed FP32 inverses of the diagonal tiles, J*T*T*8 bytes (null:
+                    // the later panel TRSMs and the V solves run as FP32 substitutions)
   int nch;          // T / 32 (row chunks of the vector tasks)
   int* cK;          // per lower K tile: updates applied (J+1 once final)
   int* cV;          // per V tile

@@ -243,11 +243,26 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs
 // 32(w%4).., a 64-column half) -> smem (row-major, the operand stages are free now) -> coalesced
 // FP64 read-modify-write of C (a warp per row, 4 columns per lane): C -= acc, only n <= m when lower.
 // Ends with __syncthreads().
-__device__ void umma_epilogue_sub(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower) {
+template <bool kStore>
+__device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower) {
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* acc_s = reinterpret_cast<float*>(u.smem);  // 128 x (128 + 4) floats
   constexpr int ldacc = kUmmaN + 4;
+  constexpr int kRows = kUmmaM / (kThreads / 32);    // rows per warp: w, w + 8, ...
+  constexpr int kBatch = 8;                          // rows whose C loads are in flight together
+  const int n = n0 + 4 * lane;
+  double2 c[kBatch][2];
+  auto load_batch = [&](int b) {
+    if (kStore) return;
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) {
+      const double2* c2 = reinterpret_cast<const double2*>(C + (size_t)(m0 + w + 8 * (b * kBatch + i)) * ldc + n);
+      c[i][0] = __ldcg(c2);
+      c[i][1] = __ldcg(c2 + 1);
+    }
+  };
+  load_batch(0);  // the first rows of C fly while the accumulator is staged
   {
     const int row = (w & 3) * 32 + lane, colh = (w >> 2) * 64;
 #pragma unroll
@@ -261,26 +276,41 @@ __device__ void umma_epilogue_sub(UmmaState& u, double* C, int ldc, int m0, int 
   }
   umma_fence_before();
   __syncthreads();
-  for (int r = w; r < kUmmaM; r += kThreads / 32) {
-    const int m = m0 + r, n = n0 + 4 * lane;
-    const float4 a = *reinterpret_cast<const float4*>(acc_s + r * ldacc + 4 * lane);
-    double2* c2 = reinterpret_cast<double2*>(C + (size_t)m * ldc + n);
-    double2 c01 = __ldcg(c2), c23 = __ldcg(c2 + 1);
-    if (!lower || n + 3 <= m) {
-      c01.x -= f32_to_f64(a.x);
-      c01.y -= f32_to_f64(a.y);
-      c23.x -= f32_to_f64(a.z);
-      c23.y -= f32_to_f64(a.w);
-    } else {
-      if (n <= m) c01.x -= f32_to_f64(a.x);
-      if (n + 1 <= m) c01.y -= f32_to_f64(a.y);
-      if (n + 2 <= m) c23.x -= f32_to_f64(a.z);
-      if (n + 3 <= m) c23.y -= f32_to_f64(a.w);
+  for (int b = 0; b < kRows / kBatch; ++b) {
+    if (b > 0) load_batch(b);
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) {
+      const int r = w + 8 * (b * kBatch + i), m = m0 + r;
+      const float4 a = *reinterpret_cast<const float4*>(acc_s + r * ldacc + 4 * lane);
+      double2* c2 = reinterpret_cast<double2*>(C + (size_t)m * ldc + n);
+      double2 c01, c23;
+      if (kStore) {  // C = acc (every entry)
+        c01 = make_double2(f32_to_f64(a.x), f32_to_f64(a.y));
+        c23 = make_double2(f32_to_f64(a.z), f32_to_f64(a.w));
+      } else {
+        c01 = c[i][0];
+        c23 = c[i][1];
+        if (!lower || n + 3 <= m) {
+          c01.x -= f32_to_f64(a.x);
+          c01.y -= f32_to_f64(a.y);
+          c23.x -= f32_to_f64(a.z);
+          c23.y -= f32_to_f64(a.w);
+        } else {
+          if (n <= m) c01.x -= f32_to_f64(a.x);
+          if (n + 1 <= m) c01.y -= f32_to_f64(a.y);
+          if (n + 2 <= m) c23.x -= f32_to_f64(a.z);
+          if (n + 3 <= m) c23.y -= f32_to_f64(a.w);
+        }
+      }
+      c2[0] = c01;
+      c2[1] = c23;
     }
-    c2[0] = c01;
-    c2[1] = c23;
   }
   __syncthreads();  // smem and TMEM are reused by the next block
+}
+
+__device__ void umma_epilogue_sub(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower) {
+  umma_epilogue<false>(u, C, ldc, m0, n0, lower);
 }
 
 // C[M x N] -= sum_p A_p B_p^T on the tensor cores for M, N multiples of 128 and K a multiple of 32;

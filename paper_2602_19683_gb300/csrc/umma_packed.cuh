@@ -112,6 +112,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long 
 // C[128 x 128 block at (m0, n0)] (FP64, ldc) -= sum_p A_p[m0..] B_p[n0..]^T over Kd, from packed
 // operands. Thread 0 runs the copy/MMA pipeline; all threads run the epilogue. Returns false (error
 // raised, copies and MMAs drained) on a time-out.
+template <bool kStore = false>
 __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int m0, int n0,
                                   bool lower, DevStatus* st, long long timeout_ns, long long where) {
   const int nkp = Kd / kUmmaKChunk, nk = nkp * pr.n;
@@ -192,22 +193,113 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
     }
   }
   if (__syncthreads_or(!ok)) return false;
-  umma_epilogue_sub(u, C, ldc, m0, n0, lower);
+  umma_epilogue<kStore>(u, C, ldc, m0, n0, lower);
   fence_async_smem();  // generic smem traffic of the epilogue before the next bulk copies
   __syncthreads();
   return true;
 }
 
 // C[M x N] -= sum_p A_p B_p^T from packed operands (M, N multiples of 128; Kd of 32); lower skips the
-// blocks above the diagonal and masks the diagonal blocks. False on a time-out.
+// blocks above the diagonal and masks the diagonal blocks. kStore: C = sum_p A_p B_p^T instead (every
+// entry written; lower must be false). False on a time-out.
+template <bool kStore = false>
 __device__ bool umma_pk_gemm_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int M, int N, bool lower,
                                  DevStatus* st, long long timeout_ns, long long where) {
   for (int m0 = 0; m0 < M; m0 += kUmmaM)
     for (int n0 = 0; n0 < N; n0 += kUmmaN) {
       if (lower && n0 > m0) continue;
-      if (!umma_pk_block_sub(u, C, ldc, pr, Kd, m0, n0, lower && n0 == m0, st, timeout_ns, where)) return false;
+      if (!umma_pk_block_sub<kStore>(u, C, ldc, pr, Kd, m0, n0, lower && n0 == m0, st, timeout_ns, where)) return false;
     }
   return true;
+}
+
+// ---------------------------------------------------------------- the inverse of a diagonal tile
+
+// X = L^{-1} in FP32 for a factored nb x nb diagonal tile L (FP64, global; nb a multiple of 32, at most
+// 128), written as the packed operand Op[r][k] = X[r][k] (upper triangle zero). It turns the TRSMs of
+// the tile's block column (L_IJ = K_IJ X^T) and the diagonal-block solves of the covariance
+// (V_Jc <- X V_Jc) into tensor-core products. Blocked by 32: warp d inverts diagonal block d (lane j
+// solves column j), then block rows i = 1.. follow X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
+// sm: (2 nb (nb + 1)) floats of shared memory.
+__device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, uint8_t* dst) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int ld = nb + 1, nblk = nb / 32;
+  float* Ls = sm;
+  float* Xs = sm + nb * ld;
+  for (int e = t; e < nb * nb; e += kThreads) {
+    const int i = e / nb, j = e % nb;
+    Ls[i * ld + j] = (j <= i) ? f64_to_f32_rn(ldcg(L + (size_t)i * ldl + j)) : 0.f;
+    Xs[i * ld + j] = 0.f;
+  }
+  __syncthreads();
+  if (w < nblk) {  // diagonal blocks
+    const int d0 = 32 * w;
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float acc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc = fmaf(-Ls[(d0 + i) * ld + d0 + k], x[k], acc);
+      x[i] = acc / Ls[(d0 + i) * ld + d0 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Xs[(d0 + i) * ld + d0 + lane] = x[i];
+  }
+  __syncthreads();
+  for (int bi = 1; bi < nblk; ++bi) {
+    // W_bj = sum_{bj <= k < bi} L_{bi,k} X_{k,bj}, parked in the (still zero) slots X_{bi,bj}
+    for (int e = t; e < bi * 1024; e += kThreads) {
+      const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+      const float* lrow = Ls + (32 * bi + r) * ld;
+      float acc = 0.f;
+      for (int kk = 32 * bj; kk < 32 * bi; ++kk) acc = fmaf(lrow[kk], Xs[kk * ld + 32 * bj + c], acc);
+      Xs[(32 * bi + r) * ld + 32 * bj + c] = acc;
+    }
+    __syncthreads();
+    // X_{bi,bj} = -X_{bi,bi} W_bj (through registers: W is read in place)
+    float res[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const int e = t + q * kThreads;
+      res[q] = 0.f;
+      if (e < bi * 1024) {
+        const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        const float* xrow = Xs + (32 * bi + r) * ld + 32 * bi;
+        float acc = 0.f;
+        for (int k = 0; k <= r; ++k) acc = fmaf(xrow[k], Xs[(32 * bi + k) * ld + 32 * bj + c], acc);
+        res[q] = -acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const int e = t + q * kThreads;
+      if (e < bi * 1024) {
+        const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        Xs[(32 * bi + r) * ld + 32 * bj + c] = res[q];
+      }
+    }
+    __syncthreads();
+  }
+  // packed operand rows r, k-chunks of 32 (one 128-row block)
+  for (int kc = 0; kc < nb / kUmmaKChunk; ++kc) {
+    uint8_t* hi = dst + pk_chunk_off(0, kc, nb);
+    uint8_t* lo = hi + kUmmaTileBytes;
+    for (int e = t; e < kUmmaM * 16; e += kThreads) {  // pairs (r, 2 kp), rows beyond nb are zero
+      const int r = e >> 4, kp = e & 15;
+      float f0 = 0.f, f1 = 0.f;
+      if (r < nb) {
+        f0 = Xs[r * ld + kc * kUmmaKChunk + 2 * kp];
+        f1 = Xs[r * ld + kc * kUmmaKChunk + 2 * kp + 1];
+      }
+      const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
+      const uint32_t off = sw128_offset(r, 2 * kp);
+      *reinterpret_cast<float2*>(hi + off) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(lo + off) = make_float2(tf32_rn(f0 - h0), tf32_rn(f1 - h1));
+    }
+  }
+  fence_proxy_async_global();
+  __syncthreads();
 }
 
 }  // namespace gpk
