@@ -424,8 +424,8 @@ def traced_cholesky(api, local, Xd, h, args):
     ncta = len(np.unique(rows[:, 4]))
     out = {"span_ms": float(span), "ctas": int(ncta),
            "busy_frac": float((rows[:, 7] - rows[:, 6]).sum() / 1e6 / (ncta * span))}
-    for k in np.unique(rows[:, 0] & 15):
-        sel = rows[(rows[:, 0] & 15) == k]
+    for k in np.unique(rows[:, 0] & 31):
+        sel = rows[(rows[:, 0] & 31) == k]
         out[api.TASK_NAMES[k]] = {"count": int(len(sel)), "run_us": float(((sel[:, 7] - sel[:, 6]) / 1e3).mean()),
                                   "wait_us": float(((sel[:, 6] - sel[:, 5]) / 1e3).mean())}
     f.free()

@@ -248,14 +248,16 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
  * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J), 14 TRTRI(J): the FP64 inverse of the factored diagonal tile
- * J, which the vector solves of gp_predict_mean apply as a matrix-vector product) into out (host, room
+ * J, which the vector solves of gp_predict_mean apply as a matrix-vector product, 15 VGEMM(I,c,J0|J1<<16)
+ * and 16 WSYRK(a,b,J0|J1<<16): products of columns J0..J1-1 applied in one pass, mixed mode with
+ * 128-multiple tiles) into out (host, room
  * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap);
 
 /* Task trace of the last persistent-kernel launch on this context (cfg.trace = 1): for each task in
  * dispatch order, {kind, p, q, r} as gp_schedule_tasks describes them (batched launches carry the GP
- * index in kind's bits 4 and up) followed by {CTA, t_taken, t_ready, t_done} in ns of %globaltimer,
+ * index in kind's bits 5 and up) followed by {CTA, t_taken, t_ready, t_done} in ns of %globaltimer,
  * 8 int64 per task, into out (host, room for cap tasks). Waits for the stream. Returns the task
  * count, or -1 when tracing is off or nothing was traced. */
 int64_t gp_trace(gp_ctx* ctx, int64_t* out, int64_t cap);

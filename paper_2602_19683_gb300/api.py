@@ -120,7 +120,7 @@ class Factor:
 
 
 TASK_NAMES = ["POTRF", "TRSM", "UPDATE", "VTRSM", "VGEMM", "WSYRK", "FSOLVE", "FGEMV", "BSOLVE", "BGEMV",
-              "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI"]
+              "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI", "VGEMM_G", "WSYRK_G"]
 
 
 def gp_trace(ctx: Context):
@@ -141,7 +141,7 @@ def trace_to_chrome(rows, path: str):
     t0 = int(rows[:, 5].min())
     ev = []
     for kind, p, q, r, cta, tt, tr, td in rows.tolist():
-        name = f"{TASK_NAMES[kind & 15]}({p},{q},{r})" + (f" gp{kind >> 4}" if kind >> 4 else "")
+        name = f"{TASK_NAMES[kind & 31]}({p},{q},{r})" + (f" gp{kind >> 5}" if kind >> 5 else "")
         ev.append({"name": "wait", "ph": "X", "pid": 0, "tid": cta, "ts": (tt - t0) / 1e3, "dur": (tr - tt) / 1e3})
         ev.append({"name": name, "ph": "X", "pid": 0, "tid": cta, "ts": (tr - t0) / 1e3, "dur": (td - tr) / 1e3})
     with open(path, "w") as fh:

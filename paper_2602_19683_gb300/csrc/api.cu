@@ -143,7 +143,7 @@ gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, cons
     std::vector<gpk::Task4> v;
     const gpk::CostModel cm = cost_model(c, mixed, T);
     if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
-    if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
+    if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);  // grouped products when cm says so
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
     if (kind == 3) v = gpk::cholesky_adjoint_tasks(Mt, T, workers, cm);
     if (kind == 4) v = gpk::cov_tasks(Mt, Mc, T, workers, cm, false);
@@ -714,7 +714,7 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     if (!d.X || !d.y || d.n < 1 || d.D < 1 || d.m < 0 || (d.m > 0 && (!d.Xs || !d.mean_out)) || !valid_hyper(d.h))
       return GP_ERR_INVALID_ARG;
     if (d.tile != 0 && (d.tile < 32 || d.tile > 1024 || d.tile % 32)) return GP_ERR_INVALID_ARG;
-    if (g >= (1 << 27)) return GP_ERR_INVALID_ARG;
+    if (g >= (1 << 26)) return GP_ERR_INVALID_ARG;  // GP index above the 5 task-kind bits
   }
   GP_CUDA(cudaSetDevice(c->device));
   const bool mixed = c->cfg.precision == GP_FP32;

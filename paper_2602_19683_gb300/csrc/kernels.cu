@@ -148,6 +148,20 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
     case TASK_VGEMM:  // (I=p, J=q, c=r)
       return wait_ge(a.cK + tri(p, q), q + 1, st, to, ti) && wait_ge(a.cV + (size_t)q * a.Mc + r, q + 1, st, to, ti) &&
              wait_ge(a.cV + (size_t)p * a.Mc + r, q, st, to, ti);
+    case TASK_VGEMM_G: {  // (I=p, c=q, J0 | J1 << 16)
+      const int J0 = r & 0xFFFF, J1 = r >> 16;
+      for (int J = J0; J < J1; ++J)
+        if (!wait_ge(a.cK + tri(p, J), J + 1, st, to, ti) || !wait_ge(a.cV + (size_t)J * a.Mc + q, J + 1, st, to, ti))
+          return false;
+      return wait_ge(a.cV + (size_t)p * a.Mc + q, J0, st, to, ti);
+    }
+    case TASK_WSYRK_G: {  // (a=p, b=q, J0 | J1 << 16)
+      const int J0 = r & 0xFFFF, J1 = r >> 16;
+      for (int J = J0; J < J1; ++J)
+        if (!wait_ge(a.cV + (size_t)J * a.Mc + p, J + 1, st, to, ti) || !wait_ge(a.cV + (size_t)J * a.Mc + q, J + 1, st, to, ti))
+          return false;
+      return wait_ge(a.cS + tri(p, q), J0, st, to, ti);
+    }
     case TASK_WSYRK:  // (a=p, b=q, J=r)
       return wait_ge(a.cV + (size_t)r * a.Mc + p, r + 1, st, to, ti) &&
              wait_ge(a.cV + (size_t)r * a.Mc + q, r + 1, st, to, ti) && wait_ge(a.cS + tri(p, q), r, st, to, ti);
@@ -201,16 +215,31 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
 // high bits of its kind, and the CTA takes that GP's pointers and sizes from the descriptor table.
 template <bool kMixed, bool kRev, bool kBatch>
 __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a0) {
-  __shared__ union {
+  union __align__(16) TileScratch {
     TileSmem d;
     TileSmemF32 f;
-  } u;
-  __shared__ int s_task;
-  __shared__ double s_red[kThreads / 32][32];
-  TileSmem& s = u.d;
-  // Tensor-core path of the mixed trailing updates: TMEM accumulator and two mbarriers per CTA.
+  };
+  static_assert(alignof(TileScratch) >= 16, "the tile routines read their scratch with 16-byte vector loads");
+  // Tensor-core path of the mixed trailing updates: TMEM accumulator and mbarriers per CTA.
   constexpr bool kUmma = kMixed && !kRev;
   extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  TileScratch* up;
+  if constexpr (kUmma) {
+    // the tile routines' scratch aliases the tensor-core stages: a task uses one or the other
+    up = reinterpret_cast<TileScratch*>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+  } else {
+    __shared__ TileScratch u_static;
+    up = &u_static;
+  }
+  TileScratch& u = *up;
+  if (((uintptr_t)up & 15) != 0) {  // guard: the layout above must keep the scratch 16-byte aligned
+    if (threadIdx.x == 0) raise_error(a0.st, GP_ERR_CUDA, -1);
+    return;
+  }
+  __shared__ int s_task;
+  __shared__ int s_flag;
+  __shared__ double s_red[kThreads / 32][32];
+  TileSmem& s = u.d;
   __shared__ uint64_t s_bar[2 + 2 * kPkStages];
   __shared__ uint32_t s_tmem;
   UmmaState um;
@@ -289,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       case TASK_POTRF: {
         const int fail = (kUmma && use_umma && T <= 128)
                              ? cta_potrf_smem(a.Kt + tri(p, p) * TT, T, T, reinterpret_cast<double*>(um.smem),
-                                              &s_red[0][0], &s.flag)
+                                              &s_red[0][0], &s_flag)
                              : cta_potrf<kMixed>(a.Kt + tri(p, p) * TT, T, T, s);
         if (fail) {
           if (threadIdx.x == 0) raise_error(a.st, GP_ERR_NOT_PD, gp_tag + (long long)p * T + fail);
@@ -426,6 +455,44 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         else
           cta_gemm_sub<A_KM, B_KN>(C, (int)a.lds, Va, (int)a.ldv, Vb, (int)a.ldv, T, T, T, p == q, 0, s.g);
         cta_publish(a.cS + tri(p, q), r + 1);
+        break;
+      }
+      case TASK_VGEMM_G:    // V_Ic -= sum_J L_IJ V_Jc (packed operands, one pass over V_Ic)
+      case TASK_WSYRK_G: {  // S_ab -= sum_J V_Ja^T V_Jb
+        const int J0 = r & 0xFFFF, J1 = r >> 16;
+        if (!(kUmma && use_umma && a.PV && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs &&
+              (tk.x == TASK_WSYRK_G || a.Pk))) {  // the host schedules these only for that path
+          if (threadIdx.x == 0) raise_error(a.st, GP_ERR_INVALID_ARG, ti);
+          aborted = true;
+          break;
+        }
+        PkPairs pr;
+        pr.n = J1 - J0;
+        double* C;
+        int ldc;
+        if (tk.x == TASK_VGEMM_G) {
+          C = a.V + (size_t)p * T * a.ldv + (size_t)q * T;
+          ldc = (int)a.ldv;
+          for (int J = J0; J < J1; ++J) {
+            pr.A[J - J0] = a.Pk + tri(p, J) * TT * 8;
+            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * 8;
+          }
+        } else {
+          C = a.S + (size_t)p * T * a.lds + (size_t)q * T;
+          ldc = (int)a.lds;
+          for (int J = J0; J < J1; ++J) {
+            pr.A[J - J0] = a.PV + ((size_t)J * a.Mc + p) * TT * 8;
+            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * 8;
+          }
+        }
+        if (!umma_pk_gemm_sub(um, C, ldc, pr, T, T, T, tk.x == TASK_WSYRK_G && p == q, a.st, a.timeout_ns, ti)) {
+          aborted = true;
+          break;
+        }
+        if (tk.x == TASK_VGEMM_G)
+          cta_publish(a.cV + (size_t)p * a.Mc + q, J1);
+        else
+          cta_publish(a.cS + tri(p, q), J1);
         break;
       }
       case TASK_FSOLVE:
@@ -983,11 +1050,17 @@ cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long r
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of the forward mixed kernel: the tensor-core stages, or (without the tensor
+// cores) just the tile routines' scratch, which lives there in both cases.
+static int mixed_dyn_smem(int use_umma) {
+  return use_umma ? kUmmaSmemBytes : (int)(sizeof(TileSmem) > sizeof(TileSmemF32) ? sizeof(TileSmem) : sizeof(TileSmemF32)) + 1024;
+}
+
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse, bool batch) {
   if (a.ntasks == 0) return cudaSuccess;
   if (batch) {
     if (mixed)
-      dag_kernel<true, false, true><<<grid, kThreads, a.use_umma ? kUmmaSmemBytes : 0, st>>>(a);
+      dag_kernel<true, false, true><<<grid, kThreads, mixed_dyn_smem(a.use_umma), st>>>(a);
     else
       dag_kernel<false, false, true><<<grid, kThreads, 0, st>>>(a);
   } else if (reverse) {
@@ -997,7 +1070,7 @@ cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, 
       dag_kernel<false, true, false><<<grid, kThreads, 0, st>>>(a);
   } else {
     if (mixed)
-      dag_kernel<true, false, false><<<grid, kThreads, a.use_umma ? kUmmaSmemBytes : 0, st>>>(a);
+      dag_kernel<true, false, false><<<grid, kThreads, mixed_dyn_smem(a.use_umma), st>>>(a);
     else
       dag_kernel<false, false, false><<<grid, kThreads, 0, st>>>(a);
   }

@@ -28,7 +28,11 @@ enum TaskKind {
   TASK_RPOTRF = 13,  // (J)       Abar_JJ = sym(L^{-T} Phi(L^T Lbar_JJ) L^{-1})  (reverse of POTRF(J))
   // Inverse of a factored diagonal tile, kept for the vector solves of Eq. (2) (each diagonal-block
   // solve becomes a matrix-vector product; not a step of the paper, which solves by substitution).
-  TASK_TRTRI = 14    // (J)        Linv_J = L_JJ^{-1} (FP64)
+  TASK_TRTRI = 14,   // (J)        Linv_J = L_JJ^{-1} (FP64)
+  // Grouped covariance products of the mixed mode on the tensor cores (one pass over the output tile
+  // for several J; never part of a batched launch):
+  TASK_VGEMM_G = 15,  // (I, c, J0 | J1 << 16)  V_Ic -= sum_{J0 <= J < J1} L_IJ V_Jc
+  TASK_WSYRK_G = 16   // (a, b, J0 | J1 << 16)  S_ab -= sum_{J0 <= J < J1} V_Ja^T V_Jb
 };
 
 // One GP of a batch: its inputs, outputs, hyperparameters and workspace (all device pointers).
@@ -59,7 +63,7 @@ struct GpDesc {
 constexpr int kAdjParts = 8;
 
 // Batched task encoding: kind | (gp index << 4) in the first component.
-constexpr int kBatchKindBits = 4;
+constexpr int kBatchKindBits = 5;  // kinds 0..16 fit below the GP index
 
 struct DagArgs {
   double* Kt;       // packed lower tiles (T x T row-major each), tile (I,J) at I(I+1)/2 + J

@@ -145,19 +145,55 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
   const double spf = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
   const double c_trsm = cm.task_overhead + spf * t3 / cm.trsm_eff;
   const double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
-  std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1);
+  // Mixed mode on the tensor cores groups the products into one output tile: V_Ic takes columns
+  // [J0, J1) together while they are far from its own solve (the last kTail one by one, as they
+  // gate the solve chain); S_ab takes every g consecutive J together.
+  const int g = cm.update_group > 1 ? cm.update_group : 1;
+  const int kTail = 2;
+  std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1), vtrsm((size_t)Mt * Mc, -1);
+  std::vector<int> gstartV((size_t)Mt * Mc, 0), gstartS(tri(Mc, 0), 0);
   for (int J = 0; J < Mt; ++J) {
-    for (int c = 0; c < Mc; ++c)
+    for (int c = 0; c < Mc; ++c) {
       lastV[(size_t)J * Mc + c] = b.add(TASK_VTRSM, J, c, 0, c_trsm, {lastV[(size_t)J * Mc + c]});
+      vtrsm[(size_t)J * Mc + c] = lastV[(size_t)J * Mc + c];
+    }
     for (int I = J + 1; I < Mt; ++I)
-      for (int c = 0; c < Mc; ++c)
-        lastV[(size_t)I * Mc + c] =
-            b.add(TASK_VGEMM, I, J, c, c_gemm, {lastV[(size_t)J * Mc + c], lastV[(size_t)I * Mc + c]});
+      for (int c = 0; c < Mc; ++c) {
+        const size_t v = (size_t)I * Mc + c;
+        if (g == 1) {
+          lastV[v] = b.add(TASK_VGEMM, I, J, c, c_gemm, {vtrsm[(size_t)J * Mc + c], lastV[v]});
+          continue;
+        }
+        const int lim = I - kTail;
+        int J0 = J;
+        if (J < lim) {
+          if ((J + 1) % g != 0 && J + 1 != lim) continue;  // the group stays open
+          J0 = gstartV[v];
+        }
+        std::vector<int> deps{lastV[v]};
+        for (int Jj = J0; Jj <= J; ++Jj) deps.push_back(vtrsm[(size_t)Jj * Mc + c]);
+        lastV[v] = b.add_v(TASK_VGEMM_G, I, c, J0 | ((J + 1) << 16), (J + 1 - J0) * c_gemm, deps);
+        gstartV[v] = J + 1;
+      }
     if (!with_w) continue;  // variance only: V is all that is needed
     for (int a = 0; a < Mc; ++a)
-      for (int bb = 0; bb <= a; ++bb)
-        lastS[tri(a, bb)] = b.add(TASK_WSYRK, a, bb, J, c_gemm,
-                                  {lastV[(size_t)J * Mc + a], lastV[(size_t)J * Mc + bb], lastS[tri(a, bb)]});
+      for (int bb = 0; bb <= a; ++bb) {
+        const size_t sidx = tri(a, bb);
+        if (g == 1) {
+          lastS[sidx] = b.add(TASK_WSYRK, a, bb, J, c_gemm,
+                              {vtrsm[(size_t)J * Mc + a], vtrsm[(size_t)J * Mc + bb], lastS[sidx]});
+          continue;
+        }
+        if ((J + 1) % g != 0 && J + 1 != Mt) continue;
+        const int J0 = gstartS[sidx];
+        std::vector<int> deps{lastS[sidx]};
+        for (int Jj = J0; Jj <= J; ++Jj) {
+          deps.push_back(vtrsm[(size_t)Jj * Mc + a]);
+          deps.push_back(vtrsm[(size_t)Jj * Mc + bb]);
+        }
+        lastS[sidx] = b.add_v(TASK_WSYRK_G, a, bb, J0 | ((J + 1) << 16), (J + 1 - J0) * c_gemm, deps);
+        gstartS[sidx] = J + 1;
+      }
   }
   return b.ordered(workers);
 }

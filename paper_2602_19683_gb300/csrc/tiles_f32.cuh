@@ -39,7 +39,7 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 
 constexpr int SBM = 128, SBN = 128, SBK = 16, SPAD = 4;
 
-struct GemmSmemF32 {
+struct __align__(16) GemmSmemF32 {  // read with 16-byte vector loads
   float a[2][SBK][SBM + SPAD];
   float b[2][SBK][SBN + SPAD];
 };
@@ -206,7 +206,7 @@ __device__ void cta_trsm_cols32_f32(const Tri32F& s, double* B, int ldb, int nco
   __syncthreads();
 }
 
-struct TileSmemF32 {
+struct __align__(16) TileSmemF32 {
   GemmSmemF32 g;  // also the 256 x 33 float staging area of the row solves
   Tri32F tri;
 };

@@ -21,11 +21,13 @@ namespace gpk {
 constexpr int kUmmaM = 128, kUmmaN = 128, kUmmaKChunk = 32;
 constexpr int kUmmaTileBytes = kUmmaM * 128;           // 128 rows x 32 tf32
 constexpr int kUmmaStageBytes = 4 * kUmmaTileBytes;    // A_hi, A_lo, B_hi, B_lo
-// Dynamic shared memory of the mixed kernel: the two operand stages, also the home of a 128 x 129 FP64
-// diagonal tile during a shared-memory POTRF; plus alignment slack.
+constexpr int kPkStages = 3;                           // stages of the packed-operand pipeline
+// Dynamic shared memory of the mixed kernel: the operand stages, also the home of a 128 x 129 FP64
+// diagonal tile during a shared-memory POTRF (and of two 128 x 129 FP32 tiles while its inverse is
+// formed), and of the FP64/FP32 tile routines' scratch; plus alignment slack.
 constexpr int kMixedTileSmemBytes = 128 * 129 * 8;
 constexpr int kUmmaSmemBytes =
-    (2 * kUmmaStageBytes > kMixedTileSmemBytes ? 2 * kUmmaStageBytes : kMixedTileSmemBytes) + 2048;
+    (kPkStages * kUmmaStageBytes > kMixedTileSmemBytes ? kPkStages * kUmmaStageBytes : kMixedTileSmemBytes) + 2048;
 constexpr int kUmmaTmemCols = 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -118,8 +120,8 @@ struct UmmaState {
   // copies' transaction bytes and an "empty" barrier completed by the MMA commit
   uint64_t* pfull;
   uint64_t* pempty;
-  uint32_t fph[2], eph[2];      // next parity to wait for
-  uint32_t fpend[2], epend[2];  // a copy / a commit is outstanding on the stage
+  uint32_t fph[kPkStages], eph[kPkStages];      // next parity to wait for
+  uint32_t fpend[kPkStages], epend[kPkStages];  // a copy / a commit is outstanding on the stage
 };
 
 // Waits (thread 0, bounded) until the MMAs committed to stage s have completed; the outcome is made

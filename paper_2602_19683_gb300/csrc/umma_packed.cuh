@@ -23,8 +23,8 @@
 namespace gpk {
 
 constexpr int kPkChunkBytes = 2 * kUmmaTileBytes;  // high + low tile of one 128-row x 32-k chunk
-constexpr int kPkStages = 2;                        // each stage: A chunk + B chunk (64 KB)
-static_assert(kPkStages * 2 * kPkChunkBytes <= 2 * kUmmaStageBytes, "stages must fit the dynamic smem");
+static_assert(2 * kPkChunkBytes == kUmmaStageBytes, "a stage holds one A and one B chunk");
+static_assert(kPkStages * kUmmaStageBytes + 1024 <= kUmmaSmemBytes, "stages must fit the dynamic smem");
 
 __device__ __forceinline__ size_t pk_chunk_off(int rb, int kc, int Kd) {
   return ((size_t)rb * (Kd / kUmmaKChunk) + kc) * kPkChunkBytes;
@@ -226,10 +226,25 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
   const int ld = nb + 1, nblk = nb / 32;
   float* Ls = sm;
   float* Xs = sm + nb * ld;
-  for (int e = t; e < nb * nb; e += kThreads) {
-    const int i = e / nb, j = e % nb;
-    Ls[i * ld + j] = (j <= i) ? f64_to_f32_rn(ldcg(L + (size_t)i * ldl + j)) : 0.f;
-    Xs[i * ld + j] = 0.f;
+  const int npair = nb / 2;  // coalesced double2 loads, eight in flight per thread
+  for (int e0 = 0; e0 < nb * npair; e0 += 8 * kThreads) {
+    double2 d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * kThreads + t;
+      if (e < nb * npair) d[q] = __ldcg(reinterpret_cast<const double2*>(L + (size_t)(e / npair) * ldl) + e % npair);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * kThreads + t;
+      if (e < nb * npair) {
+        const int i = e / npair, j = 2 * (e % npair);
+        Ls[i * ld + j] = (j <= i) ? f64_to_f32_rn(d[q].x) : 0.f;
+        Ls[i * ld + j + 1] = (j + 1 <= i) ? f64_to_f32_rn(d[q].y) : 0.f;
+        Xs[i * ld + j] = 0.f;
+        Xs[i * ld + j + 1] = 0.f;
+      }
+    }
   }
   __syncthreads();
   if (w < nblk) {  // diagonal blocks

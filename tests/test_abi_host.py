@@ -88,9 +88,13 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
     assert inverted == set(range(Mt))
 
 
-@pytest.mark.parametrize("Mt,Mc,workers", [(1, 1, 2), (4, 3, 5), (7, 2, 304)])
-def test_cov_schedule_is_topological(lib, Mt, Mc, workers):
-    t = tasks(lib, 1, Mt, Mc, 64, workers)
+@pytest.mark.parametrize("Mt,Mc,workers,mixed", [(1, 1, 2, 0), (4, 3, 5, 0), (7, 2, 304, 0), (1, 1, 2, 1),
+                                                 (9, 3, 5, 1), (13, 2, 304, 1)])
+def test_cov_schedule_is_topological(lib, Mt, Mc, workers, mixed):
+    """L V = K_{X,Xs} then S -= V^T V (Eq. 3): every block of V is solved after all its updates, in J
+    order; mixed 128-tiles group the products (V_Ic over J0..J1 while far from its solve, S_ab over g
+    consecutive J)."""
+    t = tasks(lib, 1, Mt, Mc, 128 if mixed else 64, workers, mixed)
     cv, cs = {}, {}
     for kind, p, q, r in t:
         if kind == 3:
@@ -102,9 +106,21 @@ def test_cov_schedule_is_topological(lib, Mt, Mc, workers):
         elif kind == 5:
             assert p >= q and cv.get((r, p), 0) == r + 1 and cv.get((r, q), 0) == r + 1 and cs.get((p, q), 0) == r
             cs[(p, q)] = r + 1
+        elif kind == 15:  # V_Ic -= sum_{J0 <= J < J1} L_IJ V_Jc
+            J0, J1 = r & 0xFFFF, r >> 16
+            assert mixed and p >= J1 > J0 >= 0 and J1 - J0 <= 8 and cv.get((p, q), 0) == J0
+            assert all(cv.get((J, q), 0) == J + 1 for J in range(J0, J1))
+            assert J1 - J0 == 1 or J1 <= p - 2  # the two columns next to the solve stay single
+            cv[(p, q)] = J1
+        elif kind == 16:  # S_ab -= sum_{J0 <= J < J1} V_Ja^T V_Jb
+            J0, J1 = r & 0xFFFF, r >> 16
+            assert mixed and p >= q and J1 - J0 <= 8 and cs.get((p, q), 0) == J0
+            assert all(cv.get((J, p), 0) == J + 1 and cv.get((J, q), 0) == J + 1 for J in range(J0, J1))
+            cs[(p, q)] = J1
         else:
             raise AssertionError(kind)
     assert all(cs[(a, b)] == Mt for a in range(Mc) for b in range(a + 1))
+    assert all(cv[(I, c)] == I + 1 for I in range(Mt) for c in range(Mc))
 
 
 @pytest.mark.parametrize("Mt,T,workers", [(1, 32, 1), (3, 64, 2), (6, 96, 304)])
