@@ -136,6 +136,9 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
         gstart[t] = J + 1;
       }
   }
+  // Longest-remaining-path order. (A column-group / super-tile order for the grouped updates keeps
+  // their operands in L2 — 98 % modelled hits against 14 % — but delays the updates the diagonal
+  // chain waits for; measured at n = 32768 both orders give the same factorisation time.)
   return b.ordered(workers);
 }
 
@@ -152,10 +155,21 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
   const int kTail = 2;
   std::vector<int> lastV((size_t)Mt * Mc, -1), lastS(tri(Mc, 0), -1), vtrsm((size_t)Mt * Mc, -1);
   std::vector<int> gstartV((size_t)Mt * Mc, 0), gstartS(tri(Mc, 0), 0);
+  // With grouped products: the solve chain (V solves and the single products next to them) first;
+  // the grouped products after it in column-group order, then by block row I and column block c, so
+  // that consecutive products share the L panel tiles of row I and the group's V blocks stay in L2.
+  std::vector<double> key;
+  auto keyed = [&](int t, double k) {
+    if (g == 1) return;
+    if ((int)key.size() <= t) key.resize(t + 1, 1.0);
+    key[t] = k;
+  };
+  const double grp = (double)Mt * Mc + 1.0;
   for (int J = 0; J < Mt; ++J) {
     for (int c = 0; c < Mc; ++c) {
       lastV[(size_t)J * Mc + c] = b.add(TASK_VTRSM, J, c, 0, c_trsm, {lastV[(size_t)J * Mc + c]});
       vtrsm[(size_t)J * Mc + c] = lastV[(size_t)J * Mc + c];
+      keyed(vtrsm[(size_t)J * Mc + c], 1.0);
     }
     for (int I = J + 1; I < Mt; ++I)
       for (int c = 0; c < Mc; ++c) {
@@ -174,6 +188,7 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
         for (int Jj = J0; Jj <= J; ++Jj) deps.push_back(vtrsm[(size_t)Jj * Mc + c]);
         lastV[v] = b.add_v(TASK_VGEMM_G, I, c, J0 | ((J + 1) << 16), (J + 1 - J0) * c_gemm, deps);
         gstartV[v] = J + 1;
+        keyed(lastV[v], J < lim ? -((double)(J0 / g) * grp + (double)I * Mc + c) - 1.0 : 1.0);
       }
     if (!with_w) continue;  // variance only: V is all that is needed
     for (int a = 0; a < Mc; ++a)
@@ -193,9 +208,12 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
         }
         lastS[sidx] = b.add_v(TASK_WSYRK_G, a, bb, J0 | ((J + 1) << 16), (J + 1 - J0) * c_gemm, deps);
         gstartS[sidx] = J + 1;
+        keyed(lastS[sidx], -((double)(J0 / g) * grp + (double)Mt * Mc) - 1.0);
       }
   }
-  return b.ordered(workers);
+  if (g == 1) return b.ordered(workers);
+  key.resize(b.tasks.size(), 1.0);
+  return b.ordered(workers, &key);
 }
 
 // Reverse of Fig. 1's algorithm for the adjoint Lbar -> Abar: for J = Mt-1 down to 0, first undo

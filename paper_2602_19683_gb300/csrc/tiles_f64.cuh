@@ -17,7 +17,7 @@ enum { B_NK = 0, B_KN = 1 };  // B_NK: B[n*ldb + k] (C -= A B^T); B_KN: B[k*ldb 
 
 constexpr int GBM = 64, GBN = 64, GBK = 16, GPAD = 4;
 
-struct GemmSmem {
+struct __align__(16) GemmSmem {  // read with 16-byte vector loads
   double a[2][GBK][GBM + GPAD];
   double b[2][GBK][GBN + GPAD];
 };
@@ -327,7 +327,7 @@ __device__ void cta_trsm_cols32(const Tri32& s, double* B, int ldb, int ncols) {
   __syncthreads();
 }
 
-struct TileSmem {
+struct __align__(16) TileSmem {
   GemmSmem g;
   Tri32 tri;
   int flag;
@@ -366,9 +366,25 @@ __device__ int cta_potrf(double* A, int lda, int nb, TileSmem& s) {
 // Returns 0 or the 1-based failing column.
 __device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* inv, int* flag) {
   const int ld = nb + 1, t = threadIdx.x;
-  for (int e = t; e < nb * nb; e += kThreads) {
-    const int i = e / nb, j = e % nb;
-    sm[i * ld + j] = (j <= i) ? ldcg(A + (size_t)i * lda + j) : 0.0;
+  // coalesced double2 loads, eight in flight per thread (the tile is L2-resident: latency, not
+  // bandwidth, decides how long this takes)
+  const int npair = nb / 2;
+  for (int e0 = 0; e0 < nb * npair; e0 += 8 * kThreads) {
+    double2 d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * kThreads + t;
+      if (e < nb * npair) d[q] = __ldcg(reinterpret_cast<const double2*>(A + (size_t)(e / npair) * lda) + e % npair);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * kThreads + t;
+      if (e < nb * npair) {
+        const int i = e / npair, j = 2 * (e % npair);
+        sm[i * ld + j] = (j <= i) ? d[q].x : 0.0;
+        sm[i * ld + j + 1] = (j + 1 <= i) ? d[q].y : 0.0;
+      }
+    }
   }
   if (t == 0) *flag = 0;
   __syncthreads();
@@ -399,10 +415,12 @@ __device__ int cta_potrf_smem(double* A, int lda, int nb, double* sm, double* in
       for (int c = 0; c < 32; ++c) row[c] = x[c];
     }
     __syncthreads();
-    const int m = nb - k0 - 32;  // trailing lower triangle, entries (i, j), j <= i
-    for (int e = t; e < m * m; e += kThreads) {
-      const int i = e / m, j = e % m;
-      if (j > i) continue;
+    const int m = nb - k0 - 32;  // trailing lower triangle, entries (i, j), j <= i, enumerated directly
+    for (int e = t; e < m * (m + 1) / 2; e += kThreads) {
+      int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      const int j = e - i * (i + 1) / 2;
       const double* ri = sm + (size_t)(k0 + 32 + i) * ld + k0;
       const double* rj = sm + (size_t)(k0 + 32 + j) * ld + k0;
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -561,35 +579,33 @@ __device__ void cta_trsv_lower_T(const double* L, int ldl, double* b, int nb, do
 
 // b[0..nb) <- Linv b, Linv the lower-triangular inverse of a diagonal tile (upper triangle zero): the
 // diagonal-block solve as a matrix-vector product, without the substitution's serial chain. b is
-// staged in smem (xs, nb doubles). Each warp takes four rows at a time; lanes stride the columns
-// (coalesced row segments), so 4 x (nb / 32) loads per lane are independent.
+// staged in smem (xs, nb doubles). Each warp takes eight rows at a time; lanes stride the columns
+// (coalesced row segments), so up to 8 x (nb / 32) loads per lane are in flight together.
 __device__ void cta_trsv_inv(const double* Linv, int ld, double* b, int nb, double* xs) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   for (int i = t; i < nb; i += kThreads) xs[i] = ldcg(b + i);
   __syncthreads();
-  for (int r0 = 4 * w; r0 < nb; r0 += 4 * (kThreads / 32)) {
+  for (int r0 = 8 * w; r0 < nb; r0 += 8 * (kThreads / 32)) {
     const double* L0 = Linv + (size_t)r0 * ld;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
 #pragma unroll 4
-    for (int c = lane; c <= r0 + 3; c += 32) {
+    for (int c = lane; c <= r0 + 7; c += 32) {
       const double x = xs[c];
-      a0 = fma(ldcg(L0 + c), x, a0);
-      a1 = fma(ldcg(L0 + ld + c), x, a1);
-      a2 = fma(ldcg(L0 + 2 * (size_t)ld + c), x, a2);
-      a3 = fma(ldcg(L0 + 3 * (size_t)ld + c), x, a3);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = fma(ldcg(L0 + (size_t)q * ld + c), x, acc[q]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-      a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     }
-    if (lane == 0) {
-      b[r0] = a0;
-      b[r0 + 1] = a1;
-      b[r0 + 2] = a2;
-      b[r0 + 3] = a3;
+    if (lane < 8) {
+      double v = acc[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) v = (lane == q) ? acc[q] : v;
+      b[r0 + lane] = v;
     }
   }
   __syncthreads();
@@ -602,20 +618,22 @@ __device__ void cta_trsv_inv_T(const double* Linv, int ld, double* b, int nb, do
   for (int i = t; i < nb; i += kThreads) xs[i] = ldcg(b + i);
   __syncthreads();
   for (int c0 = 0; c0 < nb; c0 += 32) {
-    double a0 = 0.0, a1 = 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int r = c0 + w;
-#pragma unroll 2
-    for (; r + kThreads / 32 < nb; r += 2 * (kThreads / 32)) {
+    constexpr int W = kThreads / 32;
+    for (; r + 3 * W < nb; r += 4 * W) {
       a0 = fma(ldcg(Linv + (size_t)r * ld + c0 + lane), xs[r], a0);
-      a1 = fma(ldcg(Linv + (size_t)(r + kThreads / 32) * ld + c0 + lane), xs[r + kThreads / 32], a1);
+      a1 = fma(ldcg(Linv + (size_t)(r + W) * ld + c0 + lane), xs[r + W], a1);
+      a2 = fma(ldcg(Linv + (size_t)(r + 2 * W) * ld + c0 + lane), xs[r + 2 * W], a2);
+      a3 = fma(ldcg(Linv + (size_t)(r + 3 * W) * ld + c0 + lane), xs[r + 3 * W], a3);
     }
-    if (r < nb) a0 = fma(ldcg(Linv + (size_t)r * ld + c0 + lane), xs[r], a0);
-    red[w][lane] = a0 + a1;
+    for (; r < nb; r += W) a0 = fma(ldcg(Linv + (size_t)r * ld + c0 + lane), xs[r], a0);
+    red[w][lane] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (t < 32) {
       double acc = 0.0;
 #pragma unroll
-      for (int q = 0; q < kThreads / 32; ++q) acc += red[q][t];
+      for (int q = 0; q < W; ++q) acc += red[q][t];
       b[c0 + t] = acc;
     }
     __syncthreads();
@@ -626,16 +644,29 @@ __device__ void cta_trsv_inv_T(const double* Linv, int ld, double* b, int nb, do
 // Entries above the diagonal stay exactly zero.
 __device__ void cta_trtri(const double* L, int ldl, double* Linv, int nb, TileSmem& s);
 
-// b[r] -= sum_c A[r][c] x[c] for r in [0, rows): one warp per row, lanes over columns.
+// b[r] -= sum_c A[r][c] x[c] for r in [0, rows): each warp takes four rows at a time, lanes over
+// columns, so the loads of the four rows are in flight together.
 __device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* b, int rows, int cols) {
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int r = w; r < rows; r += kThreads / 32) {
-    const double* Ar = A + (size_t)r * lda;
-    double acc = 0.0;
-    for (int c = lane; c < cols; c += 32) acc = fma(ldcg(Ar + c), ldcg(x + c), acc);
+  for (int r0 = 4 * w; r0 < rows; r0 += 4 * (kThreads / 32)) {
+    const int nr = rows - r0 < 4 ? rows - r0 : 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int c = lane; c < cols; c += 32) {
+      const double xv = ldcg(x + c);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) b[r] = ldcg(b + r) - acc;
+      for (int q = 0; q < 4; ++q)
+        if (q < nr) acc[q] = fma(ldcg(A + (size_t)(r0 + q) * lda + c), xv, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    }
+    if (lane < nr) {
+      const double v = lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3];
+      b[r0 + lane] = ldcg(b + r0 + lane) - v;
+    }
   }
   __syncthreads();
 }
@@ -645,10 +676,18 @@ __device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* 
 __device__ void cta_gemv_T_sub(const double* A, int lda, const double* x, double* b, int rows, int cols,
                                double (*red)[32]) {
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  double acc = 0.0;
-  if (lane < cols)
-    for (int r = w; r < rows; r += kThreads / 32) acc = fma(ldcg(A + (size_t)r * lda + lane), ldcg(x + r), acc);
-  red[w][lane] = acc;
+  double a0 = 0.0, a1 = 0.0;
+  if (lane < cols) {
+    constexpr int W = kThreads / 32;
+    int r = w;
+#pragma unroll 2
+    for (; r + W < rows; r += 2 * W) {
+      a0 = fma(ldcg(A + (size_t)r * lda + lane), ldcg(x + r), a0);
+      a1 = fma(ldcg(A + (size_t)(r + W) * lda + lane), ldcg(x + r + W), a1);
+    }
+    if (r < rows) a0 = fma(ldcg(A + (size_t)r * lda + lane), ldcg(x + r), a0);
+  }
+  red[w][lane] = a0 + a1;
   __syncthreads();
   if (threadIdx.x < cols) {
     double s = 0.0;
