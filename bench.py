@@ -29,6 +29,19 @@ sys.path.insert(0, ROOT)
 
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~2 GHz on 152 SMs)
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one FP64 Cholesky launch of the task-DAG
+# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.083 GB read + 2.579 GB written
+# (profiles/dag_kernel_fp64_cholesky_n32768.md). Traffic follows the number of tile updates,
+# (Mt^3 - Mt)/6, so a launch with Mt tile rows of edge 256 moves this times updates(Mt)/updates(32).
+FP64_CHOL_TRAFFIC_MT32_T256 = 2.083361e9 + 2.579202e9
+
+
+def fp64_cholesky_traffic(n: int, tile: int):
+    if tile != 256:
+        return None
+    mt = (n + tile - 1) // tile
+    return FP64_CHOL_TRAFFIC_MT32_T256 * (mt ** 3 - mt) / (32 ** 3 - 32)
+
 
 def algorithmic_flops(n: int, m: int) -> float:
     return n ** 3 / 3 + n * n * m + n * m * m + 2 * n * n + 2 * n * m
@@ -369,7 +382,9 @@ def run_ours(args):
             "roofline": {"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": "FP64 FFMA pipe: 2 FMA/clk/SM x 152 SMs x max SM clock (derived)",
-                         "traffic": None},
+                         "traffic": (fp64_cholesky_traffic(n, ctx_tile(n, args.tile)) if args.precision == "fp64"
+                                     else None),
+                         "traffic_note": "bytes per launch, ncu capture at n=8192 scaled by the tile-update count"},
             "gpu_launches": launches, "clocks": clocks}
     if mixed:
         line["mixed"] = mixed
