@@ -124,8 +124,8 @@ int auto_tile(long long n, bool mixed_tc) {
 
 gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
   gpk::CostModel cm;
-  // Mixed tensor-core updates are bound by their FP64 C read-modify-write: group 4 columns per task.
-  cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 4 : 1;
+  // Mixed tensor-core updates: group 8 columns per task (one FP64 C read-modify-write for eight).
+  cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 8 : 1;
   // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
   cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
   cm.sec_per_flop32 = 1.0 / 3.0e11;
@@ -347,7 +347,7 @@ int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int3
   if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4) return -1;
   gpk::CostModel cm;
   cm.mixed = mixed != 0;
-  cm.update_group = (mixed && T % 128 == 0) ? 4 : 1;
+  cm.update_group = (mixed && T % 128 == 0) ? 8 : 1;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);
@@ -489,15 +489,17 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
     GP_TRY(grow(f->rvec, npad * sizeof(double)));
     GP_TRY(grow(f->part, (size_t)6 * Mt * nch * sizeof(double)));
     bool converged = false;
-    double eta_prev = 0.0;
+    double eta_prev = 0.0, knorm = 0.0;
     for (int it = 0;; ++it) {
+      // ||K||_inf is the same every step: the first residual computes it, the later ones reuse it
       GP_CUDA(gpk::launch_residual((const double*)f->Kt0.p, T, Mt, f->n, y, (const double*)f->alpha.p,
-                                   (double*)f->bvec.p, (double*)f->part.p, c->d_scalar, c->stream));
+                                   (double*)f->bvec.p, (double*)f->part.p, c->d_scalar, c->stream, it == 0));
       count_launch(c, 2);
       double nr[6];
       GP_CUDA(cudaMemcpyAsync(nr, c->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       GP_CUDA(cudaStreamSynchronize(c->stream));
-      const double den = nr[3] * nr[4] + nr[5];
+      if (it == 0) knorm = nr[3];
+      const double den = knorm * nr[4] + nr[5];
       const double eta = den > 0 ? nr[2] / den : 0.0;
       f->ir_eta = eta;
       if (!(eta == eta)) break;  // NaN: the device status (if any) reports why

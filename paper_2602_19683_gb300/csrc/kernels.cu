@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           aborted = true;
           break;
         }
-        if (kUmma && use_umma && a.PLinv && T == kUmmaM)  // FP32 inverse for the column's TRSMs and V solves
-          cta_inverse_pack(a.Kt + tri(p, p) * TT, T, T, reinterpret_cast<float*>(um.smem), a.PLinv + p * TT * 8);
+        if (kUmma && use_umma && a.PLinv && T == kUmmaM)  // FP32 inverse for the column's TRSMs and V solves,
+          cta_inverse_pack_smem(um.smem, T, a.PLinv + p * TT * 8);  // from the factor left in shared memory
         cta_publish(a.cK + tri(p, p), p + 1);
         break;
       }
@@ -594,7 +594,10 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
 // r = y - K alpha for the 32 rows (tile row I = blockIdx.x / nch, chunk ch) from the packed lower
 // FP64 tiles of the symmetric K (diagonal tiles hold both triangles): row part from tiles (I, J<=I),
 // transposed part from tiles (J>I, I). Per-block partials (6 doubles): sum r^2, sum y^2,
-// max |r|, max row sum |K_i.|, max |alpha|, max |y| (for the normwise backward error).
+// max |r|, max row sum |K_i.|, max |alpha|, max |y| (for the normwise backward error). kNorm = false
+// skips the row sums of |K| (they do not change between refinement steps; entry 3 is then 0), which
+// halves the kernel's FP64 work.
+template <bool kNorm>
 __global__ void __launch_bounds__(kThreads) residual_kernel(const double* __restrict__ Kt, int T, int Mt,
                                                             long long n, const double* __restrict__ y,
                                                             const double* __restrict__ alpha, double* __restrict__ r,
@@ -618,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(const double* __rest
       for (int k = 0; k < 4; ++k) {
         const double kv = tile[(size_t)k * T + c];
         acc[k] = fma(kv, av, acc[k]);
-        abs4[k] += fabs(kv);
+        if (kNorm) abs4[k] += fabs(kv);
       }
     }
   }
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(const double* __rest
     for (int rr = w; rr < T; rr += kThreads / 32) {
       const double kv = tile[(size_t)rr * T];
       accT = fma(kv, aJ[rr], accT);
-      absT += fabs(kv);
+      if (kNorm) absT += fabs(kv);
     }
   }
 #pragma unroll
@@ -1105,9 +1108,12 @@ int dag_max_ctas_per_sm(bool mixed) {
 }
 
 cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
-                            double* r, double* partial, double* norms, cudaStream_t st) {
+                            double* r, double* partial, double* norms, cudaStream_t st, bool with_knorm) {
   const int nb = Mt * (T / 32);
-  residual_kernel<<<nb, kThreads, 0, st>>>(Kt, T, Mt, n, y, alpha, r, partial);
+  if (with_knorm)
+    residual_kernel<true><<<nb, kThreads, 0, st>>>(Kt, T, Mt, n, y, alpha, r, partial);
+  else
+    residual_kernel<false><<<nb, kThreads, 0, st>>>(Kt, T, Mt, n, y, alpha, r, partial);
   reduce_residual_kernel<<<1, kThreads, 0, st>>>(partial, nb, norms);
   return cudaGetLastError();
 }

@@ -130,9 +130,9 @@ cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs,
 cudaError_t launch_batch_post(const int4* items, int nitems, const GpDesc* descs, cudaStream_t st);
 int dag_max_ctas_per_sm(bool mixed);
 // r = y - K alpha from packed lower FP64 tiles; norms = {||r||_2^2, ||y||_2^2, ||r||_inf, ||K||_inf,
-// ||alpha||_inf, ||y||_inf}. partial needs 6 * Mt * (T/32) doubles.
+// ||alpha||_inf, ||y||_inf} (||K||_inf only with with_knorm, else 0). partial needs 6 * Mt * (T/32) doubles.
 cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
-                            double* r, double* partial, double* norms, cudaStream_t st);
+                            double* r, double* partial, double* norms, cudaStream_t st, bool with_knorm);
 cudaError_t launch_axpy(double* alpha, const double* d, long long n, cudaStream_t st);
 // beta = L^T alpha from the factor tiles (so that beta = L^{-1} y when alpha = K^{-1} y).
 cudaError_t launch_beta(const double* Lt, int T, int Mt, const double* alpha, double* beta, cudaStream_t st);

@@ -160,6 +160,26 @@ __device__ __forceinline__ void tri32_load(Tri32& s, const double* L, int ldl) {
   __syncthreads();
 }
 
+// Square root of a positive pivot d and its reciprocal, for the serial chain of a diagonal block
+// (one thread computes them while the CTA waits): an FP32 reciprocal-square-root seed refined by two
+// Newton-Raphson steps in FP64, r <- r (3 - d r^2) / 2, each of which doubles the correct bits (about
+// 2^-22 -> 2^-44 -> below FP64 rounding); then sqrt(d) = d r. About ten FP64 operations instead of an
+// FP64 square root and a division, whose longer dependent sequences cost microseconds per pivot on
+// this GPU's FP64 pipe. Pivots outside the FP32 range take the library square root and division.
+__device__ __forceinline__ void pivot_sqrt_rcp(double d, double& s, double& r) {
+  if (d > 1e-30 && d < 1e30) {
+    double y = (double)rsqrtf((float)d);
+    const double h = 0.5 * d;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    r = y;
+    s = d * y;
+  } else {
+    s = sqrt(d);
+    r = 1.0 / s;
+  }
+}
+
 // CTA-parallel right-looking Cholesky of a 32 x 32 block B (smem, leading dimension ld): step j, thread
 // 0 takes the pivot, 31 threads scale column j, and all 8 warps share the rank-1 update of the trailing
 // triangle (thread t: row j+1+t/8, columns j+1+(t%8), +8, ...), so every SM sub-partition's FP64 unit
@@ -173,9 +193,10 @@ __device__ int cta_potrf32_par(double* B, int ld, double* inv, int* flag) {
       if (!(d > 0.0)) {
         *flag = j + 1;
       } else {
-        const double ljj = sqrt(d);
+        double ljj, rj;
+        pivot_sqrt_rcp(d, ljj, rj);
         B[j * ld + j] = ljj;
-        inv[j] = 1.0 / ljj;
+        inv[j] = rj;
       }
     }
     __syncthreads();

@@ -27,8 +27,8 @@ constexpr int kPkStages = 3;                           // stages of the packed-o
 // formed), and of the FP64/FP32 tile routines' scratch; plus alignment slack.
 constexpr int kMixedTileSmemBytes = 128 * 129 * 8;
 constexpr int kUmmaSmemBytes =
-    (kPkStages * kUmmaStageBytes > kMixedTileSmemBytes ? kPkStages * kUmmaStageBytes : kMixedTileSmemBytes) + 2048;
-constexpr int kUmmaTmemCols = 128;
+    (kPkStages * kUmmaStageBytes > kMixedTileSmemBytes ? kPkStages * kUmmaStageBytes : kMixedTileSmemBytes) + 4096;
+constexpr int kUmmaTmemCols = 256;  // two 128 x 128 FP32 accumulators (see umma_packed.cuh)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -246,7 +246,7 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs
 // FP64 read-modify-write of C (a warp per row, 4 columns per lane): C -= acc, only n <= m when lower.
 // Ends with __syncthreads().
 template <bool kStore>
-__device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower) {
+__device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int nacc = 1) {
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* acc_s = reinterpret_cast<float*>(u.smem);  // 128 x (128 + 4) floats
@@ -271,6 +271,12 @@ __device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, 
     for (int half = 0; half < 2; ++half) {
       float v[32];
       tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(colh + 32 * half), v);
+      if (nacc > 1) {  // second accumulator (columns 128..255): one FP32 round-to-nearest add
+        float v2[32];
+        tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(kUmmaN + colh + 32 * half), v2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += v2[j];
+      }
       float* dst = acc_s + row * ldacc + colh + 32 * half;
 #pragma unroll
       for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);

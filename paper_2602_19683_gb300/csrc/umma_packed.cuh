@@ -23,8 +23,13 @@
 namespace gpk {
 
 constexpr int kPkChunkBytes = 2 * kUmmaTileBytes;  // high + low tile of one 128-row x 32-k chunk
+constexpr int kPairsPerAcc = 4;                     // operand pairs per TMEM accumulator (two of them)
+static_assert(2 * kPairsPerAcc >= kUmmaMaxPairs, "every pair needs an accumulator");
+static_assert(2 * kUmmaN <= kUmmaTmemCols, "two accumulators must fit the allocated TMEM columns");
 static_assert(2 * kPkChunkBytes == kUmmaStageBytes, "a stage holds one A and one B chunk");
 static_assert(kPkStages * kUmmaStageBytes + 1024 <= kUmmaSmemBytes, "stages must fit the dynamic smem");
+static_assert(kMixedTileSmemBytes + 128 * 128 * 4 + 1024 <= kUmmaSmemBytes,
+              "a 128 x 129 FP64 tile and a 128 x 128 FP32 copy must fit the dynamic smem");
 
 __device__ __forceinline__ size_t pk_chunk_off(int rb, int kc, int Kd) {
   return ((size_t)rb * (Kd / kUmmaKChunk) + kc) * kPkChunkBytes;
@@ -142,12 +147,17 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
       umma_fence_after();
       const uint32_t a_hi = smem_u32(u.smem + s * 2 * kPkChunkBytes), a_lo = a_hi + kUmmaTileBytes;
       const uint32_t b_hi = a_hi + kPkChunkBytes, b_lo = b_hi + kUmmaTileBytes;
+      // pairs 0..3 accumulate in TMEM columns 0..127, pairs 4..7 in columns 128..255, so no FP32
+      // accumulation chain (whose additions truncate) runs over more than four column pairs
+      const int pair = i / nkp, acc_i = pair >= kPairsPerAcc ? 1 : 0;
+      const uint32_t d_tmem = u.tmem + (uint32_t)(acc_i * kUmmaN);
+      const bool first = (i % (kPairsPerAcc * nkp)) == 0;  // first chunk of this accumulator
 #pragma unroll
       for (int ks = 0; ks < kUmmaKChunk / 8; ++ks) {
         const uint32_t o = ks * 32;
-        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_hi + o), (i > 0 || ks > 0) ? 1u : 0u);
-        umma_tf32(u.tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
-        umma_tf32(u.tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
+        umma_tf32(d_tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_hi + o), (!first || ks > 0) ? 1u : 0u);
+        umma_tf32(d_tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
+        umma_tf32(d_tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
       }
       umma_commit(&u.pempty[s]);
       u.epend[s] = 1;
@@ -193,7 +203,7 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
     }
   }
   if (__syncthreads_or(!ok)) return false;
-  umma_epilogue<kStore>(u, C, ldc, m0, n0, lower);
+  umma_epilogue<kStore>(u, C, ldc, m0, n0, lower, pr.n > kPairsPerAcc ? 2 : 1);
   fence_async_smem();  // generic smem traffic of the epilogue before the next bulk copies
   __syncthreads();
   return true;
@@ -215,38 +225,16 @@ __device__ bool umma_pk_gemm_sub(UmmaState& u, double* C, int ldc, const PkPairs
 
 // ---------------------------------------------------------------- the inverse of a diagonal tile
 
-// X = L^{-1} in FP32 for a factored nb x nb diagonal tile L (FP64, global; nb a multiple of 32, at most
-// 128), written as the packed operand Op[r][k] = X[r][k] (upper triangle zero). It turns the TRSMs of
-// the tile's block column (L_IJ = K_IJ X^T) and the diagonal-block solves of the covariance
-// (V_Jc <- X V_Jc) into tensor-core products. Blocked by 32: warp d inverts diagonal block d (lane j
-// solves column j), then block rows i = 1.. follow X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
-// sm: (2 nb (nb + 1)) floats of shared memory.
-__device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, uint8_t* dst) {
+// X = L^{-1} in FP32 for a factored nb x nb diagonal tile (nb a multiple of 32, at most 128), written as
+// the packed operand Op[r][k] = X[r][k] (upper triangle zero). It turns the TRSMs of the tile's block
+// column (L_IJ = K_IJ X^T) and the diagonal-block solves of the covariance (V_Jc <- X V_Jc) into
+// tensor-core products. Blocked by 32: warp d inverts diagonal block d (lane j solves column j), then
+// block rows i = 1.. follow X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
+// Ls: the factor's lower triangle in FP32 (leading dimension lds, upper triangle zero); Xs: zeroed
+// FP32 workspace (leading dimension ldx).
+__device__ void cta_inverse_core(const float* Ls, int lds, float* Xs, int ldx, int nb, uint8_t* dst) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int ld = nb + 1, nblk = nb / 32;
-  float* Ls = sm;
-  float* Xs = sm + nb * ld;
-  const int npair = nb / 2;  // coalesced double2 loads, eight in flight per thread
-  for (int e0 = 0; e0 < nb * npair; e0 += 8 * kThreads) {
-    double2 d[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * kThreads + t;
-      if (e < nb * npair) d[q] = __ldcg(reinterpret_cast<const double2*>(L + (size_t)(e / npair) * ldl) + e % npair);
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * kThreads + t;
-      if (e < nb * npair) {
-        const int i = e / npair, j = 2 * (e % npair);
-        Ls[i * ld + j] = (j <= i) ? f64_to_f32_rn(d[q].x) : 0.f;
-        Ls[i * ld + j + 1] = (j + 1 <= i) ? f64_to_f32_rn(d[q].y) : 0.f;
-        Xs[i * ld + j] = 0.f;
-        Xs[i * ld + j + 1] = 0.f;
-      }
-    }
-  }
-  __syncthreads();
+  const int nblk = nb / 32;
   if (w < nblk) {  // diagonal blocks
     const int d0 = 32 * w;
     float x[32];
@@ -254,21 +242,21 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
     for (int i = 0; i < 32; ++i) {
       float acc = (i == lane) ? 1.f : 0.f;
 #pragma unroll
-      for (int k = 0; k < i; ++k) acc = fmaf(-Ls[(d0 + i) * ld + d0 + k], x[k], acc);
-      x[i] = acc / Ls[(d0 + i) * ld + d0 + i];
+      for (int k = 0; k < i; ++k) acc = fmaf(-Ls[(d0 + i) * lds + d0 + k], x[k], acc);
+      x[i] = acc / Ls[(d0 + i) * lds + d0 + i];
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) Xs[(d0 + i) * ld + d0 + lane] = x[i];
+    for (int i = 0; i < 32; ++i) Xs[(d0 + i) * ldx + d0 + lane] = x[i];
   }
   __syncthreads();
   for (int bi = 1; bi < nblk; ++bi) {
     // W_bj = sum_{bj <= k < bi} L_{bi,k} X_{k,bj}, parked in the (still zero) slots X_{bi,bj}
     for (int e = t; e < bi * 1024; e += kThreads) {
       const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
-      const float* lrow = Ls + (32 * bi + r) * ld;
+      const float* lrow = Ls + (32 * bi + r) * lds;
       float acc = 0.f;
-      for (int kk = 32 * bj; kk < 32 * bi; ++kk) acc = fmaf(lrow[kk], Xs[kk * ld + 32 * bj + c], acc);
-      Xs[(32 * bi + r) * ld + 32 * bj + c] = acc;
+      for (int kk = 32 * bj; kk < 32 * bi; ++kk) acc = fmaf(lrow[kk], Xs[kk * ldx + 32 * bj + c], acc);
+      Xs[(32 * bi + r) * ldx + 32 * bj + c] = acc;
     }
     __syncthreads();
     // X_{bi,bj} = -X_{bi,bi} W_bj (through registers: W is read in place)
@@ -279,9 +267,9 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
       res[q] = 0.f;
       if (e < bi * 1024) {
         const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
-        const float* xrow = Xs + (32 * bi + r) * ld + 32 * bi;
+        const float* xrow = Xs + (32 * bi + r) * ldx + 32 * bi;
         float acc = 0.f;
-        for (int k = 0; k <= r; ++k) acc = fmaf(xrow[k], Xs[(32 * bi + k) * ld + 32 * bj + c], acc);
+        for (int k = 0; k <= r; ++k) acc = fmaf(xrow[k], Xs[(32 * bi + k) * ldx + 32 * bj + c], acc);
         res[q] = -acc;
       }
     }
@@ -291,7 +279,7 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
       const int e = t + q * kThreads;
       if (e < bi * 1024) {
         const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
-        Xs[(32 * bi + r) * ld + 32 * bj + c] = res[q];
+        Xs[(32 * bi + r) * ldx + 32 * bj + c] = res[q];
       }
     }
     __syncthreads();
@@ -304,8 +292,8 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
       const int r = e >> 4, kp = e & 15;
       float f0 = 0.f, f1 = 0.f;
       if (r < nb) {
-        f0 = Xs[r * ld + kc * kUmmaKChunk + 2 * kp];
-        f1 = Xs[r * ld + kc * kUmmaKChunk + 2 * kp + 1];
+        f0 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp];
+        f1 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp + 1];
       }
       const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
       const uint32_t off = sw128_offset(r, 2 * kp);
@@ -315,6 +303,25 @@ __device__ void cta_inverse_pack(const double* L, int ldl, int nb, float* sm, ui
   }
   fence_proxy_async_global();
   __syncthreads();
+}
+
+// The inverse of a factored diagonal tile still held in shared memory as FP64 (sL, leading dimension
+// nb + 1, the layout cta_potrf_smem leaves behind at the start of `smem`): converted to FP32 beside it
+// (smem + nb (nb + 1) 8 bytes, leading dimension nb), then the FP32 workspace takes the FP64 tile's
+// place. Needs nb (nb + 1) 8 + nb nb 4 bytes of shared memory; no global reads.
+__device__ void cta_inverse_pack_smem(uint8_t* smem, int nb, uint8_t* dst) {
+  const int t = threadIdx.x, ldl = nb + 1;
+  const double* sL = reinterpret_cast<const double*>(smem);
+  float* Ls = reinterpret_cast<float*>(smem + (size_t)nb * ldl * 8);
+  float* Xs = reinterpret_cast<float*>(smem);
+  for (int e = t; e < nb * nb; e += kThreads) {
+    const int i = e / nb, j = e % nb;
+    Ls[i * nb + j] = (j <= i) ? f64_to_f32_rn(sL[i * ldl + j]) : 0.f;
+  }
+  __syncthreads();  // the FP64 tile is dead from here: Xs reuses its bytes
+  for (int e = t; e < nb * ldl; e += kThreads) Xs[e] = 0.f;
+  __syncthreads();
+  cta_inverse_core(Ls, nb, Xs, ldl, nb, dst);
 }
 
 }  // namespace gpk

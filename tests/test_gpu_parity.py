@@ -210,3 +210,42 @@ def test_full_size_sampled(api):
     cref = oracle.assemble_prior(Xs[cols], H0) - V.T @ V
     c = cov.cpu().numpy()[np.ix_(cols, cols)]
     assert rel(c, cref) <= 1e-9
+
+
+def test_full_size_sampled_mixed(api):
+    """The mixed-precision form of the large workload (n = 32768, m = 4096, D = 8) in the benchmark's
+    launch configuration (tile 128, tensor cores, packed operands, FP64 refinement), checked at sampled
+    entries against the oracle: LL^T = K to the FP32-class bound, the refined solution's residual
+    y - K alpha to the FP64 bar and the mean from alpha to 1e-10, and sampled covariance entries against
+    k(a,b) - v_a^T v_b with v_a = L^{-1} k_a by the oracle's FP64 forward substitution on the GPU's own
+    factor (what remains is the FP32-class error of the V solve and of V^T V). That error is bounded in
+    absolute terms against the prior scale v: Sigma = K** - V^T V cancels at that scale, and test
+    points near the data have posterior entries far below it."""
+    n, m, D = 32768, 4096, 8
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
+    ctx = api.Context(0, precision="fp32")
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    mean, iters = api.gp_predict_mean(ctx, f, yd, Xsd, want_iters=True)
+    alpha = api.gp_alpha(ctx, f).cpu().numpy()
+    cov = api.gp_predict_full_cov(ctx, f, Xsd)
+    api.gp_sync(ctx)
+    assert 1 <= iters <= 10
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(n, 24, replace=False))
+    Lrows = np.concatenate([api.gp_factor_rows(ctx, f, int(r), 1).cpu().numpy() for r in rows])
+    ii, jj = np.meshgrid(np.arange(len(rows)), np.arange(len(rows)), indexing="ij")
+    Kij = oracle.kernel_entries(X, X, rows[ii.ravel()], rows[jj.ravel()], rows[ii.ravel()] == rows[jj.ravel()], H0)
+    assert rel((Lrows @ Lrows.T).ravel(), Kij) <= 2e-5
+    r = y[rows] - oracle.kernel_rows_matvec(X, rows, alpha, H0)
+    assert np.max(np.abs(r)) <= 1e-9 * np.max(np.abs(y))
+    cols = np.sort(rng.choice(m, 16, replace=False))
+    mref = oracle.assemble_cross(Xs[cols], X, H0) @ alpha
+    assert rel(mean.cpu().numpy()[cols], mref) <= 1e-10
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    ks = oracle.assemble_cross(Xs[cols], X, H0)
+    V = oracle.forward(L, np.ascontiguousarray(ks.T))
+    cref = oracle.assemble_prior(Xs[cols], H0) - V.T @ V
+    c = cov.cpu().numpy()[np.ix_(cols, cols)]
+    assert np.max(np.abs(c - cref)) <= 1e-4 * H0[1]
