@@ -120,7 +120,8 @@ class Factor:
 
 
 TASK_NAMES = ["POTRF", "TRSM", "UPDATE", "VTRSM", "VGEMM", "WSYRK", "FSOLVE", "FGEMV", "BSOLVE", "BGEMV",
-              "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI", "VGEMM_G", "WSYRK_G"]
+              "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI", "VGEMM_G", "WSYRK_G",
+              "FSOLVE_C", "BSOLVE_C"]
 
 
 def gp_trace(ctx: Context):

@@ -97,6 +97,7 @@ struct gp_factor {
   DevBuf Kt, cK;              // packed lower tiles and their counters
   DevBuf Kt0;                 // mixed precision: FP64 copy of K for the refinement residual
   DevBuf bvec, cMean;         // solve work vector (rhs -> beta -> solution), and the solve counters
+  DevBuf xvec;                // second solve vector (the forward result of the chunked vector solves)
   DevBuf Linv;                // inverses of the diagonal tiles of L (written by the Cholesky launch)
   DevBuf Pk, PV;              // mixed mode with tensor cores: packed operands of the panel tiles and of V
   DevBuf PLinv;               // mixed mode, T = 128: packed FP32 inverses of the diagonal tiles
@@ -204,8 +205,10 @@ gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
   GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
   const TaskBuf* tb;
   GP_TRY(get_tasks(c, 2, Mt, 0, T, false, &tb));
+  GP_TRY(grow(f->xvec, (size_t)Mt * T * sizeof(double)));
   gpk::DagArgs a = base_args(c, f);
   a.bvec = (double*)f->bvec.p;
+  a.xvec = (double*)f->xvec.p;
   a.Linv = (double*)f->Linv.p;  // diagonal-block solves as products with the stored inverses
   int* cm = (int*)f->cMean.p;
   a.cF = cm;
@@ -393,6 +396,7 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->cRev);
   release(f->beta);
   release(f->bvec);
+  release(f->xvec);
   release(f->cMean);
   release(f->Linv);
   release(f->Pk);

@@ -79,6 +79,16 @@ __device__ __forceinline__ void cta_publish(int* counter, int value) {
   }
 }
 
+// Publishes a CTA's results by adding 1 to a counter that several CTAs complete together (the
+// fence before the add makes every thread's stores visible first, as in cta_publish).
+__device__ __forceinline__ void cta_publish_add(int* counter) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1);
+  }
+}
+
 // L2-only load (bypasses L1, so data written by other SMs after an acquire is never stale).
 template <class T>
 __device__ __forceinline__ T ldcg(const T* p) {

@@ -172,8 +172,20 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
       return true;
     }
     case TASK_FGEMV:  // (I=p, J=q, ch=r)
-      return wait_ge(a.cK + tri(p, q), q + 1, st, to, ti) && wait_ge(a.dF + q, 1, st, to, ti) &&
+      return wait_ge(a.cK + tri(p, q), q + 1, st, to, ti) && wait_ge(a.dF + q, a.xvec ? a.nch : 1, st, to, ti) &&
              wait_ge(a.cF + (size_t)p * a.nch + r, q, st, to, ti);
+    case TASK_FSOLVE_C: {  // (J=p, ch=q): every chunk of block J has all its updates
+      if (!wait_ge(a.cK + tri(p, p), p + 1, st, to, ti)) return false;
+      for (int ch = 0; ch < a.nch; ++ch)
+        if (!wait_ge(a.cF + (size_t)p * a.nch + ch, p, st, to, ti)) return false;
+      return true;
+    }
+    case TASK_BSOLVE_C: {  // (J=p, ch=q): forward block J done, every chunk of xvec_J has its updates
+      if (!wait_ge(a.dF + p, a.nch, st, to, ti)) return false;
+      for (int ch = 0; ch < a.nch; ++ch)
+        if (!wait_ge(a.cB + (size_t)p * a.nch + ch, a.Mt - 1 - p, st, to, ti)) return false;
+      return true;
+    }
     case TASK_BSOLVE: {  // (J=p)
       if (!wait_ge(a.dF + p, 1, st, to, ti)) return false;
       for (int ch = 0; ch < a.nch; ++ch)
@@ -181,8 +193,9 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
       return true;
     }
     case TASK_BGEMV:  // (J=p, I=q, ch=r)
-      return wait_ge(a.cK + tri(q, p), p + 1, st, to, ti) && wait_ge(a.dB + q, 1, st, to, ti) &&
-             wait_ge(a.dF + p, 1, st, to, ti) && wait_ge(a.cB + (size_t)p * a.nch + r, a.Mt - 1 - q, st, to, ti);
+      return wait_ge(a.cK + tri(q, p), p + 1, st, to, ti) && wait_ge(a.dB + q, a.xvec ? a.nch : 1, st, to, ti) &&
+             wait_ge(a.dF + p, a.xvec ? a.nch : 1, st, to, ti) &&
+             wait_ge(a.cB + (size_t)p * a.nch + r, a.Mt - 1 - q, st, to, ti);
     case TASK_RUPD: {  // (P=p, K=q, J=r); terms applied with K descending
       const int hi = p > q ? p : q, lo = p > q ? q : p;
       return wait_ge(a.fa + tri(hi, lo), 1, st, to, ti) && wait_ge(a.rc + tri(p, r), a.Mt - 1 - q, st, to, ti);
@@ -502,10 +515,20 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsv_lower(a.Kt + tri(p, p) * TT, T, a.bvec + (size_t)p * T, T, &s_red[0][0], s.tri);
         cta_publish(a.dF + p, 1);
         break;
-      case TASK_FGEMV:
-        cta_gemv_sub(a.Kt + tri(p, q) * TT + (size_t)r * 32 * T, T, a.bvec + (size_t)q * T,
+      case TASK_FGEMV:  // b_I[ch] -= L_IJ[ch, :] x_J, x_J in xvec for the chunked solves
+        cta_gemv_sub(a.Kt + tri(p, q) * TT + (size_t)r * 32 * T, T, (a.xvec ? a.xvec : a.bvec) + (size_t)q * T,
                      a.bvec + (size_t)p * T + r * 32, 32, T);
         cta_publish(a.cF + (size_t)p * a.nch + r, q + 1);
+        break;
+      case TASK_FSOLVE_C:  // xvec_J[ch] = Linv_J[ch rows, :] bvec_J
+        cta_gemv_sub<true>(a.Linv + (size_t)p * TT + (size_t)q * 32 * T, T, a.bvec + (size_t)p * T,
+                           a.xvec + (size_t)p * T + q * 32, 32, T);
+        cta_publish_add(a.dF + p);
+        break;
+      case TASK_BSOLVE_C:  // bvec_J[ch] = sum_r Linv_J[r][ch cols] xvec_J[r]
+        cta_gemv_T_sub<true>(a.Linv + (size_t)p * TT + q * 32, T, a.xvec + (size_t)p * T,
+                             a.bvec + (size_t)p * T + q * 32, T, 32, s_red);
+        cta_publish_add(a.dB + p);
         break;
       case TASK_BSOLVE:
         if (a.Linv)
@@ -517,9 +540,9 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       case TASK_TRTRI:  // read by later launches only: nothing to publish
         cta_trtri(a.Kt + tri(p, p) * TT, T, a.Linv + (size_t)p * TT, T, s);
         break;
-      case TASK_BGEMV:
+      case TASK_BGEMV:  // b_J[ch] -= L_IJ[:, ch]^T x_I; chunked solves: xvec_J[ch] -= L_IJ[:, ch]^T bvec_I
         cta_gemv_T_sub(a.Kt + tri(q, p) * TT + (size_t)r * 32, T, a.bvec + (size_t)q * T,
-                       a.bvec + (size_t)p * T + r * 32, T, 32, s_red);
+                       (a.xvec ? a.xvec : a.bvec) + (size_t)p * T + r * 32, T, 32, s_red);
         cta_publish(a.cB + (size_t)p * a.nch + r, a.Mt - q);
         break;
       }

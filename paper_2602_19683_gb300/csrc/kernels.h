@@ -32,7 +32,11 @@ enum TaskKind {
   // Grouped covariance products of the mixed mode on the tensor cores (one pass over the output tile
   // for several J; never part of a batched launch):
   TASK_VGEMM_G = 15,  // (I, c, J0 | J1 << 16)  V_Ic -= sum_{J0 <= J < J1} L_IJ V_Jc
-  TASK_WSYRK_G = 16   // (a, b, J0 | J1 << 16)  S_ab -= sum_{J0 <= J < J1} V_Ja^T V_Jb
+  TASK_WSYRK_G = 16,  // (a, b, J0 | J1 << 16)  S_ab -= sum_{J0 <= J < J1} V_Ja^T V_Jb
+  // Vector solves with the stored inverses, each diagonal block split into 32-row chunks that run in
+  // parallel (a second vector, xvec, holds the forward result so no chunk overwrites what another reads):
+  TASK_FSOLVE_C = 17,  // (J, ch)  xvec_J[ch] = Linv_J[ch, :] bvec_J
+  TASK_BSOLVE_C = 18   // (J, ch)  bvec_J[ch] = (Linv_J^T)[ch, :] xvec_J
 };
 
 // One GP of a batch: its inputs, outputs, hyperparameters and workspace (all device pointers).
@@ -75,6 +79,8 @@ struct DagArgs {
   long long lds;
   double* bvec;     // Mt*T vector: y on entry, beta then alpha
   double* Linv;     // Mt x T x T: inverses of the diagonal tiles of L (null: solves by substitution)
+  double* xvec;     // Mt*T vector of the chunked solves (forward result; non-null: FSOLVE_C/BSOLVE_C graph,
+                    // whose per-block completion counters dF/dB count chunks up to nch)
   uint8_t* Pk;      // mixed mode: packed tensor-core operands of the panel tiles L_IJ (I > J), same tile
                     // index as Kt, T*T*8 bytes each (null: operands staged from FP64 per update)
   uint8_t* PV;      // mixed mode: packed operands of the blocks V_Jc (transposed), (J*Mc + c)*T*T*8 bytes

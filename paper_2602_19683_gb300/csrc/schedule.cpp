@@ -355,40 +355,34 @@ std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, i
 std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm) {
   Builder b;
   const int nch = T / 32;
-  const double c_solve = cm.task_overhead + cm.sec_per_flop * (double)T * T / cm.vec_eff;
+  // Each diagonal block is solved as nch 32-row chunks in parallel (products with the stored inverse
+  // of the diagonal tile); the updates of the blocks further down are 32-row GEMV chunks.
+  const double c_solve = cm.task_overhead + cm.sec_per_flop * 2.0 * 32.0 * T / cm.vec_eff;
   const double c_gemv = cm.task_overhead + cm.sec_per_flop * 2.0 * 32.0 * T / cm.vec_eff;
-  std::vector<int> lastF((size_t)Mt * nch, -1), lastB((size_t)Mt * nch, -1), fsolve(Mt, -1);
+  std::vector<int> lastF((size_t)Mt * nch, -1), lastB((size_t)Mt * nch, -1);
+  std::vector<std::vector<int>> fsolve(Mt), bsolve(Mt);
   for (int J = 0; J < Mt; ++J) {
-    std::vector<int> d;
-    int fs;
-    {
-      b.tasks.push_back({TASK_FSOLVE, J, 0, 0});
-      b.cost.push_back(c_solve);
-      std::vector<int> pr;
-      for (int ch = 0; ch < nch; ++ch)
-        if (lastF[(size_t)J * nch + ch] >= 0) pr.push_back(lastF[(size_t)J * nch + ch]);
-      b.preds.push_back(pr);
-      fs = (int)b.tasks.size() - 1;
-    }
-    fsolve[J] = fs;
+    std::vector<int> pr;
+    for (int ch = 0; ch < nch; ++ch) pr.push_back(lastF[(size_t)J * nch + ch]);
+    for (int ch = 0; ch < nch; ++ch) fsolve[J].push_back(b.add_v(TASK_FSOLVE_C, J, ch, 0, c_solve, pr));
     for (int I = J + 1; I < Mt; ++I)
-      for (int ch = 0; ch < nch; ++ch)
-        lastF[(size_t)I * nch + ch] = b.add(TASK_FGEMV, I, J, ch, c_gemv, {fs, lastF[(size_t)I * nch + ch]});
+      for (int ch = 0; ch < nch; ++ch) {
+        std::vector<int> d(fsolve[J]);
+        d.push_back(lastF[(size_t)I * nch + ch]);
+        lastF[(size_t)I * nch + ch] = b.add_v(TASK_FGEMV, I, J, ch, c_gemv, d);
+      }
   }
   for (int I = Mt - 1; I >= 0; --I) {
-    int bs;
-    {
-      b.tasks.push_back({TASK_BSOLVE, I, 0, 0});
-      b.cost.push_back(c_solve);
-      std::vector<int> pr{fsolve[I]};
-      for (int ch = 0; ch < nch; ++ch)
-        if (lastB[(size_t)I * nch + ch] >= 0) pr.push_back(lastB[(size_t)I * nch + ch]);
-      b.preds.push_back(pr);
-      bs = (int)b.tasks.size() - 1;
-    }
+    std::vector<int> pr(fsolve[I]);
+    for (int ch = 0; ch < nch; ++ch) pr.push_back(lastB[(size_t)I * nch + ch]);
+    for (int ch = 0; ch < nch; ++ch) bsolve[I].push_back(b.add_v(TASK_BSOLVE_C, I, ch, 0, c_solve, pr));
     for (int J = 0; J < I; ++J)
-      for (int ch = 0; ch < nch; ++ch)
-        lastB[(size_t)J * nch + ch] = b.add(TASK_BGEMV, J, I, ch, c_gemv, {bs, fsolve[J], lastB[(size_t)J * nch + ch]});
+      for (int ch = 0; ch < nch; ++ch) {
+        std::vector<int> d(bsolve[I]);
+        d.insert(d.end(), fsolve[J].begin(), fsolve[J].end());
+        d.push_back(lastB[(size_t)J * nch + ch]);
+        lastB[(size_t)J * nch + ch] = b.add_v(TASK_BGEMV, J, I, ch, c_gemv, d);
+      }
   }
   return b.ordered(workers);
 }

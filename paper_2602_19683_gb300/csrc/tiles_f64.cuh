@@ -665,8 +665,9 @@ __device__ void cta_trsv_inv_T(const double* Linv, int ld, double* b, int nb, do
 // Entries above the diagonal stay exactly zero.
 __device__ void cta_trtri(const double* L, int ldl, double* Linv, int nb, TileSmem& s);
 
-// b[r] -= sum_c A[r][c] x[c] for r in [0, rows): each warp takes four rows at a time, lanes over
-// columns, so the loads of the four rows are in flight together.
+// b[r] -= sum_c A[r][c] x[c] for r in [0, rows) (kSet: b[r] = sum ...): each warp takes four rows at a
+// time, lanes over columns, so the loads of the four rows are in flight together.
+template <bool kSet = false>
 __device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* b, int rows, int cols) {
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   for (int r0 = 4 * w; r0 < rows; r0 += 4 * (kThreads / 32)) {
@@ -686,14 +687,15 @@ __device__ void cta_gemv_sub(const double* A, int lda, const double* x, double* 
     }
     if (lane < nr) {
       const double v = lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3];
-      b[r0 + lane] = ldcg(b + r0 + lane) - v;
+      b[r0 + lane] = kSet ? v : ldcg(b + r0 + lane) - v;
     }
   }
   __syncthreads();
 }
 
-// b[c] -= sum_r A[r][c] x[r] for c in [0, cols) with cols <= 32: warps split the rows, lanes own
-// columns, partial sums reduced through smem (red[8][32]).
+// b[c] -= sum_r A[r][c] x[r] for c in [0, cols) with cols <= 32 (kSet: b[c] = sum ...): warps split the
+// rows, lanes own columns, partial sums reduced through smem (red[8][32]).
+template <bool kSet = false>
 __device__ void cta_gemv_T_sub(const double* A, int lda, const double* x, double* b, int rows, int cols,
                                double (*red)[32]) {
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -714,7 +716,7 @@ __device__ void cta_gemv_T_sub(const double* A, int lda, const double* x, double
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
-    b[threadIdx.x] = ldcg(b + threadIdx.x) - s;
+    b[threadIdx.x] = kSet ? s : ldcg(b + threadIdx.x) - s;
   }
   __syncthreads();
 }

@@ -125,25 +125,27 @@ def test_cov_schedule_is_topological(lib, Mt, Mc, workers, mixed):
 
 @pytest.mark.parametrize("Mt,T,workers", [(1, 32, 1), (3, 64, 2), (6, 96, 304)])
 def test_mean_schedule_is_topological(lib, Mt, T, workers):
+    """L beta = y then L^T alpha = beta (Eq. 2): each diagonal block is solved in 32-row chunks after
+    every update of all its chunks; a block's updates of later blocks follow all its chunks."""
     t = tasks(lib, 2, Mt, 0, T, workers)
     nch = T // 32
-    cf, cb, df, db = {}, {}, set(), set()
+    cf, cb, df, db = {}, {}, {}, {}
     for kind, p, q, r in t:
-        if kind == 6:
+        if kind == 17:  # forward chunk q of block p
             assert all(cf.get((p, ch), 0) == p for ch in range(nch))
-            df.add(p)
+            df[p] = df.get(p, 0) + 1
         elif kind == 7:
-            assert q in df and cf.get((p, r), 0) == q and p > q
+            assert df.get(q, 0) == nch and cf.get((p, r), 0) == q and p > q
             cf[(p, r)] = q + 1
-        elif kind == 8:
-            assert p in df and all(cb.get((p, ch), 0) == Mt - 1 - p for ch in range(nch))
-            db.add(p)
+        elif kind == 18:  # backward chunk q of block p
+            assert df.get(p, 0) == nch and all(cb.get((p, ch), 0) == Mt - 1 - p for ch in range(nch))
+            db[p] = db.get(p, 0) + 1
         elif kind == 9:
-            assert q in db and p in df and cb.get((p, r), 0) == Mt - 1 - q and q > p
+            assert db.get(q, 0) == nch and df.get(p, 0) == nch and cb.get((p, r), 0) == Mt - 1 - q and q > p
             cb[(p, r)] = Mt - q
         else:
             raise AssertionError(kind)
-    assert df == db == set(range(Mt))
+    assert all(df[J] == nch and db[J] == nch for J in range(Mt))
 
 
 @pytest.mark.parametrize("Mt,workers,mixed", [(1, 2, 0), (2, 1, 0), (5, 7, 1), (9, 304, 0)])
