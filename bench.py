@@ -36,6 +36,19 @@ FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~
 FP64_CHOL_TRAFFIC_MT32_T256 = 2.083361e9 + 2.579202e9
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak for the 3xTF32 products: the measured BF16 peak of this GPU pool
+    (MEASURED_PEAKS.json, burst) times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); without the
+    file, the profiling recipe's fallback BF16 figure (1.9 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            bf16, src = float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        bf16, src = 1900.0, "fallback"
+    return bf16 * 1.1 / 2.25, f"{src} BF16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
+
+
 def fp64_cholesky_traffic(n: int, tile: int):
     if tile != 256:
         return None
@@ -351,8 +364,14 @@ def run_ours(args):
 
             def relerr(a, b):
                 return float((a - b).abs().max() / b.abs().max())
+            tf32_peak, tf32_src = tf32_peak_tflops()
+            executed = 3 * (n ** 3 / 3) / phase32[1] / 1e12  # three TF32 split products per update
             mixed = {"precision": "fp32 trailing updates, FP64 POTRF/first-column TRSM/refinement",
                      "tile": ctx_tile(n, args.tile, True),
+                     "roofline": {"kernel": "dag_kernel mixed (tiled Cholesky, 3xTF32 on tcgen05)", "bound": "tensor",
+                                  "achieved": executed, "peak": tf32_peak, "unit": "TFLOP/s",
+                                  "frac": executed / tf32_peak, "peak_source": tf32_src,
+                                  "algorithmic_tflops": (n ** 3 / 3) / phase32[1] / 1e12, "traffic": None},
                      "s_per_solve": ms32 / 1e3, "tflops": algorithmic_flops(n, m) / (ms32 / 1e3) / 1e12,
                      "speedup_vs_fp64": ms / ms32, "ir_iterations": iters[0],
                      "phases_s": {"assemble": phase32[0], "cholesky": phase32[1], "mean_refined": phase32[2],

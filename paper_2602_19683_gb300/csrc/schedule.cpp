@@ -96,11 +96,20 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   Builder b;
   const double t3 = (double)T * T * T;
   const double spf_upd = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
-  const double c_potrf = cm.task_overhead + cm.sec_per_flop * t3 / 3.0 / cm.potrf_eff;
-  const double c_trsm0 = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
-  const double c_trsm = cm.task_overhead + spf_upd * t3 / cm.trsm_eff;
-  const double c_gemm = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
-  const double c_syrk = cm.task_overhead + spf_upd * (t3 + 64.0 * T * T) / cm.gemm_eff;
+  double c_potrf = cm.task_overhead + cm.sec_per_flop * t3 / 3.0 / cm.potrf_eff;
+  double c_trsm0 = cm.task_overhead + cm.sec_per_flop * t3 / cm.trsm_eff;
+  double c_trsm = cm.task_overhead + spf_upd * t3 / cm.trsm_eff;
+  double c_gemm = cm.task_overhead + spf_upd * 2.0 * t3 / cm.gemm_eff;
+  double c_syrk = cm.task_overhead + spf_upd * (t3 + 64.0 * T * T) / cm.gemm_eff;
+  if (cm.tensor_cores) {  // measured at T = 128: POTRF + FP32 inverse 403 us, FP64 TRSM 440 us, tensor
+                          // TRSM 30 us, one column pair of a grouped update 6.6 us (5 us on the diagonal)
+    const double s3 = t3 / (128.0 * 128.0 * 128.0), s2 = (double)T * T / (128.0 * 128.0);
+    c_potrf = 403e-6 * s3;
+    c_trsm0 = 440e-6 * s3;
+    c_trsm = 30e-6 * s2;
+    c_gemm = 6.6e-6 * s2;
+    c_syrk = 5.0e-6 * s2;
+  }
   // Updates of a tile whose critical use is still far away are grouped: columns [J0, J1) in one task
   // (one pass over the tile's C instead of J1 - J0); the last kTail columns before the tile is needed
   // stay single so the critical path is not lengthened.
@@ -146,8 +155,13 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
   Builder b;
   const double t3 = (double)T * T * T;
   const double spf = cm.mixed ? cm.sec_per_flop32 : cm.sec_per_flop;
-  const double c_trsm = cm.task_overhead + spf * t3 / cm.trsm_eff;
-  const double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
+  double c_trsm = cm.task_overhead + spf * t3 / cm.trsm_eff;
+  double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
+  if (cm.tensor_cores) {  // measured at T = 128: V solve 35 us, one column pair of a grouped product 5.5 us
+    const double s2 = (double)T * T / (128.0 * 128.0);
+    c_trsm = 35e-6 * s2;
+    c_gemm = 5.5e-6 * s2;
+  }
   // Mixed mode on the tensor cores groups the products into one output tile: V_Ic takes columns
   // [J0, J1) together while they are far from its own solve (the last kTail one by one, as they
   // gate the solve chain); S_ab takes every g consecutive J together.

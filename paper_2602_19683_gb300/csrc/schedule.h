@@ -15,6 +15,10 @@ struct CostModel {
   double sec_per_flop32 = 1.0 / 3.0e11;  // FP32 work (mixed mode): one CTA per SM
   bool mixed = false;                    // trailing updates / later panel TRSMs / V solve in FP32
   int update_group = 1;                  // trailing updates per task for tiles off the critical path
+  // Mixed mode on the tensor cores (packed operands, T a multiple of 128): task costs measured on
+  // GB300 at T = 128 (per-task trace at n = 32768) replace the flop-rate model, scaled by (T/128)^3
+  // for the FP64 work and (T/128)^2 for the memory-bound products.
+  bool tensor_cores = false;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
 };
