@@ -30,10 +30,10 @@ sys.path.insert(0, ROOT)
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~2 GHz on 152 SMs)
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one FP64 Cholesky launch of the task-DAG
-# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.083 GB read + 2.579 GB written
+# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.072 GB read + 2.594 GB written
 # (profiles/dag_kernel_fp64_cholesky_n32768.md). Traffic follows the number of tile updates,
 # (Mt^3 - Mt)/6, so a launch with Mt tile rows of edge 256 moves this times updates(Mt)/updates(32).
-FP64_CHOL_TRAFFIC_MT32_T256 = 2.083361e9 + 2.579202e9
+FP64_CHOL_TRAFFIC_MT32_T256 = 2.072146688e9 + 2.593921536e9
 
 
 def tf32_peak_tflops():
