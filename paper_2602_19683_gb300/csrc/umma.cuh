@@ -111,9 +111,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 // Per-CTA state of the tensor-core path (lives in the persistent kernel for its whole run).
 struct UmmaState {
-  uint8_t* smem;       // 1024-aligned dynamic shared memory, 2 stages
+  uint8_t* smem;       // 1024-aligned dynamic shared memory: 2 register-staged or kPkStages packed stages
   uint64_t* bar;       // 2 mbarriers (smem)
-  uint32_t tmem;       // TMEM base address (128 columns)
+  uint32_t tmem;       // TMEM base address (kUmmaTmemCols columns: two 128-column accumulators)
   uint32_t phase[2];   // next parity to wait for, per stage
   uint32_t pending[2]; // stage has an uncompleted commit
   // packed-operand pipeline (umma_packed.cuh): per stage, a "full" barrier completed by the bulk
