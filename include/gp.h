@@ -26,6 +26,12 @@
  *     context and the factor objects, allocated with cudaMalloc when they are created or grown.
  *   - Nothing traps: every device-side wait is bounded by cfg.timeout_ns and ends with
  *     GP_ERR_TIMEOUT instead of hanging.
+ *   - Input values are checked on the device: a NaN or infinity in X (gp_assemble), y or Xs
+ *     (gp_predict_mean), or Xs (gp_predict_full_cov, gp_predict_var) raises GP_ERR_NONFINITE in the
+ *     status word with info = 1-based flat index of the first such entry (for gp_predict_mean: y's
+ *     n entries first, then Xs's m*D). The first device error of a context stops every later
+ *     persistent-kernel launch on it (their tasks are skipped) until gp_sync returns and clears it.
+ *     The batched entry points and gp_predict_mean_noalloc do not check input values.
  */
 #ifndef GP_H_
 #define GP_H_
@@ -41,7 +47,7 @@ enum {
   GP_OK = 0,
   GP_ERR_INVALID_ARG = 1,     /* bad size, null pointer, unsupported option                     */
   GP_ERR_NOT_PD = 2,          /* a Cholesky pivot was not positive; info = 1-based column       */
-  GP_ERR_NONFINITE = 3,       /* NaN/Inf in an input or a pivot                                 */
+  GP_ERR_NONFINITE = 3,       /* NaN/Inf in an input (a NaN pivot reports GP_ERR_NOT_PD)        */
   GP_ERR_OOM = 4,             /* cudaMalloc failed                                               */
   GP_ERR_CUDA = 5,            /* another CUDA runtime error (launch, copy)                      */
   GP_ERR_TIMEOUT = 6,         /* a bounded device wait expired (scheduler dependency not met)   */
@@ -119,7 +125,9 @@ gp_status gp_cholesky(gp_ctx* ctx, gp_factor* K);
 /* Eq. (2): mean[0..m) = K_{Xs,X} K^{-1} y, using the factor L from gp_cholesky. y and Xs are device
  * arrays (n and m x D). With GP_FP32 precision the solve is refined in FP64 against the stored FP64
  * K; *ir_iters_out (host, may be NULL) receives the iteration count, which makes this call wait for
- * the stream. alpha = K^{-1} y stays in the factor for gp_nlml. */
+ * the stream. With GP_FP32 the call waits for the stream at every refinement step; it stops refining
+ * at the first device error (left in the status word for gp_sync) and returns GP_ERR_NONFINITE for a
+ * non-finite residual without one. alpha = K^{-1} y stays in the factor for gp_nlml. */
 gp_status gp_predict_mean(gp_ctx* ctx, gp_factor* L, const double* y, const double* Xs, int64_t m,
                           double* mean_out, int32_t* ir_iters_out);
 
@@ -183,6 +191,11 @@ gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp
  * NOT_PD info holds the GP index in its high 32 bits and the column in the low 32 bits). */
 gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
 gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
+/* Sets the schedule of later gp_batch_create calls: cfg.batch_order (0 or 1) and
+ * cfg.batch_ctas_per_sm (0..2), as gp_create validates them (GP_ERR_INVALID_ARG otherwise). For a
+ * schedule chosen earlier by gp_batch_autotune and kept by the caller (the Python binding's JSON
+ * cache). Host only. */
+gp_status gp_set_batch_schedule(gp_ctx* ctx, int32_t order, int32_t ctas_per_sm);
 
 /* Autotuner of the batched path (not in the paper, whose tile count is fixed per run): chooses each
  * GP's tile edge and the batch's schedule by timing them on this GPU.
@@ -268,6 +281,12 @@ const char* gp_status_string(gp_status s);
 
 /* Number of kernel launches the library has enqueued on this context so far. */
 int64_t gp_launch_count(const gp_ctx* ctx);
+
+/* TEST HOOK (host-side fault injection): counting device allocations from this call on, the k-th one
+ * made by any context of the process fails as cudaMalloc would, and the entry point that needed it
+ * returns GP_ERR_OOM with its objects left valid (retry after freeing memory); k <= 0 turns it off.
+ * Not thread-safe against concurrent calls into the library. */
+void gp_debug_fail_alloc(int64_t k);
 
 #ifdef __cplusplus
 }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "gp_batch_create": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(_P)], _I32),
     "gp_batch_run": ([_P, _P], _I32),
     "gp_batch_free": ([_P, _P], _I32),
+    "gp_set_batch_schedule": ([_P, _I32, _I32], _I32),
     "gp_batch_autotune": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(gp_autotune_opts),
                            ctypes.POINTER(gp_autotune_result)], _I32),
     "gp_factor_rows": ([_P, _P, _I64, _I64, _P], _I32),
@@ -70,6 +71,7 @@ SIGNATURES = {
     "gp_sync": ([_P, ctypes.POINTER(_I64)], _I32),
     "gp_status_string": ([_I32], ctypes.c_char_p),
     "gp_launch_count": ([_P], _I64),
+    "gp_debug_fail_alloc": ([_I64], None),
     "gp_trace": ([_P, _P, _I64], _I64),
     "gp_predict_mean_noalloc": ([_P, _P, _I64, _I32, gp_hyper, _P, _I64, _P, _P, ctypes.POINTER(_I64)], _I32),
     "gp_schedule_tasks": ([_I32, _I32, _I32, _I32, _I32, _I32, _P, _I64], _I64),

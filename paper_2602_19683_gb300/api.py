@@ -57,6 +57,7 @@ class Context:
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
                  tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0):
         self.lib = N.load()
+        self.precision = precision
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         cfg = N.gp_config()
@@ -147,6 +148,11 @@ def trace_to_chrome(rows, path: str):
         ev.append({"name": name, "ph": "X", "pid": 0, "tid": cta, "ts": (tr - t0) / 1e3, "dur": (td - tr) / 1e3})
     with open(path, "w") as fh:
         json.dump({"traceEvents": ev}, fh)
+
+
+def debug_fail_alloc(k: int) -> None:
+    """Test hook: the k-th device allocation of the library from now on fails (GP_ERR_OOM); 0 = off."""
+    N.load().gp_debug_fail_alloc(int(k))
 
 
 def gp_sync(ctx: Context) -> None:
@@ -282,10 +288,70 @@ def _batch_descs(gps, want_cov: bool):
     return descs, inputs, means, covs
 
 
+def _pow2_ceil(x: int) -> int:
+    return 1 << max(0, int(x) - 1).bit_length()
+
+
+def autotune_cache_key(gpu: str, precision: str, gps_shape, want_cov: bool, tiles=(), classes: int = 0) -> str:
+    """Key of a batch in the autotuner's JSON cache: the GPU's name, the precision, whether the
+    covariance is wanted, the search options, and the batch's shape in coarse buckets -- the GP count
+    and, for each of the autotuner's equal-count size classes (GPs sorted by n), its largest n, both
+    rounded up to powers of two; the set of input dimensions D; the largest m rounded up to a power
+    of two. gps_shape: (n, m, D) per GP."""
+    ns = sorted(int(n) for n, _, _ in gps_shape)
+    B = len(ns)
+    nc = min(classes if classes > 0 else 3, 8, B)
+    nmax = [ns[(k + 1) * B // nc - 1] for k in range(nc)]
+    ds = sorted({int(d) for _, _, d in gps_shape})
+    mmax = max(int(m) for _, m, _ in gps_shape)
+    cand = sorted({int(t) for t in tiles if t}) or [32, 64, 128, 256]
+    return (f"{gpu}|{precision}|cov{int(bool(want_cov))}|tiles{cand}|B{_pow2_ceil(B)}"
+            f"|n{[_pow2_ceil(x) for x in nmax]}|D{ds}|m{_pow2_ceil(mmax)}")
+
+
+def tiles_from_classes(classes, ns):
+    """Tile edge per GP from an autotuner class table [{"n_max", "tile"}, ...] (ascending n_max): a
+    GP takes the tile of the first class whose n_max >= n, beyond the last class the last one's."""
+    out = []
+    for n in ns:
+        t = classes[-1]["tile"]
+        for c in classes:
+            if n <= c["n_max"]:
+                t = c["tile"]
+                break
+        out.append(int(t))
+    return out
+
+
 def batch_autotune(ctx: Context, gps, want_cov: bool = True, tiles=(), classes: int = 0, sample: int = 0,
-                   reps: int = 0):
+                   reps: int = 0, cache_path: str | None = None):
     """Runs gp_batch_autotune on entries (X, y, Xs, hyper[, tile]). Returns (entries with the chosen
-    tile edge appended, report dict); the chosen schedule stays in the context for later Batch()es."""
+    tile edge appended, report dict); the chosen schedule stays in the context for later Batch()es.
+
+    cache_path: a JSON file of earlier choices keyed by autotune_cache_key (GPU name, precision,
+    batch-shape buckets). On a hit the cached class table and schedule are applied without timing
+    anything (report["cached"] is True); on a miss the search runs and its choice is added to the file."""
+    import json
+    import os
+    key = None
+    if cache_path:
+        shape = [(e[0].shape[0], e[2].shape[0], e[0].shape[1]) for e in gps]
+        key = autotune_cache_key(torch.cuda.get_device_name(ctx.device), ctx.precision, shape, want_cov, tiles,
+                                 classes)
+        try:
+            with open(cache_path) as fh:
+                cache = json.load(fh)
+        except (FileNotFoundError, ValueError):
+            cache = {}
+        hit = cache.get(key)
+        if hit:
+            if hit["default"]:  # the library's own rule won: no per-GP tile, default schedule
+                tl = [0] * len(gps)
+            else:
+                tl = tiles_from_classes(hit["classes"], [e[0].shape[0] for e in gps])
+            _check(ctx.lib.gp_set_batch_schedule(ctx.h, int(hit["order"]), int(hit["ctas_per_sm"])),
+                   "gp_set_batch_schedule")
+            return [tuple(e[:4]) + (t,) for e, t in zip(gps, tl)], dict(hit, cached=True)
     descs, inputs, means, covs = _batch_descs(gps, want_cov)
     o = N.gp_autotune_opts()
     for k, t in enumerate(list(tiles)[:6]):
@@ -298,9 +364,20 @@ def batch_autotune(ctx: Context, gps, want_cov: bool = True, tiles=(), classes: 
                         "sample_s": float(r.class_seconds[k])} for k in range(r.nclass)],
            "order": int(r.order), "ctas_per_sm": int(r.ctas_per_sm), "trials": int(r.trials),
            "seconds_tuned": float(r.seconds_tuned), "seconds_default": float(r.seconds_default),
-           "seconds_spent": float(r.seconds_spent)}
+           "seconds_spent": float(r.seconds_spent), "default": all(t[4] == 0 for t in tuned)}
     del inputs, means, covs
-    return tuned, rep
+    if cache_path:
+        try:
+            with open(cache_path) as fh:
+                cache = json.load(fh)
+        except (FileNotFoundError, ValueError):
+            cache = {}
+        cache[key] = rep
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return tuned, dict(rep, cached=False)
 
 
 class Batch:
@@ -353,22 +430,95 @@ def nlml(X, y, l, v, s2, ctx: Context):
     return GPNLML.apply(X, y, l, v, s2, ctx)
 
 
-def fit_adam(ctx: Context, X, y, theta0=(0.5, 2.0, 0.5), steps: int = 50, lr: float = 0.05, floor: float = 1e-6):
-    """Hyperparameter fitting with torch's Adam (textbook update, beta = (0.9, 0.999), eps = 1e-8) on
-    the raw (l, v, s2), each clamped to >= floor after every step. Returns [(theta, nlml, grad)]."""
-    params = [torch.tensor(float(t), dtype=torch.float64, device=X.device, requires_grad=True) for t in theta0]
+def _adam_log_read(path: str, theta0, steps: int):
+    """The complete step records of an Adam log, in order from step 0 (a torn last line, or anything
+    after the first unreadable line, is dropped)."""
+    import json
+    recs = []
+    try:
+        with open(path) as fh:
+            lines = fh.read().split("\n")
+    except FileNotFoundError:
+        return recs
+    for line in lines:
+        try:
+            r = json.loads(line)
+            ok = r["step"] == len(recs) and all(k in r for k in ("theta", "loss", "grad", "next", "adam"))
+        except (ValueError, KeyError, TypeError):
+            ok = False
+        if not ok:
+            break
+        recs.append(r)
+    if recs and [float(t) for t in recs[0]["theta"]] != [float(t) for t in theta0]:
+        raise ValueError(f"{path}: the log starts from {recs[0]['theta']}, not from {list(theta0)}")
+    return recs[:steps]
+
+
+def adam_fit(loss_fn, theta0, steps: int = 50, lr: float = 0.05, floor: float = 1e-6, device=None,
+             log_path: str | None = None, resume: bool = False):
+    """Adam (torch.optim.Adam, beta = (0.9, 0.999), eps = 1e-8) on raw parameters, each clamped to
+    >= floor after every step. loss_fn(params) takes the list of 0-d float64 parameter tensors and
+    returns a differentiable 0-d loss. Returns [(theta, loss, grad)], one entry per step.
+
+    Checkpoint and resume: with log_path, every step appends one flushed JSON line {step, theta, loss,
+    grad, next, adam}, where next holds the parameters after the step and adam the optimizer's
+    per-parameter state after it (JSON floats round-trip exactly). resume=True continues from the
+    last complete line of an existing log (a run that was cut off, even mid-line): parameters and
+    optimizer state are restored from it, so the resumed run repeats the uninterrupted run's
+    trajectory bit for bit. A log that starts from other parameters raises ValueError."""
+    import json
+    import os
+    theta0 = [float(t) for t in theta0]
+    recs = _adam_log_read(log_path, theta0, steps) if (log_path and resume) else []
+    start = [float(t) for t in recs[-1]["next"]] if recs else theta0
+    params = [torch.tensor(t, dtype=torch.float64, device=device, requires_grad=True) for t in start]
     opt = torch.optim.Adam(params, lr=lr, betas=(0.9, 0.999), eps=1e-8)
-    hist = []
-    for _ in range(steps):
-        opt.zero_grad()
-        loss = nlml(X, y, *params, ctx)
-        loss.backward()
-        hist.append(([float(p) for p in params], float(loss), [float(p.grad) for p in params]))
-        opt.step()
-        with torch.no_grad():
-            for p in params:
-                p.clamp_(min=floor)
+    if recs:
+        sd = opt.state_dict()
+        sd["state"] = {i: {"step": torch.tensor(float(a["step"]), dtype=torch.float32),
+                           "exp_avg": torch.tensor(float(a["exp_avg"]), dtype=torch.float64),
+                           "exp_avg_sq": torch.tensor(float(a["exp_avg_sq"]), dtype=torch.float64)}
+                       for i, a in enumerate(recs[-1]["adam"])}
+        opt.load_state_dict(sd)
+    hist = [([float(t) for t in r["theta"]], float(r["loss"]), [float(g) for g in r["grad"]]) for r in recs]
+    fh = None
+    if log_path:
+        tmp = log_path + ".tmp"  # the kept records only: drops a torn tail before appending
+        with open(tmp, "w") as out:
+            out.writelines(json.dumps(r) + "\n" for r in recs)
+        os.replace(tmp, log_path)
+        fh = open(log_path, "a")
+    try:
+        for k in range(len(recs), steps):
+            opt.zero_grad()
+            loss = loss_fn(params)
+            loss.backward()
+            theta = [p.item() for p in params]
+            grad = [p.grad.item() for p in params]
+            opt.step()
+            with torch.no_grad():
+                for p in params:
+                    p.clamp_(min=floor)
+            hist.append((theta, loss.item(), grad))
+            if fh:
+                st = [opt.state[p] for p in params]
+                rec = {"step": k, "theta": theta, "loss": loss.item(), "grad": grad, "next": [p.item() for p in params],
+                       "adam": [{"step": float(s["step"]), "exp_avg": float(s["exp_avg"]),
+                                 "exp_avg_sq": float(s["exp_avg_sq"])} for s in st]}
+                fh.write(json.dumps(rec) + "\n")
+                fh.flush()
+    finally:
+        if fh:
+            fh.close()
     return hist
+
+
+def fit_adam(ctx: Context, X, y, theta0=(0.5, 2.0, 0.5), steps: int = 50, lr: float = 0.05, floor: float = 1e-6,
+             log_path: str | None = None, resume: bool = False):
+    """Hyperparameter fitting of (l, v, s2) by adam_fit on the library's NLML (GPNLML: the gradient
+    from the blocked Cholesky adjoint), parameters on X's device. log_path / resume: checkpoint and
+    restart, as adam_fit describes. Returns [(theta, nlml, grad)]."""
+    return adam_fit(lambda p: nlml(X, y, *p, ctx), theta0, steps, lr, floor, X.device, log_path, resume)
 
 
 def predict(X, y, Xs, hyper=Hyper(), ctx: Context | None = None, full_cov: bool = True):

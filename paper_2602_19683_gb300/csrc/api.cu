@@ -1,6 +1,7 @@
 // C ABI of libgp (declared in include/gp.h): contexts, factor objects, workspace and the entry
 // points of the hot path (assembly, tiled Cholesky, mean and covariance prediction).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -22,12 +23,22 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Allocation-failure injection (gp_debug_fail_alloc): device allocations counted from the last call
+// of the hook; the one numbered g_fail_at fails as if cudaMalloc had (0 = off).
+std::atomic<long long> g_alloc_count{0}, g_fail_at{0};
+
+bool injected_failure() {
+  const long long at = g_fail_at.load();
+  return at > 0 && g_alloc_count.fetch_add(1) + 1 == at;
+}
+
 gp_status grow(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return GP_OK;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
   if (bytes == 0) return GP_OK;
+  if (injected_failure()) return GP_ERR_OOM;
   if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_OOM;
@@ -281,7 +292,7 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
     ctx->grid[mixed] = c.grid > 0 ? c.grid : ctx->sms * ctx->ctas_per_sm[mixed];
     if (c.grid > 0) ctx->ctas_per_sm[mixed] = (c.grid + ctx->sms - 1) / ctx->sms;
   }
-  if (cudaMalloc(&ctx->d_status, sizeof(gpk::DevStatus)) != cudaSuccess ||
+  if (injected_failure() || cudaMalloc(&ctx->d_status, sizeof(gpk::DevStatus)) != cudaSuccess ||
       cudaMalloc(&ctx->d_scalar, 64 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -320,6 +331,11 @@ gp_status gp_set_stream(gp_ctx* c, void* stream) {
 }
 
 int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
+
+void gp_debug_fail_alloc(int64_t k) {
+  g_alloc_count.store(0);
+  g_fail_at.store(k > 0 ? k : 0);
+}
 
 int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
   if (!c || !c->cfg.trace || !c->trace_tasks || c->trace_ntasks <= 0) return -1;
@@ -425,11 +441,19 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   }
   const size_t ntiles = (size_t)Mt * (Mt + 1) / 2;
   const bool mixed = c->cfg.precision == GP_FP32;
+  f->factored = false;  // a reused factor holds neither L nor alpha from here on, even if growing fails
+  f->alpha_valid = false;
   gp_status s = grow(f->Kt, ntiles * T * T * sizeof(double));
   if (s == GP_OK) s = grow(f->cK, ntiles * sizeof(int));
   if (s == GP_OK && mixed) s = grow(f->Kt0, ntiles * T * T * sizeof(double));
   if (s != GP_OK) {
-    if (fresh) gp_factor_free(c, f);
+    if (fresh) {
+      gp_factor_free(c, f);
+    } else {  // left empty: later calls on it fail with GP_ERR_INVALID_ARG until it is re-assembled
+      release(f->Kt);
+      release(f->cK);
+      release(f->Kt0);
+    }
     return s;
   }
   f->n = n;
@@ -441,8 +465,9 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   f->X = X;
   f->factored = false;
   f->alpha_valid = false;
+  GP_CUDA(gpk::launch_scan_nonfinite(X, n * D, 0, c->d_status, c->stream));
   GP_CUDA(gpk::launch_assemble_tiles(X, n, D, h.l, h.v, h.s2, (double*)f->Kt.p, T, (int)Mt, c->stream));
-  count_launch(c);
+  count_launch(c, 2);
   if (mixed)
     GP_CUDA(cudaMemcpyAsync(f->Kt0.p, f->Kt.p, ntiles * T * T * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   *K_out = f;
@@ -477,9 +502,14 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   const int T = f->T, Mt = f->Mt, nch = T / 32;
   const size_t npad = (size_t)Mt * T;
   const bool mixed = f->precision == GP_FP32;
+  f->alpha_valid = false;
   GP_TRY(grow(f->bvec, npad * sizeof(double)));
   GP_TRY(grow(f->alpha, npad * sizeof(double)));
   GP_TRY(grow(f->cMean, ((size_t)Mt * nch * 2 + (size_t)Mt * 2) * sizeof(int)));
+  // inputs: y, then Xs (info counts through both)
+  GP_CUDA(gpk::launch_scan_nonfinite(y, f->n, 0, c->d_status, c->stream));
+  if (m > 0) GP_CUDA(gpk::launch_scan_nonfinite(Xs, m * f->D, f->n, c->d_status, c->stream));
+  count_launch(c, m > 0 ? 2 : 1);
   // alpha = L^{-T} L^{-1} y (Eq. 2's two substitutions)
   GP_CUDA(cudaMemsetAsync(f->bvec.p, 0, npad * sizeof(double), c->stream));
   GP_CUDA(cudaMemcpyAsync(f->bvec.p, y, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -494,7 +524,7 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
     // than a halving per step) at a level <= 100 ir_tol (the attainable FP64 accuracy).
     GP_TRY(grow(f->rvec, npad * sizeof(double)));
     GP_TRY(grow(f->part, (size_t)6 * Mt * nch * sizeof(double)));
-    bool converged = false;
+    bool converged = false, device_error = false;
     double eta_prev = 0.0, knorm = 0.0;
     for (int it = 0;; ++it) {
       // ||K||_inf is the same every step: the first residual computes it, the later ones reuse it
@@ -502,13 +532,22 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
                                    (double*)f->bvec.p, (double*)f->part.p, c->d_scalar, c->stream, it == 0));
       count_launch(c, 2);
       double nr[6];
+      int32_t dev_code = 0;
       GP_CUDA(cudaMemcpyAsync(nr, c->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      GP_CUDA(cudaMemcpyAsync(&dev_code, &c->d_status->code, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
       GP_CUDA(cudaStreamSynchronize(c->stream));
+      if (dev_code != 0) {  // a device error (bad input, pivot, time-out): stays for gp_sync to report
+        device_error = true;
+        break;
+      }
       if (it == 0) knorm = nr[3];
       const double den = knorm * nr[4] + nr[5];
       const double eta = den > 0 ? nr[2] / den : 0.0;
       f->ir_eta = eta;
-      if (!(eta == eta)) break;  // NaN: the device status (if any) reports why
+      if (!(eta == eta)) {
+        result = GP_ERR_NONFINITE;
+        break;
+      }
       if (eta <= c->cfg.ir_tol) {
         converged = true;
         break;
@@ -524,7 +563,7 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
       count_launch(c);
       ++iters;
     }
-    if (!converged) result = GP_ERR_NO_CONVERGENCE;
+    if (!converged && !device_error && result == GP_OK) result = GP_ERR_NO_CONVERGENCE;
   }
   f->alpha_valid = true;
   if (m > 0) {
@@ -548,6 +587,8 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   GP_TRY(grow(f->S, ldv * ldv * sizeof(double)));
   const size_t ncnt = (size_t)Mt * Mc + (size_t)Mc * (Mc + 1) / 2;
   GP_TRY(grow(f->cCov, ncnt * sizeof(int)));
+  GP_CUDA(gpk::launch_scan_nonfinite(Xs, m * f->D, 0, c->d_status, c->stream));
+  count_launch(c);
   // Right-hand side K_{X,Xs} (n x m, zero padded) and the prior K_{Xs,Xs} (Eq. 3).
   GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
                                      (long long)npad, (long long)ldv, c->stream));
@@ -589,6 +630,8 @@ gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, d
   GP_TRY(grow(f->V, npad * ldv * sizeof(double)));
   const size_t ncnt = (size_t)Mt * Mc;
   GP_TRY(grow(f->cCov, ncnt * sizeof(int)));
+  GP_CUDA(gpk::launch_scan_nonfinite(Xs, m * f->D, 0, c->d_status, c->stream));
+  count_launch(c);
   GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
                                      (long long)npad, (long long)ldv, c->stream));
   count_launch(c);
@@ -854,6 +897,13 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     return cuda_status(e);
   }
   *out = b;
+  return GP_OK;
+}
+
+gp_status gp_set_batch_schedule(gp_ctx* c, int32_t order, int32_t ctas_per_sm) {
+  if (!c || order < 0 || order > 1 || ctas_per_sm < 0 || ctas_per_sm > 2) return GP_ERR_INVALID_ARG;
+  c->cfg.batch_order = order;
+  c->cfg.batch_ctas_per_sm = ctas_per_sm;
   return GP_OK;
 }
 

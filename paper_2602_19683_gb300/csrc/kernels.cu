@@ -730,6 +730,20 @@ __global__ void __launch_bounds__(kThreads) reduce_residual_kernel(const double*
 }
 
 // alpha[i] += d[i] for i < n.
+// Input check: any NaN or infinity among a[0..cnt) raises GP_ERR_NONFINITE with info = base + (index of
+// the first such entry) + 1 (1-based; the smallest index wins). The exponent field is tested with
+// integer operations, one warp ballot per 32 entries, one lane of a warp with a hit raises.
+__global__ void scan_nonfinite_kernel(const double* __restrict__ a, long long cnt, long long base,
+                                      DevStatus* st) {
+  for (long long i0 = (long long)blockIdx.x * kThreads; i0 < cnt; i0 += (long long)gridDim.x * kThreads) {
+    const long long i = i0 + threadIdx.x;
+    bool bad = false;
+    if (i < cnt) bad = ((__double_as_longlong(a[i]) >> 52) & 0x7ff) == 0x7ff;
+    const unsigned hit = __ballot_sync(0xffffffffu, bad);
+    if (hit && (int)(threadIdx.x & 31) == __ffs(hit) - 1) raise_error(st, GP_ERR_NONFINITE, base + i + 1);
+  }
+}
+
 __global__ void axpy_kernel(double* __restrict__ alpha, const double* __restrict__ d, long long n) {
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
     alpha[i] += d[i];
@@ -1181,6 +1195,14 @@ cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* 
 
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* out, cudaStream_t st) {
   dot_kernel<<<1, kThreads, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_nonfinite(const double* a, long long cnt, long long base, DevStatus* status,
+                                  cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  const long long b = (cnt + kThreads - 1) / kThreads;
+  scan_nonfinite_kernel<<<(unsigned)(b < 1216 ? b : 1216), kThreads, 0, st>>>(a, cnt, base, status);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,9 @@ int dag_max_ctas_per_sm(bool mixed);
 cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,
                             double* r, double* partial, double* norms, cudaStream_t st, bool with_knorm);
 cudaError_t launch_axpy(double* alpha, const double* d, long long n, cudaStream_t st);
+// NaN/Inf in a[0..cnt) -> GP_ERR_NONFINITE in the status word, info = base + first index + 1.
+cudaError_t launch_scan_nonfinite(const double* a, long long cnt, long long base, DevStatus* status,
+                                  cudaStream_t st);
 // beta = L^T alpha from the factor tiles (so that beta = L^{-1} y when alpha = K^{-1} y).
 cudaError_t launch_beta(const double* Lt, int T, int Mt, const double* alpha, double* beta, cudaStream_t st);
 // Lbar of the NLML w.r.t. L: -alpha beta^T on the lower triangle plus diag(1/L_ii), i, j < n.

@@ -184,3 +184,21 @@ def test_schedule_rejects_bad_arguments(lib):
     assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(5, 4, 0, 64, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1
+
+
+def test_autotune_cache_key_and_class_table():
+    """Host logic of the autotuner's JSON cache: batches of the same coarse shape share a key, other
+    shapes, precisions or GPUs do not; GPs take their size class's tile edge."""
+    from paper_2602_19683_gb300 import api
+    shape = [(n, 256, d) for n, d in zip((130, 900, 4000, 2100, 700, 3000), (4, 8, 16, 4, 8, 16))]
+    k = api.autotune_cache_key("GB300", "fp64", shape, True)
+    near = [(n + 7, m, d) for n, m, d in shape]  # same power-of-two buckets
+    assert api.autotune_cache_key("GB300", "fp64", near, True) == k
+    assert api.autotune_cache_key("GB300", "fp32", shape, True) != k
+    assert api.autotune_cache_key("B200", "fp64", shape, True) != k
+    assert api.autotune_cache_key("GB300", "fp64", shape, False) != k
+    assert api.autotune_cache_key("GB300", "fp64", shape + [(5000, 256, 8)] * 3, True) != k
+    assert api.autotune_cache_key("GB300", "fp64", shape, True, tiles=(64, 32)) == \
+        api.autotune_cache_key("GB300", "fp64", shape, True, tiles=(32, 64, 0))
+    table = [{"n_max": 700, "tile": 32}, {"n_max": 2100, "tile": 64}, {"n_max": 4000, "tile": 128}]
+    assert api.tiles_from_classes(table, [1, 700, 701, 2100, 4000, 9999]) == [32, 32, 64, 64, 128, 128]

@@ -110,6 +110,32 @@ def test_autotuner_choices_and_tuned_batch(api, precision):
     batch.free()
 
 
+def test_autotuner_json_cache(api, tmp_path):
+    """batch_autotune with a cache file: the first call searches and stores its choice; a second
+    context with the same batch shape gets the same tiles and schedule from the file without timing
+    anything, and its batch reproduces the tuned batch's results bit for bit."""
+    gps = make_gps(8, 24, seed0=3500)
+    dev = [(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(Xs).cuda(), h)
+           for X, y, Xs, h in gps]
+    path = str(tmp_path / "autotune.json")
+    ctx1 = api.Context(0)
+    tuned1, rep1 = api.batch_autotune(ctx1, dev, tiles=(32, 64), classes=2, sample=3, reps=1, cache_path=path)
+    ctx2 = api.Context(0)
+    tuned2, rep2 = api.batch_autotune(ctx2, dev, tiles=(32, 64), classes=2, sample=3, reps=1, cache_path=path)
+    assert not rep1["cached"] and rep2["cached"]
+    assert [t[4] for t in tuned1] == [t[4] for t in tuned2]
+    assert (rep2["order"], rep2["ctas_per_sm"]) == (rep1["order"], rep1["ctas_per_sm"])
+    outs = []
+    for ctx, tuned in ((ctx1, tuned1), (ctx2, tuned2)):
+        b = api.Batch(ctx, tuned, want_cov=True)
+        b.run()
+        api.gp_sync(ctx)
+        outs.append(([m.cpu().numpy() for m in b.means], [c.cpu().numpy() for c in b.covs]))
+        b.free()
+    for g in range(len(gps)):
+        assert np.array_equal(outs[0][0][g], outs[1][0][g]) and np.array_equal(outs[0][1][g], outs[1][1][g])
+
+
 @pytest.mark.parametrize("order,ctas", [(1, 1), (0, 1), (1, 2)])
 def test_batch_schedule_options(api, order, ctas):
     """Both dispatch orders and both residencies give the same FP64 results (bit-identical: updates

@@ -81,3 +81,16 @@ def test_autograd_function_and_adam_trajectory(api):
     for (th, loss_, _), (th_r, loss_r, _) in zip(hist, ref):
         assert np.allclose(th, th_r, rtol=1e-9, atol=0)
         assert loss_ == pytest.approx(loss_r, rel=1e-11)
+
+
+def test_adam_checkpoint_resume_on_the_library_gradient(api, tmp_path):
+    """fit_adam with a JSONL checkpoint: a run stopped after 3 of 6 steps and resumed from its log
+    repeats the uninterrupted run bit for bit (the FP64 gradient is run-to-run bit-identical)."""
+    X, y, _, _ = nfir.make_dataset(256, 1, 8, 9)
+    ctx = api.Context(0, tile=64)
+    Xd, yd = dev(X, y)
+    full = api.fit_adam(ctx, Xd, yd, (0.5, 2.0, 0.5), steps=6, log_path=str(tmp_path / "full.jsonl"))
+    log = str(tmp_path / "run.jsonl")
+    api.fit_adam(ctx, Xd, yd, (0.5, 2.0, 0.5), steps=3, log_path=log)
+    resumed = api.fit_adam(ctx, Xd, yd, (0.5, 2.0, 0.5), steps=6, log_path=log, resume=True)
+    assert resumed == full

@@ -5,6 +5,8 @@ the predictive mean (Eq. 2) agrees to <= 1e-10 and the covariance (Eq. 3) to <= 
 max-abs error relative to the oracle's max-abs value. Assembly (Eq. 1) agrees to 1e-14 relative:
 both sides evaluate the same expression, the only freedom being fused multiply-adds in |x_i-x_j|^2.
 """
+import warnings
+
 import numpy as np
 import pytest
 import torch
@@ -142,6 +144,93 @@ def test_not_positive_definite_reports_column(api):
     f2 = api.gp_assemble(ctx, Xd, api.Hyper(1.0, 1.0, 0.1))
     api.gp_cholesky(ctx, f2)
     api.gp_sync(ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_nonfinite_inputs_reported_and_context_recovers(api, precision):
+    """NaN/Inf in X, y or Xs: GP_ERR_NONFINITE with the 1-based flat index of the first bad entry (for
+    the mean: y's n entries, then Xs's m*D), the context's later persistent launches skip their tasks
+    until gp_sync collects the error, and the same context then reproduces the oracle."""
+    n, m, D = 600, 70, 4
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 21)
+    ref = oracle.gp_predict(X, y, Xs, H0)
+    ctx = api.Context(0, tile=128, precision=precision)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+
+    def expect_nonfinite(info, fn):
+        with pytest.raises(api.GPError) as e:
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore", RuntimeWarning)  # mixed mode: refinement cut short
+                fn()
+            api.gp_sync(ctx)
+        assert e.value.status == 3 and e.value.info == info
+
+    Xb = Xd.clone()
+    Xb[300, 1] = float("inf")
+    Xb[17, 2] = float("nan")
+    f = None
+
+    def factor_bad():
+        nonlocal f
+        f = api.gp_assemble(ctx, Xb, api.Hyper(*H0))
+        api.gp_cholesky(ctx, f)
+
+    expect_nonfinite(17 * D + 2 + 1, factor_bad)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0), f)
+    api.gp_cholesky(ctx, f)
+    yb = yd.clone()
+    yb[5] = float("-inf")
+    expect_nonfinite(5 + 1, lambda: api.gp_predict_mean(ctx, f, yb, Xsd))
+    Xsb = Xsd.clone()
+    Xsb[3, 0] = float("nan")
+    expect_nonfinite(n + 3 * D + 1, lambda: api.gp_predict_mean(ctx, f, yd, Xsb))
+    expect_nonfinite(3 * D + 1, lambda: api.gp_predict_full_cov(ctx, f, Xsb))
+    expect_nonfinite(3 * D + 1, lambda: api.gp_predict_var(ctx, f, Xsb))
+    mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+    cov = api.gp_predict_full_cov(ctx, f, Xsd)
+    api.gp_sync(ctx)
+    tol_mean, tol_cov = (1e-10, 1e-9) if precision == "fp64" else (1e-10, 1e-4)
+    assert rel(mean.cpu().numpy(), ref["mean"]) <= tol_mean
+    assert rel(cov.cpu().numpy(), ref["cov"]) <= tol_cov
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_allocation_failures_leave_objects_usable(api, precision):
+    """Host-side fault injection: the k-th device allocation of the pipeline fails, for every k in
+    turn. The entry point that needed it returns GP_ERR_OOM, nothing faults, and with the hook off the
+    same context, reusing the factor object when there is one, reproduces the oracle."""
+    n, m, D = 500, 60, 4
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 22)
+    ref = oracle.gp_predict(X, y, Xs, H0)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    tol_cov = 1e-9 if precision == "fp64" else 1e-4
+    failures = 0
+    for k in range(1, 60):
+        ctx = api.Context(0, tile=128, precision=precision)  # its own allocations come before the hook
+        f, failed = None, None
+        api.debug_fail_alloc(k)
+        try:
+            f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+            api.gp_cholesky(ctx, f)
+            api.gp_predict_mean(ctx, f, yd, Xsd)
+            api.gp_predict_full_cov(ctx, f, Xsd)
+            api.gp_sync(ctx)
+        except api.GPError as e:
+            failed = e
+        finally:
+            api.debug_fail_alloc(0)
+        if failed is None:
+            break  # k is past the pipeline's last allocation
+        assert failed.status == 4, str(failed)
+        failures += 1
+        f = api.gp_assemble(ctx, Xd, api.Hyper(*H0), f)
+        api.gp_cholesky(ctx, f)
+        mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+        cov = api.gp_predict_full_cov(ctx, f, Xsd)
+        api.gp_sync(ctx)
+        assert rel(mean.cpu().numpy(), ref["mean"]) <= 1e-10
+        assert rel(cov.cpu().numpy(), ref["cov"]) <= tol_cov
+    assert 8 <= failures < 59
 
 
 def test_withheld_task_times_out_and_context_survives(api):

@@ -29,7 +29,7 @@ def _rank_main(rank, ws, port, out):
 
 def test_two_gloo_ranks_max_and_whole_job_value():
     ws, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of this multi-threaded process
         out = mgr.dict()
         mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
