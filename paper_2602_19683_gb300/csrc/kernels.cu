@@ -729,7 +729,6 @@ __global__ void __launch_bounds__(kThreads) reduce_residual_kernel(const double*
   }
 }
 
-// alpha[i] += d[i] for i < n.
 // Input check: any NaN or infinity among a[0..cnt) raises GP_ERR_NONFINITE with info = base + (index of
 // the first such entry) + 1 (1-based; the smallest index wins). The exponent field is tested with
 // integer operations, one warp ballot per 32 entries, one lane of a warp with a hit raises.
@@ -744,6 +743,7 @@ __global__ void scan_nonfinite_kernel(const double* __restrict__ a, long long cn
   }
 }
 
+// alpha[i] += d[i] for i < n.
 __global__ void axpy_kernel(double* __restrict__ alpha, const double* __restrict__ d, long long n) {
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
     alpha[i] += d[i];
