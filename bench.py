@@ -49,6 +49,39 @@ def tf32_peak_tflops():
     return bf16 * 1.1 / 2.25, f"{src} BF16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
 
 
+# DRAM bytes (read + written) of one mixed-precision Cholesky launch at n = 32768, tile 128, from an
+# ncu capture of the whole launch (dram__bytes_read.sum + dram__bytes_write.sum, one pass).
+MIXED_CHOL_TRAFFIC_N32768_T128 = 630.63e9 + 74.45e9
+
+
+def hbm_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def mixed_cholesky_roofline(n: int, tile: int, chol_s: float):
+    """Roofline object of the mixed-precision Cholesky launch: the tensor pipe (three TF32 split
+    products per update against the TF32 peak) plus its measured DRAM traffic where a capture exists
+    for this size, with the HBM rate that traffic implies."""
+    tf32_peak, tf32_src = tf32_peak_tflops()
+    executed = 3 * (n ** 3 / 3) / chol_s / 1e12
+    traffic = MIXED_CHOL_TRAFFIC_N32768_T128 if (n, tile) == (32768, 128) else None
+    r = {"kernel": "dag_kernel mixed (tiled Cholesky, 3xTF32 on tcgen05)", "bound": "tensor",
+         "achieved": executed, "peak": tf32_peak, "unit": "TFLOP/s", "frac": executed / tf32_peak,
+         "peak_source": tf32_src, "algorithmic_tflops": (n ** 3 / 3) / chol_s / 1e12, "traffic": traffic}
+    if traffic is not None:
+        hbm, src = hbm_peak_gbs()
+        r["traffic_gbs"] = traffic / chol_s / 1e9
+        r["traffic_frac_of_hbm"] = traffic / chol_s / 1e9 / hbm
+        r["traffic_note"] = (f"bytes per launch, ncu capture of the n=32768 launch; rate vs the {src} HBM copy "
+                             f"peak {hbm:.0f} GB/s: the updates stream their packed operands from HBM")
+    return r
+
+
 def fp64_cholesky_traffic(n: int, tile: int):
     if tile != 256:
         return None
@@ -384,14 +417,9 @@ def run_ours(args):
 
             def relerr(a, b):
                 return float((a - b).abs().max() / b.abs().max())
-            tf32_peak, tf32_src = tf32_peak_tflops()
-            executed = 3 * (n ** 3 / 3) / phase32[1] / 1e12  # three TF32 split products per update
             mixed = {"precision": "fp32 trailing updates, FP64 POTRF/first-column TRSM/refinement",
                      "tile": ctx_tile(n, args.tile, True),
-                     "roofline": {"kernel": "dag_kernel mixed (tiled Cholesky, 3xTF32 on tcgen05)", "bound": "tensor",
-                                  "achieved": executed, "peak": tf32_peak, "unit": "TFLOP/s",
-                                  "frac": executed / tf32_peak, "peak_source": tf32_src,
-                                  "algorithmic_tflops": (n ** 3 / 3) / phase32[1] / 1e12, "traffic": None},
+                     "roofline": mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), phase32[1]),
                      "s_per_solve": ms32 / 1e3, "tflops": algorithmic_flops(n, m) / (ms32 / 1e3) / 1e12,
                      "speedup_vs_fp64": ms / ms32, "ir_iterations": iters[0],
                      "phases_s": {"assemble": phase32[0], "cholesky": phase32[1], "mean_refined": phase32[2],
@@ -418,12 +446,13 @@ def run_ours(args):
                        "tile": ctx_tile(n, args.tile, args.precision == "fp32"), "precision": args.precision,
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (K is 4.4 GB)",
                        "s_per_solve": ms / 1e3, "cholesky_s": chol_ms / 1e3},
-            "roofline": {"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "peak_source": "FP64 FFMA pipe: 2 FMA/clk/SM x 152 SMs x max SM clock (derived)",
-                         "traffic": (fp64_cholesky_traffic(n, ctx_tile(n, args.tile)) if args.precision == "fp64"
-                                     else None),
-                         "traffic_note": "bytes per launch, ncu capture at n=8192 scaled by the tile-update count"},
+            "roofline": ({"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
+                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                          "peak_source": "FP64 FFMA pipe: 2 FMA/clk/SM x 152 SMs x max SM clock (derived)",
+                          "traffic": fp64_cholesky_traffic(n, ctx_tile(n, args.tile)),
+                          "traffic_note": "bytes per launch, ncu capture at n=8192 scaled by the tile-update count"}
+                         if args.precision == "fp64" else
+                         mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), chol_ms / 1e3)),
             "gpu_launches": launches, "clocks": clocks}
     if mixed:
         line["mixed"] = mixed
