@@ -264,8 +264,10 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * J, which the vector solves of gp_predict_mean apply as a matrix-vector product, 15 VGEMM(I,c,J0|J1<<16)
  * and 16 WSYRK(a,b,J0|J1<<16): products of columns J0..J1-1 applied in one pass, mixed mode with
  * 128-multiple tiles; 17 FSOLVE(J,ch) and 18 BSOLVE(J,ch): 32-row chunk ch of the diagonal-block solve of
- * the mean graph, a product with the stored inverse of the diagonal tile) into out (host, room
- * for cap tasks). Returns the task count, or -1 on bad arguments. Needs no GPU. */
+ * the mean graph, a product with the stored inverse of the diagonal tile; 19 UPDATE2(I,K,J0|J1<<16):
+ * the grouped updates of tiles (I,K) and (I+1,K) in one pass over the shared L_KJ, mixed mode with
+ * tile edge 128) into out (host, room for cap tasks). Returns the task count, or -1 on bad
+ * arguments. Needs no GPU. */
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap);
 

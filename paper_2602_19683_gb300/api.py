@@ -122,7 +122,7 @@ class Factor:
 
 TASK_NAMES = ["POTRF", "TRSM", "UPDATE", "VTRSM", "VGEMM", "WSYRK", "FSOLVE", "FGEMV", "BSOLVE", "BGEMV",
               "RUPD", "RTRSM", "RDIAG", "RPOTRF", "TRTRI", "VGEMM_G", "WSYRK_G",
-              "FSOLVE_C", "BSOLVE_C"]
+              "FSOLVE_C", "BSOLVE_C", "UPDATE2"]
 
 
 def gp_trace(ctx: Context):

@@ -139,6 +139,7 @@ gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
   // Mixed tensor-core updates: group 8 columns per task (one FP64 C read-modify-write for eight).
   cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 8 : 1;
   cm.tensor_cores = cm.update_group > 1;
+  cm.pair_rows = cm.tensor_cores && T == 128;
   // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
   cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
   cm.sec_per_flop32 = 1.0 / 3.0e11;
@@ -369,6 +370,7 @@ int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int3
   cm.mixed = mixed != 0;
   cm.update_group = (mixed && T % 128 == 0) ? 8 : 1;
   cm.tensor_cores = cm.update_group > 1;
+  cm.pair_rows = cm.tensor_cores && T == 128;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);

@@ -141,6 +141,14 @@ __device__ bool wait_deps(const DagArgs& a, int4 tk, int ti) {
         if (!wait_ge(a.cK + tri(p, J), J + 1, st, to, ti) || !wait_ge(a.cK + tri(q, J), J + 1, st, to, ti)) return false;
       return wait_ge(a.cK + tri(p, q), J0, st, to, ti);
     }
+    case TASK_UPD2: {  // rows p and p + 1 of column q, J in [J0, J1)
+      const int J0 = r & 0xFFFF, J1 = r >> 16;
+      for (int J = J0; J < J1; ++J)
+        if (!wait_ge(a.cK + tri(p, J), J + 1, st, to, ti) || !wait_ge(a.cK + tri(p + 1, J), J + 1, st, to, ti) ||
+            !wait_ge(a.cK + tri(q, J), J + 1, st, to, ti))
+          return false;
+      return wait_ge(a.cK + tri(p, q), J0, st, to, ti) && wait_ge(a.cK + tri(p + 1, q), J0, st, to, ti);
+    }
     // The solve tasks also wait for the factor tiles they read to be final (immediately true when the
     // factorisation ran in an earlier launch; needed when one launch runs a GP's whole pipeline).
     case TASK_VTRSM:  // (J=p, c=q)
@@ -368,41 +376,57 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         }
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
-      case TASK_UPD: {  // K_IK -= sum_{J0 <= J < J1} L_IJ L_KJ^T (SYRK when I == K), J in increasing order
+      case TASK_UPD:    // K_IK -= sum_{J0 <= J < J1} L_IJ L_KJ^T (SYRK when I == K), J in increasing order
+      case TASK_UPD2: {  // the same for tiles (I, K) and (I + 1, K) together
         const int J0 = r & 0xFFFF, J1 = (r >> 16) ? (r >> 16) : J0 + 1;
-        double* C = a.Kt + tri(p, q) * TT;
-        if (kUmma && use_umma && a.Pk && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
-          PkPairs pr;
+        const int rows = tk.x == TASK_UPD2 ? 2 : 1;
+        if (rows == 2 && kUmma && use_umma && a.Pk && T == kUmmaM && J1 - J0 <= kUmmaMaxPairs) {
+          PkPairs2 pr;
           pr.n = J1 - J0;
           for (int J = J0; J < J1; ++J) {
-            pr.A[J - J0] = a.Pk + tri(p, J) * TT * 8;
+            pr.A0[J - J0] = a.Pk + tri(p, J) * TT * 8;
+            pr.A1[J - J0] = a.Pk + tri(p + 1, J) * TT * 8;
             pr.B[J - J0] = a.Pk + tri(q, J) * TT * 8;
           }
-          if (!umma_pk_gemm_sub(um, C, T, pr, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
-            aborted = true;
-            break;
-          }
-        } else if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
-          UmmaPairs pr;
-          pr.n = J1 - J0;
-          for (int J = J0; J < J1; ++J) {
-            pr.A[J - J0] = a.Kt + tri(p, J) * TT;
-            pr.B[J - J0] = a.Kt + tri(q, J) * TT;
-          }
-          if (!umma_gemm_sub(um, C, T, pr, T, T, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
+          if (!umma_pk_block2_sub(um, a.Kt + tri(p, q) * TT, a.Kt + tri(p + 1, q) * TT, T, pr, T, p == q, a.st,
+                                  a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
         } else {
-          for (int J = J0; J < J1; ++J) {
-            if (kMixed)
-              cta_gemm_sub_f32<0, 0>(C, T, a.Kt + tri(p, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, p == q, u.f.g);
-            else
-              cta_gemm_sub<A_MK, B_NK>(C, T, a.Kt + tri(p, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, p == q, 0,
-                                       s.g);
+          for (int I = p; I < p + rows && !aborted; ++I) {  // one tile at a time
+            double* C = a.Kt + tri(I, q) * TT;
+            if (kUmma && use_umma && a.Pk && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
+              PkPairs pr;
+              pr.n = J1 - J0;
+              for (int J = J0; J < J1; ++J) {
+                pr.A[J - J0] = a.Pk + tri(I, J) * TT * 8;
+                pr.B[J - J0] = a.Pk + tri(q, J) * TT * 8;
+              }
+              if (!umma_pk_gemm_sub(um, C, T, pr, T, T, T, I == q, a.st, a.timeout_ns, ti)) aborted = true;
+            } else if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
+              UmmaPairs pr;
+              pr.n = J1 - J0;
+              for (int J = J0; J < J1; ++J) {
+                pr.A[J - J0] = a.Kt + tri(I, J) * TT;
+                pr.B[J - J0] = a.Kt + tri(q, J) * TT;
+              }
+              if (!umma_gemm_sub(um, C, T, pr, T, T, T, T, T, I == q, a.st, a.timeout_ns, ti)) aborted = true;
+            } else {
+              for (int J = J0; J < J1; ++J) {
+                if (kMixed)
+                  cta_gemm_sub_f32<0, 0>(C, T, a.Kt + tri(I, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, I == q,
+                                         u.f.g);
+                else
+                  cta_gemm_sub<A_MK, B_NK>(C, T, a.Kt + tri(I, J) * TT, T, a.Kt + tri(q, J) * TT, T, T, T, T, I == q,
+                                           0, s.g);
+              }
+            }
           }
+          if (aborted) break;
         }
         cta_publish(a.cK + tri(p, q), J1);
+        if (rows == 2) cta_publish(a.cK + tri(p + 1, q), J1);
         break;
       }
       case TASK_VTRSM: {

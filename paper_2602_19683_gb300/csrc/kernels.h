@@ -36,7 +36,10 @@ enum TaskKind {
   // Vector solves with the stored inverses, each diagonal block split into 32-row chunks that run in
   // parallel (a second vector, xvec, holds the forward result so no chunk overwrites what another reads):
   TASK_FSOLVE_C = 17,  // (J, ch)  xvec_J[ch] = Linv_J[ch, :] bvec_J
-  TASK_BSOLVE_C = 18   // (J, ch)  bvec_J[ch] = (Linv_J^T)[ch, :] xvec_J
+  TASK_BSOLVE_C = 18,  // (J, ch)  bvec_J[ch] = (Linv_J^T)[ch, :] xvec_J
+  // Two vertically adjacent tiles of one column updated together (mixed mode on the tensor cores,
+  // tile edge 128): both products read the same L_KJ, loaded once per k chunk.
+  TASK_UPD2 = 19  // (I, K, J0 | J1 << 16)  K_IK and K_{I+1,K} -= sum_{J0 <= J < J1} L_{I(+1),J} L_KJ^T
 };
 
 // One GP of a batch: its inputs, outputs, hyperparameters and workspace (all device pointers).

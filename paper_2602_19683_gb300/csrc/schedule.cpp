@@ -126,24 +126,37 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
       last[tri(I, J)] = b.add(TASK_TRSM, I, J, 0, J == 0 ? c_trsm0 : c_trsm, {po, last[tri(I, J)]});
       trsm_of[tri(I, J)] = last[tri(I, J)];
     }
-    for (int I = J + 1; I < Mt; ++I)
-      for (int K = J + 1; K <= I; ++K) {
+    for (int K = J + 1; K < Mt; ++K) {
+      const int lim = K - kTail;  // columns >= lim are applied one by one
+      const bool grouped = g > 1 && J < lim;
+      // group boundaries depend on the column K only, so every row of column K closes its group here
+      if (grouped && (J + 1) % g != 0 && J + 1 != lim) continue;  // the group stays open
+      for (int I = K; I < Mt; ++I) {
         const size_t t = tri(I, K);
-        const int lim = K - kTail;  // columns >= lim are applied one by one
-        int J0 = J;
-        if (g > 1 && J < lim) {
-          if ((J + 1) % g != 0 && J + 1 != lim) continue;  // the group stays open
-          J0 = gstart[t];
-        }
+        const int J0 = grouped ? gstart[t] : J;
+        // rows K, K+1 | K+2, K+3 | ... of a closing group share one pass over L_KJ
+        const bool pair = grouped && cm.pair_rows && (I - K) % 2 == 0 && I + 1 < Mt;
         std::vector<int> deps{last[t]};
+        if (pair) deps.push_back(last[tri(I + 1, K)]);
         for (int Jj = J0; Jj <= J; ++Jj) {
           deps.push_back(trsm_of[tri(I, Jj)]);
+          if (pair) deps.push_back(trsm_of[tri(I + 1, Jj)]);
           deps.push_back(trsm_of[tri(K, Jj)]);
         }
         const int r = J0 | ((J + 1) << 16);
-        last[t] = b.add_v(TASK_UPD, I, K, r, (J + 1 - J0) * (I == K ? c_syrk : c_gemm), deps);
-        gstart[t] = J + 1;
+        const double cost = (J + 1 - J0) * (I == K ? c_syrk : c_gemm);
+        if (pair) {
+          // measured: the shared operand saves about a fifth of the two tiles' time
+          const int id = b.add_v(TASK_UPD2, I, K, r, 0.8 * (cost + (J + 1 - J0) * c_gemm), deps);
+          last[t] = last[tri(I + 1, K)] = id;
+          gstart[t] = gstart[tri(I + 1, K)] = J + 1;
+          ++I;
+        } else {
+          last[t] = b.add_v(TASK_UPD, I, K, r, cost, deps);
+          gstart[t] = J + 1;
+        }
       }
+    }
   }
   // Longest-remaining-path order. (A column-group / super-tile order for the grouped updates keeps
   // their operands in L2 — 98 % modelled hits against 14 % — but delays the updates the diagonal

@@ -19,6 +19,9 @@ struct CostModel {
   // GB300 at T = 128 (per-task trace at n = 32768) replace the flop-rate model, scaled by (T/128)^3
   // for the FP64 work and (T/128)^2 for the memory-bound products.
   bool tensor_cores = false;
+  // Grouped updates of tiles (I, K) and (I + 1, K) as one task (TASK_UPD2; tile edge 128 on the tensor
+  // cores): the shared L_KJ is read once for both, a quarter fewer operand bytes per product.
+  bool pair_rows = false;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
 };

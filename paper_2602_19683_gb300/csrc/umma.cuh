@@ -28,7 +28,9 @@ constexpr int kPkStages = 3;                           // stages of the packed-o
 constexpr int kMixedTileSmemBytes = 128 * 129 * 8;
 constexpr int kUmmaSmemBytes =
     (kPkStages * kUmmaStageBytes > kMixedTileSmemBytes ? kPkStages * kUmmaStageBytes : kMixedTileSmemBytes) + 4096;
-constexpr int kUmmaTmemCols = 256;  // two 128 x 128 FP32 accumulators (see umma_packed.cuh)
+// four 128 x 128 FP32 accumulators: two per output tile, for the paired-row updates (umma_packed.cuh);
+// the whole tensor memory of the SM, which holds one CTA of the mixed kernel (shared memory bound)
+constexpr int kUmmaTmemCols = 512;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -113,7 +115,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 struct UmmaState {
   uint8_t* smem;       // 1024-aligned dynamic shared memory: 2 register-staged or kPkStages packed stages
   uint64_t* bar;       // 2 mbarriers (smem)
-  uint32_t tmem;       // TMEM base address (kUmmaTmemCols columns: two 128-column accumulators)
+  uint32_t tmem;       // TMEM base address (kUmmaTmemCols columns: four 128-column accumulators)
   uint32_t phase[2];   // next parity to wait for, per stage
   uint32_t pending[2]; // stage has an uncompleted commit
   // packed-operand pipeline (umma_packed.cuh): per stage, a "full" barrier completed by the bulk
@@ -244,9 +246,11 @@ __device__ bool umma_block_sub(UmmaState& u, double* C, int ldc, const UmmaPairs
 // Epilogue of a 128 x 128 block whose MMAs are all complete: TMEM -> registers (warp w: lanes
 // 32(w%4).., a 64-column half) -> smem (row-major, the operand stages are free now) -> coalesced
 // FP64 read-modify-write of C (a warp per row, 4 columns per lane): C -= acc, only n <= m when lower.
+// The accumulator starts at TMEM column acc_col (a second one, nacc = 2, at acc_col + 128).
 // Ends with __syncthreads().
 template <bool kStore>
-__device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int nacc = 1) {
+__device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int nacc = 1,
+                              uint32_t acc_col = 0) {
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* acc_s = reinterpret_cast<float*>(u.smem);  // 128 x (128 + 4) floats
@@ -270,10 +274,10 @@ __device__ void umma_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, 
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       float v[32];
-      tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(colh + 32 * half), v);
-      if (nacc > 1) {  // second accumulator (columns 128..255): one FP32 round-to-nearest add
+      tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + acc_col + (uint32_t)(colh + 32 * half), v);
+      if (nacc > 1) {  // second accumulator (the next 128 columns): one FP32 round-to-nearest add
         float v2[32];
-        tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(kUmmaN + colh + 32 * half), v2);
+        tmem_ld32(u.tmem + ((uint32_t)((w & 3) * 32) << 16) + acc_col + (uint32_t)(kUmmaN + colh + 32 * half), v2);
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] += v2[j];
       }

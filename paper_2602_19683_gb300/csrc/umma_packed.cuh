@@ -209,6 +209,122 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
   return true;
 }
 
+// Two output tiles that share their right operands: C0 -= sum_p A0_p B_p^T and C1 -= sum_p A1_p B_p^T.
+struct PkPairs2 {
+  const uint8_t* A0[kUmmaMaxPairs];
+  const uint8_t* A1[kUmmaMaxPairs];
+  const uint8_t* B[kUmmaMaxPairs];
+  int n;
+};
+
+// Both 128 x 128 FP64 tiles C0, C1 (ldc) of a PkPairs2 product from packed 128-row operands (Kd a
+// multiple of 32), in one pass over the shared B_p: a stage holds the k chunk of A0_p, A1_p and B_p
+// (three bulk copies, 96 KB; two stages in the stage memory), and one thread issues the MMAs of both
+// outputs on it. Accumulators: output o, column pairs 0..3 / 4..7 -> TMEM columns 256 o + 128 h, so
+// no FP32 accumulation chain runs over more than four column pairs. lower0: C0 is a diagonal tile
+// (only its lower triangle is updated). Same bounded waits and drain as umma_pk_block_sub; false on a
+// time-out.
+__device__ bool umma_pk_block2_sub(UmmaState& u, double* C0, double* C1, int ldc, const PkPairs2& pr, int Kd,
+                                   bool lower0, DevStatus* st, long long timeout_ns, long long where) {
+  constexpr int kStages2 = 2, kStage2Bytes = 3 * kPkChunkBytes;
+  static_assert(kStages2 * kStage2Bytes <= kPkStages * kUmmaStageBytes, "two three-operand stages fit the stages");
+  static_assert(kStages2 <= kPkStages, "the stages use the first kStages2 barrier pairs");
+  static_assert(kUmmaTmemCols >= 4 * kUmmaN, "four accumulators");
+  static_assert(kStage2Bytes % 1024 == 0 && kPkChunkBytes % 1024 == 0, "swizzled operands stay 1024-byte aligned");
+  const int nkp = Kd / kUmmaKChunk, nk = nkp * pr.n;
+  bool ok = true;
+  fence_async_smem();  // earlier generic use of the stage memory (other tile routines) before the copies
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();  // tiles acquired through the dependency counters feed bulk copies
+    auto load = [&](int i) {
+      const int s = i % kStages2, p = i / nkp, kc = i % nkp;
+      uint8_t* base = u.smem + s * kStage2Bytes;
+      mbar_expect_tx(&u.pfull[s], 3 * kPkChunkBytes);
+      tma_bulk_g2s(base, pr.A0[p] + pk_chunk_off(0, kc, Kd), kPkChunkBytes, &u.pfull[s]);
+      tma_bulk_g2s(base + kPkChunkBytes, pr.A1[p] + pk_chunk_off(0, kc, Kd), kPkChunkBytes, &u.pfull[s]);
+      tma_bulk_g2s(base + 2 * kPkChunkBytes, pr.B[p] + pk_chunk_off(0, kc, Kd), kPkChunkBytes, &u.pfull[s]);
+      u.fpend[s] = 1;
+    };
+    for (int i = 0; i < nk && i < kStages2; ++i) load(i);
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % kStages2;
+      if (!mbar_wait(&u.pfull[s], u.fph[s], st, timeout_ns, where)) {
+        ok = false;
+        break;
+      }
+      u.fph[s] ^= 1u;
+      u.fpend[s] = 0;
+      umma_fence_after();
+      const uint32_t a0_hi = smem_u32(u.smem + s * kStage2Bytes), a0_lo = a0_hi + kUmmaTileBytes;
+      const uint32_t a1_hi = a0_hi + kPkChunkBytes, a1_lo = a1_hi + kUmmaTileBytes;
+      const uint32_t b_hi = a0_hi + 2 * kPkChunkBytes, b_lo = b_hi + kUmmaTileBytes;
+      const int pair = i / nkp, h = pair >= kPairsPerAcc ? 1 : 0;
+      const uint32_t d0 = u.tmem + (uint32_t)(h * kUmmaN), d1 = d0 + (uint32_t)(2 * kUmmaN);
+      const bool first = (i % (kPairsPerAcc * nkp)) == 0;  // first chunk of these accumulators
+#pragma unroll
+      for (int ks = 0; ks < kUmmaKChunk / 8; ++ks) {
+        const uint32_t o = ks * 32, acc = (!first || ks > 0) ? 1u : 0u;
+        const uint64_t bh = umma_desc_sw128(b_hi + o), bl = umma_desc_sw128(b_lo + o);
+        umma_tf32(d0, umma_desc_sw128(a0_hi + o), bh, acc);
+        umma_tf32(d0, umma_desc_sw128(a0_hi + o), bl, 1u);
+        umma_tf32(d0, umma_desc_sw128(a0_lo + o), bh, 1u);
+        umma_tf32(d1, umma_desc_sw128(a1_hi + o), bh, acc);
+        umma_tf32(d1, umma_desc_sw128(a1_hi + o), bl, 1u);
+        umma_tf32(d1, umma_desc_sw128(a1_lo + o), bh, 1u);
+      }
+      umma_commit(&u.pempty[s]);
+      u.epend[s] = 1;
+      if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
+        const int sp = (i - 1) % kStages2, j = i - 1 + kStages2;
+        if (j < nk) {
+          if (!mbar_wait(&u.pempty[sp], u.eph[sp], st, timeout_ns, where)) {
+            ok = false;
+            break;
+          }
+          u.eph[sp] ^= 1u;
+          u.epend[sp] = 0;
+          load(j);
+        }
+      }
+    }
+    // every MMA must be complete before TMEM is read (and before the stages are reused)
+    for (int i = 0; i < kStages2; ++i) {
+      const int s = (nk + i) % kStages2;  // oldest outstanding commit first
+      if (u.epend[s]) {
+        if (ok) {
+          ok = mbar_wait(&u.pempty[s], u.eph[s], st, timeout_ns, where);
+        } else {
+          mbar_drain(&u.pempty[s], u.eph[s], timeout_ns);
+        }
+        u.eph[s] ^= 1u;
+        u.epend[s] = 0;
+      }
+    }
+    if (!ok) {
+      for (int s = 0; s < kStages2; ++s)
+        if (u.fpend[s]) {
+          mbar_drain(&u.pfull[s], u.fph[s], timeout_ns);
+          u.fph[s] ^= 1u;
+          u.fpend[s] = 0;
+        }
+      for (int s = 0; s < kStages2; ++s)
+        if (u.epend[s]) {
+          mbar_drain(&u.pempty[s], u.eph[s], timeout_ns);
+          u.eph[s] ^= 1u;
+          u.epend[s] = 0;
+        }
+    }
+  }
+  if (__syncthreads_or(!ok)) return false;
+  const int nacc = pr.n > kPairsPerAcc ? 2 : 1;
+  umma_epilogue<false>(u, C0, ldc, 0, 0, lower0, nacc, 0);
+  umma_epilogue<false>(u, C1, ldc, 0, 0, false, nacc, (uint32_t)(2 * kUmmaN));
+  fence_async_smem();  // generic smem traffic of the epilogues before the next bulk copies
+  __syncthreads();
+  return true;
+}
+
 // C[M x N] -= sum_p A_p B_p^T from packed operands (M, N multiples of 128; Kd of 32); lower skips the
 // blocks above the diagonal and masks the diagonal blocks. kStore: C = sum_p A_p B_p^T instead (every
 // entry written; lower must be false). False on a time-out.

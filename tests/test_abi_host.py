@@ -65,6 +65,7 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
         assert len(t) == 2 * Mt + Mt * (Mt - 1) // 2 + sum((Mt - J - 1) * (Mt - J) // 2 for J in range(Mt))
     cnt = {}  # tile -> updates applied (+1 once final)
     inverted = set()
+    paired = 0
     for kind, p, q, r in t:
         if kind == 0:
             assert cnt.get((p, p), 0) == p
@@ -75,17 +76,24 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
         elif kind == 1:
             assert cnt.get((q, q), 0) == q + 1 and cnt.get((p, q), 0) == q and p > q
             cnt[(p, q)] = q + 1
-        elif kind == 2:  # columns [J0, J1) of updates, r = J0 | J1 << 16
+        elif kind in (2, 19):  # columns [J0, J1) of updates, r = J0 | J1 << 16; 19: rows p and p + 1
             J0, J1 = r & 0xFFFF, (r >> 16) or (r & 0xFFFF) + 1
-            assert p >= q >= J1 > J0 >= 0 and J1 - J0 <= 8
-            for J in range(J0, J1):
-                assert cnt.get((p, J), 0) == J + 1 and cnt.get((q, J), 0) == J + 1
-            assert cnt.get((p, q), 0) == J0
-            cnt[(p, q)] = J1
+            rows = (p, p + 1) if kind == 19 else (p,)
+            assert mixed or kind == 2
+            for I in rows:
+                assert I < Mt and I >= q >= J1 > J0 >= 0 and J1 - J0 <= 8
+                for J in range(J0, J1):
+                    assert cnt.get((I, J), 0) == J + 1 and cnt.get((q, J), 0) == J + 1
+                assert cnt.get((I, q), 0) == J0
+            for I in rows:
+                cnt[(I, q)] = J1
+            paired += kind == 19
         else:
             raise AssertionError(kind)
     assert all(cnt[(I, J)] == J + 1 for I in range(Mt) for J in range(I + 1))
     assert inverted == set(range(Mt))
+    if mixed and Mt >= 16:  # tile 128 on the tensor cores: grouped updates of row pairs share L_KJ
+        assert paired > 0
 
 
 @pytest.mark.parametrize("Mt,Mc,workers,mixed", [(1, 1, 2, 0), (4, 3, 5, 0), (7, 2, 304, 0), (1, 1, 2, 1),
