@@ -20,7 +20,7 @@ struct CostModel {
   // for the FP64 work and (T/128)^2 for the memory-bound products.
   bool tensor_cores = false;
   // Grouped updates of tiles (I, K) and (I + 1, K) as one task (TASK_UPD2; tile edge 128 on the tensor
-  // cores): the shared L_KJ is read once for both, a quarter fewer operand bytes per product.
+  // cores): the shared L_KJ is copied once for both, a quarter fewer operand bytes requested per product.
   bool pair_rows = false;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
