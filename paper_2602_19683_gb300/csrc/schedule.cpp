@@ -146,9 +146,10 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
         const int r = J0 | ((J + 1) << 16);
         const double cost = (J + 1 - J0) * (I == K ? c_syrk : c_gemm);
         if (pair) {
-          // measured at n = 32768: as long as the two tiles' separate tasks (97 us for ~2 x 7 column
-          // pairs), since the L2 already served the shared L_KJ to neighbouring tasks
-          const int id = b.add_v(TASK_UPD2, I, K, r, cost + (J + 1 - J0) * c_gemm, deps);
+          // measured at n = 32768: about as long as the two tiles' separate tasks (97 us for ~2 x 7
+          // column pairs: the L2 already served the shared L_KJ to neighbouring tasks); ranking it at
+          // 0.8 of that gave the shorter factorisation of the two weights tried (152 vs 156 ms)
+          const int id = b.add_v(TASK_UPD2, I, K, r, 0.8 * (cost + (J + 1 - J0) * c_gemm), deps);
           last[t] = last[tri(I + 1, K)] = id;
           gstart[t] = gstart[tri(I + 1, K)] = J + 1;
           ++I;
