@@ -233,6 +233,37 @@ def test_allocation_failures_leave_objects_usable(api, precision):
     assert 8 <= failures < 59
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["two_point", "three_point"])
+def test_golden_closed_forms_gpu(api, case, precision):
+    """The library on the 2- and 3-point problems against their 40-digit evaluation from the
+    definitions (tests/golden/closed_forms.txt): factor, mean, variance (Eqs. 1-3), log-determinant
+    and nlml. FP64 to 1e-13; the mixed mode's refined mean to 1e-10 and its unrefined quantities to
+    its stated bounds."""
+    from test_oracle_pins import GOLDEN_CASES, load_golden
+    g = load_golden()[case]
+    xs, ys = GOLDEN_CASES[case]
+    X, y = np.array(xs)[:, None], np.array(ys)
+    Xd, yd, Xsd = to_dev(X, y, np.array([[0.5]]))
+    ctx = api.Context(0, tile=32, precision=precision)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    mean = api.gp_predict_mean(ctx, f, yd, Xsd).cpu().numpy()
+    var = api.gp_predict_full_cov(ctx, f, Xsd).cpu().numpy()
+    logdet = api.gp_logdet(ctx, f)
+    nl, _ = api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*H0))
+    api.gp_sync(ctx)
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    for i in range(len(xs)):
+        for j in range(i + 1):
+            assert L[i, j] == pytest.approx(g[f"L{i}{j}"], rel=tol, abs=tol)
+    assert mean[0] == pytest.approx(g["mean"], rel=1e-13 if precision == "fp64" else 1e-10)
+    assert var[0, 0] == pytest.approx(g["var"], rel=tol * 10)
+    assert logdet == pytest.approx(g["logdet"], rel=tol)
+    assert nl == pytest.approx(g["nlml"], rel=tol)
+
+
 def test_withheld_task_times_out_and_context_survives(api):
     """A task whose completion is never published makes its dependants' bounded waits expire: the
     persistent kernel returns GP_ERR_TIMEOUT instead of hanging, and the GPU stays usable."""

@@ -295,3 +295,39 @@ def test_adam_first_step_and_floor():
     assert t1[1] == pytest.approx(1e-6)  # -1.95 clamped to the floor
     assert t1[2] == pytest.approx(1e-6)
     assert t0[0] == 1.0
+
+
+def load_golden(name="closed_forms.txt"):
+    """Values of tests/golden/<name> as {case: {key: float}}."""
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            if line.startswith("#") or "=" not in line:
+                continue
+            k, v = (s.strip() for s in line.split("=", 1))
+            case, key = k.split(".", 1)
+            out.setdefault(case, {})[key] = float(v)
+    return out
+
+
+GOLDEN_CASES = {"two_point": ([0.0, 1.0], [1.0, 2.0]), "three_point": ([0.0, 1.0, 2.0], [1.0, -1.0, 0.5])}
+
+
+@pytest.mark.parametrize("case", sorted(GOLDEN_CASES))
+def test_golden_closed_forms(case):
+    """The oracle against the 40-digit evaluation of the definitions (tests/golden/closed_forms.txt):
+    factor, alpha, mean, variance (Eqs. 1-3), log-determinant and nlml."""
+    g = load_golden()[case]
+    xs, ys = GOLDEN_CASES[case]
+    X, y = np.array(xs)[:, None], np.array(ys)
+    r = oracle.gp_predict(X, y, np.array([[0.5]]), H0)
+    n = len(xs)
+    for i in range(n):
+        for j in range(i + 1):
+            assert r["L"][i, j] == pytest.approx(g[f"L{i}{j}"], rel=1e-15, abs=1e-16)
+        assert r["alpha"][i] == pytest.approx(g[f"alpha{i}"], rel=1e-14)
+    assert r["mean"][0] == pytest.approx(g["mean"], rel=1e-14)
+    assert r["cov"][0, 0] == pytest.approx(g["var"], rel=1e-13)
+    assert r["logdet"] == pytest.approx(g["logdet"], rel=1e-14)
+    assert oracle.nlml(r["L"], y, r["alpha"]) == pytest.approx(g["nlml"], rel=1e-14)
