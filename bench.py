@@ -130,6 +130,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (GP_FP32) leg")
     p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
+    p.add_argument("--locality-order", action="store_true",
+                   help="mixed precision: start grouped updates that share a packed operand back to back "
+                        "(cfg.locality_order)")
     p.add_argument("--cpu-n", type=int, default=8192, help="oracle sample size for the CPU baseline")
     p.add_argument("--cpu-m", type=int, default=1024)
     p.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference-arm step")
@@ -289,7 +292,8 @@ def run_ours(args):
     Xd, yd, Xsd = (torch.from_numpy(a).to(dev) for a in (X, y, Xs))
     h = api.Hyper(1.0, 1.0, 0.1)
     stream = torch.cuda.Stream(dev)
-    ctx = api.Context(local, stream=stream, tile=args.tile, precision=args.precision, grid=args.grid)
+    ctx = api.Context(local, stream=stream, tile=args.tile, precision=args.precision, grid=args.grid,
+                      locality_order=args.locality_order)
     mean = torch.empty(m, dtype=torch.float64, device=dev)
     cov = torch.empty((m, m), dtype=torch.float64, device=dev)
     fac = [None]
@@ -373,7 +377,8 @@ def run_ours(args):
         if not args.no_mixed and args.precision == "fp64":
             mean64, cov64 = mean.clone(), cov.clone()
             logdet64 = api.gp_logdet(ctx, fac[0])
-            ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32")
+            ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32",
+                                locality_order=args.locality_order)
             fac32 = [None]
             mean32 = torch.empty_like(mean)
             cov32 = torch.empty_like(cov)
@@ -444,6 +449,7 @@ def run_ours(args):
             "data": "synthetic NFIR mass-spring-damper (seeded)",
             "config": {"workload": f"exact GP solve n={n} m={m} D={D}", "n": n, "m": m, "D": D,
                        "tile": ctx_tile(n, args.tile, args.precision == "fp32"), "precision": args.precision,
+                       "locality_order": bool(args.locality_order),
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (K is 4.4 GB)",
                        "s_per_solve": ms / 1e3, "cholesky_s": chol_ms / 1e3},
             "roofline": ({"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
@@ -544,7 +550,8 @@ def run_large(args):
     outs = {}
     with torch.cuda.stream(stream):
         for prec in ("fp32", "fp64"):
-            ctx = api.Context(0, stream=stream, tile=args.tile, precision=prec, timeout_s=900.0)
+            ctx = api.Context(0, stream=stream, tile=args.tile, precision=prec, timeout_s=900.0,
+                              locality_order=args.locality_order)
             mean = torch.empty(m, dtype=torch.float64, device=dev)
             cov = torch.empty((m, m), dtype=torch.float64, device=dev)
             fac = [None]

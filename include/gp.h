@@ -96,7 +96,10 @@ typedef struct {
   int32_t batch_ctas_per_sm; /* persistent-kernel CTAs per SM of batched launches (0 = library choice: two
                              for GP_FP64, one for GP_FP32; capped by occupancy). gp_batch_autotune stores
                              its choice here.                                                          */
-  int32_t reserved[1];
+  int32_t locality_order;  /* GP_FP32 on the tensor cores: 1 = start the grouped trailing updates that share a
+                             packed operand group back to back when their longest-path rank is within
+                             10 % of the best ready task's (they then read the shared operand from L2);
+                             0 = longest-path order only (default)                                    */
 } gp_config;
 
 typedef struct gp_ctx gp_ctx;
@@ -257,7 +260,7 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
  * Cholesky used by gp_nlml_grad, 4 = the V solve of gp_predict_var) for Mt tile rows, Mc covariance
  * tile columns, tile edge T, `workers` CTAs and the cost model of precision `mixed` (0 = FP64,
- * 1 = GP_FP32) as int32 quadruples {kind, p, q, r} (kinds as in the
+ * 1 = GP_FP32; 3 = GP_FP32 with cfg.locality_order = 1) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
  * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J), 14 TRTRI(J): the FP64 inverse of the factored diagonal tile

@@ -55,7 +55,8 @@ class Context:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, tile: int = 0,
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
-                 tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0):
+                 tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0,
+                 locality_order: bool = False):
         self.lib = N.load()
         self.precision = precision
         self.device = torch.device("cuda", device)
@@ -72,6 +73,7 @@ class Context:
         cfg.trace = int(trace)
         cfg.batch_order = batch_order
         cfg.batch_ctas_per_sm = batch_ctas_per_sm
+        cfg.locality_order = int(locality_order)
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1

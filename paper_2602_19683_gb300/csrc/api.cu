@@ -140,6 +140,7 @@ gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
   cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 8 : 1;
   cm.tensor_cores = cm.update_group > 1;
   cm.pair_rows = cm.tensor_cores && T == 128;
+  cm.locality_eps = (cm.tensor_cores && c->cfg.locality_order) ? 0.1 : 0.0;
   // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
   cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
   cm.sec_per_flop32 = 1.0 / 3.0e11;
@@ -272,7 +273,8 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   if (c.ir_tol <= 0) c.ir_tol = 1e-15;
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
-  if (c.batch_order < 0 || c.batch_order > 1 || c.batch_ctas_per_sm < 0 || c.batch_ctas_per_sm > 2)
+  if (c.batch_order < 0 || c.batch_order > 1 || c.batch_ctas_per_sm < 0 || c.batch_ctas_per_sm > 2 ||
+      c.locality_order < 0 || c.locality_order > 1)
     return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(device));
   gp_ctx* ctx = new (std::nothrow) gp_ctx();
@@ -365,12 +367,15 @@ int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
 
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap) {
-  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4) return -1;
+  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4 || mixed < 0 || mixed > 3 ||
+      mixed == 2)
+    return -1;
   gpk::CostModel cm;
   cm.mixed = mixed != 0;
   cm.update_group = (mixed && T % 128 == 0) ? 8 : 1;
   cm.tensor_cores = cm.update_group > 1;
   cm.pair_rows = cm.tensor_cores && T == 128;
+  cm.locality_eps = (cm.tensor_cores && (mixed & 2)) ? 0.1 : 0.0;
   std::vector<gpk::Task4> v;
   if (graph == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
   if (graph == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);

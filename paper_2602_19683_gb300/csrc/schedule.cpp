@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <queue>
+#include <unordered_map>
 #include <utility>
 
 #include "kernels.h"
@@ -13,7 +14,7 @@
 namespace gpk {
 
 std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
-                               int workers, const std::vector<double>* group_key) {
+                               int workers, const std::vector<double>* group_key, const LocalityKeys* loc) {
   const int n = (int)cost.size();
   std::vector<std::vector<int>> succ(n);
   std::vector<int> indeg(n, 0);
@@ -34,8 +35,34 @@ std::vector<int> list_schedule(const std::vector<double>& cost, const std::vecto
     return bl[a] < bl[b] || (bl[a] == bl[b] && a > b);
   };
   std::priority_queue<int, std::vector<int>, decltype(cmp)> ready(cmp);
+  // operand locality: ready tasks by key (entries of started tasks are dropped lazily)
+  const bool use_loc = loc && loc->eps > 0 && (int)loc->a.size() == n && (int)loc->b.size() == n;
+  std::unordered_map<long long, std::vector<int>> by_a, by_b;
+  std::vector<char> started(n, 0);
+  long long last_a = -1, last_b = -1;
+  auto make_ready = [&](int t) {
+    ready.push(t);
+    if (use_loc) {
+      if (loc->a[t] >= 0) by_a[loc->a[t]].push_back(t);
+      if (loc->b[t] >= 0) by_b[loc->b[t]].push_back(t);
+    }
+  };
+  // the best-ranked ready task sharing key k (or -1), dropping started ones from the list
+  auto best_sharing = [&](std::unordered_map<long long, std::vector<int>>& m, long long k, int best) {
+    if (k < 0) return best;
+    auto it = m.find(k);
+    if (it == m.end()) return best;
+    std::vector<int>& v = it->second;
+    size_t w = 0;
+    for (size_t i = 0; i < v.size(); ++i)
+      if (!started[v[i]]) v[w++] = v[i];
+    v.resize(w);
+    for (int c : v)
+      if (best < 0 || bl[c] > bl[best]) best = c;
+    return best;
+  };
   for (int t = 0; t < n; ++t)
-    if (indeg[t] == 0) ready.push(t);
+    if (indeg[t] == 0) make_ready(t);
   using Ev = std::pair<double, int>;  // (finish time, task)
   std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
   std::vector<int> order;
@@ -43,9 +70,18 @@ std::vector<int> list_schedule(const std::vector<double>& cost, const std::vecto
   double now = 0.0;
   int free_workers = std::max(1, workers);
   while ((int)order.size() < n) {
-    while (free_workers > 0 && !ready.empty()) {
-      const int t = ready.top();
-      ready.pop();
+    while (free_workers > 0) {
+      while (!ready.empty() && started[ready.top()]) ready.pop();
+      if (ready.empty()) break;
+      int t = ready.top();
+      if (use_loc) {
+        const int c = best_sharing(by_b, last_b, best_sharing(by_a, last_a, -1));
+        if (c >= 0 && bl[c] >= (1.0 - loc->eps) * bl[t]) t = c;
+        if (loc->a[t] >= 0) last_a = loc->a[t];
+        if (loc->b[t] >= 0) last_b = loc->b[t];
+      }
+      if (t == ready.top()) ready.pop();
+      started[t] = 1;
       order.push_back(t);
       running.push({now + cost[t], t});
       --free_workers;
@@ -56,7 +92,7 @@ std::vector<int> list_schedule(const std::vector<double>& cost, const std::vecto
     now = e.first;
     ++free_workers;
     for (int s : succ[e.second])
-      if (--indeg[s] == 0) ready.push(s);
+      if (--indeg[s] == 0) make_ready(s);
   }
   return order;
 }
@@ -79,8 +115,9 @@ struct Builder {
     preds.push_back(std::move(d));
     return (int)tasks.size() - 1;
   }
-  std::vector<Task4> ordered(int workers, const std::vector<double>* group_key = nullptr) const {
-    std::vector<int> ord = list_schedule(cost, preds, workers, group_key);
+  std::vector<Task4> ordered(int workers, const std::vector<double>* group_key = nullptr,
+                             const LocalityKeys* loc = nullptr) const {
+    std::vector<int> ord = list_schedule(cost, preds, workers, group_key, loc);
     std::vector<Task4> out;
     out.reserve(ord.size());
     for (int t : ord) out.push_back(tasks[t]);
@@ -162,8 +199,23 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   }
   // Longest-remaining-path order. (A column-group / super-tile order for the grouped updates keeps
   // their operands in L2 — 98 % modelled hits against 14 % — but delays the updates the diagonal
-  // chain waits for; measured at n = 32768 both orders give the same factorisation time.)
-  return b.ordered(workers);
+  // chain waits for; measured at n = 32768 both orders give the same factorisation time.) With
+  // cm.locality_eps, grouped updates that share a packed operand group -- L_{I,J0..J1} (a) or
+  // L_{K,J0..J1} (b) -- are started back to back when their rank allows (LocalityKeys).
+  if (cm.locality_eps <= 0.0) return b.ordered(workers);
+  LocalityKeys loc;
+  loc.eps = cm.locality_eps;
+  loc.a.assign(b.tasks.size(), -1);
+  loc.b.assign(b.tasks.size(), -1);
+  for (size_t i = 0; i < b.tasks.size(); ++i) {
+    const Task4& t = b.tasks[i];
+    const int J0 = t.r & 0xFFFF, J1 = t.r >> 16;
+    if ((t.kind == TASK_UPD || t.kind == TASK_UPD2) && J1 - J0 > 1) {
+      loc.a[i] = (long long)t.p * 65536 + J0;
+      loc.b[i] = (long long)t.q * 65536 + J0;
+    }
+  }
+  return b.ordered(workers, nullptr, &loc);
 }
 
 std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel& cm, bool with_w) {

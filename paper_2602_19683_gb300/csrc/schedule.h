@@ -22,8 +22,21 @@ struct CostModel {
   // Grouped updates of tiles (I, K) and (I + 1, K) as one task (TASK_UPD2; tile edge 128 on the tensor
   // cores): the shared L_KJ is copied once for both, a quarter fewer operand bytes requested per product.
   bool pair_rows = false;
+  // > 0: the grouped updates are ordered with operand locality (LocalityKeys, this eps).
+  double locality_eps = 0.0;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
+};
+
+// Operand locality for list_schedule: per task the keys of the packed left (a) and right (b) operand
+// groups it reads (-1: none). After starting a task, the scheduler starts next a ready task that
+// shares the last started task's a or b key -- the best-ranked such task -- as long as its bottom
+// level is within a factor (1 - eps) of the best ready task's; otherwise the best ready task. Tasks
+// started back to back run side by side on the persistent kernel's CTAs, so the shared operand is
+// read from HBM once and from L2 by the others.
+struct LocalityKeys {
+  std::vector<long long> a, b;
+  double eps = 0.0;
 };
 
 // Tasks of the tiled right-looking Cholesky (Fig. 1) on Mt x Mt tiles of edge T, in the order a
@@ -39,7 +52,7 @@ std::vector<Task4> mean_tasks(int Mt, int T, int workers, const CostModel& cm);
 
 // One dispatch order for a batch of independent GPs, each running its tiled Cholesky, the two
 // substitutions of the mean solve and the covariance solve (each solve task depending on the factor
-// tiles it reads). Task kinds carry the GP index in their high bits (kind | g << 4).
+// tiles it reads). Task kinds carry the GP index in their high bits (kind | g << 5).
 struct BatchGp {
   int Mt, Mc, T;
 };
@@ -50,8 +63,10 @@ std::vector<Task4> batch_tasks(const std::vector<BatchGp>& gps, bool want_cov, i
 
 // Generic list scheduling: returns the start order of tasks with the given costs and
 // predecessor lists, simulated on `workers` identical workers. Ready tasks are ranked by
-// (group_key, bottom level) when group_key is given, else by bottom level alone.
+// (group_key, bottom level) when group_key is given, else by bottom level alone; with loc, a ready
+// task sharing an operand with the last started one may go first (LocalityKeys).
 std::vector<int> list_schedule(const std::vector<double>& cost, const std::vector<std::vector<int>>& preds,
-                               int workers, const std::vector<double>* group_key = nullptr);
+                               int workers, const std::vector<double>* group_key = nullptr,
+                               const LocalityKeys* loc = nullptr);
 
 }  // namespace gpk

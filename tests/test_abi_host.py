@@ -55,7 +55,8 @@ def tasks(lib, graph, Mt, Mc, T, workers, mixed=0):
     return out
 
 
-@pytest.mark.parametrize("Mt,workers,mixed", [(1, 4, 0), (2, 1, 0), (5, 3, 1), (9, 304, 0), (16, 304, 1)])
+@pytest.mark.parametrize("Mt,workers,mixed", [(1, 4, 0), (2, 1, 0), (5, 3, 1), (9, 304, 0), (16, 304, 1),
+                                               (16, 152, 3), (40, 152, 3)])
 def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
     """Every tile of the lower triangle receives POTRF/TRSM once and its updates J = 0..min-1 in order,
     and each task appears after the tasks whose tiles it reads (Fig. 1's dependencies)."""
@@ -192,6 +193,25 @@ def test_schedule_rejects_bad_arguments(lib):
     assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(5, 4, 0, 64, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 128, 1, 2, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 128, 1, 4, None, 0) == -1
+
+
+def _shared_neighbours(t):
+    """Fraction of consecutive grouped updates (in dispatch order) that share a packed operand group
+    (same row I or same column K, same first column J0) with the one started just before."""
+    g = [(p, q, r & 0xFFFF) for kind, p, q, r in t if kind in (2, 19) and (r >> 16) - (r & 0xFFFF) > 1]
+    same = sum(1 for a, b in zip(g, g[1:]) if a[2] == b[2] and (a[0] == b[0] or a[1] == b[1]))
+    return same / max(1, len(g) - 1)
+
+
+def test_locality_order_starts_operand_sharers_together(lib):
+    """cfg.locality_order: the same tasks (a valid order, checked above) with far more grouped updates
+    started right after one that reads the same packed operand group."""
+    base = tasks(lib, 0, 128, 0, 128, 152, 1)
+    loc = tasks(lib, 0, 128, 0, 128, 152, 3)
+    assert sorted(map(tuple, base)) == sorted(map(tuple, loc))
+    assert _shared_neighbours(loc) > 0.8 and _shared_neighbours(base) < 0.3
 
 
 def test_autotune_cache_key_and_class_table():
