@@ -1,0 +1,148 @@
+"""Parity at the full sizes of the extension workloads, on outputs the oracle can check one by one or
+on properties that hold at any size:
+
+* the large GP (n = 65536 training, m = 8192 test, D = 16) in mixed precision, in the benchmark's
+  launch configuration: factor entries, refined residual, mean, and predictive variances against the
+  oracle's FP64 substitution on the GPU's own factor (read back in row blocks);
+* the NLML gradient at n = 16384, D = 8: the FP64 gradient against central differences of the
+  library's own FP64 NLML, and the mixed gradient against the FP64 one;
+* 512 uneven GPs (n ~ U[128, 4096], m = 256, D in {4, 8, 16}) in one batched launch, FP64 and FP32:
+  sampled GPs against the oracle, every GP's covariance symmetric with variances in [0, v], and the
+  FP32 batch against the FP64 batch.
+"""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import nfir
+import oracle
+from oracle import Hyper
+
+H0 = Hyper(1.0, 1.0, 0.1)
+
+
+@pytest.fixture(scope="module")
+def api():
+    __graft_entry__.build()
+    from paper_2602_19683_gb300 import api as A
+    return A
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    d = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (d if d > 0 else 1.0))
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to("cuda") for a in arrs]
+
+
+def blocked_forward(read_rows, n, rhs, block):
+    """V = L^{-1} rhs (rhs: n x k) for a lower-triangular L available only as row blocks:
+    read_rows(r0, nrows) -> the nrows x n rows r0.. of L. Each block: subtract the product with the
+    solved part (numpy), then the oracle's forward substitution on the block's diagonal part."""
+    V = np.zeros_like(rhs)
+    for r0 in range(0, n, block):
+        nb = min(block, n - r0)
+        Lb = read_rows(r0, nb)
+        b = rhs[r0:r0 + nb] - Lb[:, :r0] @ V[:r0]
+        V[r0:r0 + nb] = oracle.forward(np.ascontiguousarray(Lb[:, r0:r0 + nb]), np.ascontiguousarray(b))
+    return V
+
+
+def test_blocked_forward_matches_whole_substitution():
+    """The row-block substitution used below against the oracle's whole-matrix forward substitution."""
+    X, _, Xs, _ = nfir.make_dataset(300, 5, 3, 4)
+    L = oracle.cholesky(oracle.assemble_K(X, H0))
+    rhs = oracle.assemble_cross(Xs, X, H0).T.copy()
+    V = blocked_forward(lambda r0, nb: L[r0:r0 + nb], 300, rhs, 64)
+    assert rel(V, oracle.forward(L, rhs)) <= 1e-14
+
+
+@pytest.mark.gpu
+def test_large_gp_mixed_sampled(api):
+    n, m, D = 65536, 8192, 16
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
+    ctx = api.Context(0, precision="fp32")
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    mean, iters = api.gp_predict_mean(ctx, f, yd, Xsd, want_iters=True)
+    alpha = api.gp_alpha(ctx, f).cpu().numpy()
+    var = api.gp_predict_var(ctx, f, Xsd)
+    api.gp_sync(ctx)
+    assert 1 <= iters <= 10
+    rng = np.random.default_rng(2)
+    rows = np.sort(rng.choice(n, 24, replace=False))
+    Lrows = np.concatenate([api.gp_factor_rows(ctx, f, int(r), 1).cpu().numpy() for r in rows])
+    ii, jj = np.meshgrid(np.arange(len(rows)), np.arange(len(rows)), indexing="ij")
+    Kij = oracle.kernel_entries(X, X, rows[ii.ravel()], rows[jj.ravel()], rows[ii.ravel()] == rows[jj.ravel()], H0)
+    assert rel((Lrows @ Lrows.T).ravel(), Kij) <= 1e-4  # FP32-class updates over 512 tile columns
+    # refined residual at the scale the refinement's stopping rule (normwise backward error) uses;
+    # ||K||_inf <= n (v + s2)
+    r = y[rows] - oracle.kernel_rows_matvec(X, rows, alpha, H0)
+    scale = n * (H0.v + H0.s2) * np.max(np.abs(alpha)) + np.max(np.abs(y))
+    assert np.max(np.abs(r)) <= 1e-13 * scale
+    cols = np.sort(rng.choice(m, 8, replace=False))
+    ks = oracle.assemble_cross(Xs[cols], X, H0)  # 8 x n
+    assert rel(mean.cpu().numpy()[cols], ks @ alpha) <= 1e-10
+    V = blocked_forward(lambda r0, nb: api.gp_factor_rows(ctx, f, r0, nb).cpu().numpy(), n,
+                        np.ascontiguousarray(ks.T), 4096)
+    vref = H0.v - np.sum(V * V, axis=0)
+    # what remains is the FP32-class error of the tensor-core V solve (the factor's own error cancels)
+    assert np.max(np.abs(var.cpu().numpy()[cols] - vref)) <= 1e-3 * H0.v
+
+
+@pytest.mark.gpu
+def test_nlml_gradient_full_size(api):
+    n, D = 16384, 8
+    X, y, _, _ = nfir.make_dataset(n, 1, D, 0)
+    Xd, yd = to_dev(X, y)
+    ctx = api.Context(0)
+    theta = np.array([1.0, 1.0, 0.1])
+    nl, g = api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*theta))
+    g = np.array(g)
+    for k in range(3):
+        h = 1e-5 * theta[k]
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*tp))[0] - api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*tm))[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-4 * abs(g[k]), (k, fd, g[k])
+    nl32, g32 = api.gp_nlml_grad(api.Context(0, precision="fp32"), Xd, yd, api.Hyper(*theta))
+    assert abs(nl32 - nl) <= 1e-5 * abs(nl)
+    assert np.max(np.abs(np.array(g32) - g)) <= 1e-4 * np.max(np.abs(g))
+
+
+@pytest.mark.gpu
+def test_batch_512_uneven_gps(api):
+    B, m = 512, 256
+    data = nfir.make_batch(B, m)
+    gps = [tuple(torch.from_numpy(a).cuda() for a in (X, y, Xs)) + (api.Hyper(*H0),) for X, y, Xs, _ in data]
+    out = {}
+    for prec in ("fp64", "fp32"):
+        ctx = api.Context(0, precision=prec)
+        b = api.Batch(ctx, gps, want_cov=True)
+        b.run()
+        api.gp_sync(ctx)
+        out[prec] = ([x.cpu().numpy() for x in b.means], [c.cpu().numpy() for c in b.covs])
+        b.free()
+    means, covs = out["fp64"]
+    for c in covs:
+        assert np.all(np.isfinite(c))
+        assert np.max(np.abs(c - c.T)) <= 1e-12 * H0.v
+        d = np.diag(c)
+        assert np.all(d >= -1e-12) and np.all(d <= H0.v * (1 + 1e-12))
+    ns = np.array([X.shape[0] for X, _, _, _ in data])
+    rng = np.random.default_rng(5)
+    sample = sorted(set(rng.choice(B, 4, replace=False).tolist()) | {int(np.argmax(ns)), int(np.argmin(ns))})
+    for g in sample:
+        X, y, Xs, _ = data[g]
+        ref = oracle.gp_predict(X, y, Xs, H0)
+        assert rel(means[g], ref["mean"]) <= 1e-10, g
+        assert rel(covs[g], ref["cov"]) <= 1e-9, g
+    m32, c32 = out["fp32"]
+    assert max(rel(a, r) for a, r in zip(m32, means)) <= 1e-2
+    assert max(np.max(np.abs(a - r)) for a, r in zip(c32, covs)) <= 1e-2 * H0.v
