@@ -194,6 +194,12 @@ gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp
  * NOT_PD info holds the GP index in its high 32 bits and the column in the low 32 bits). */
 gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
 gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
+/* One-shot batch: gp_batch_create, one gp_batch_run and gp_batch_free, then the device status as
+ * gp_sync returns it (and clears it; create/run/gp_sync separately give the error's detail). With
+ * want_cov = 0 only the means are computed (the descriptors' cov_out are ignored). Synchronous;
+ * for repeated solves of the same shapes keep a gp_batch instead (its graph is captured once). */
+gp_status gp_batch_predict(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, int32_t want_cov);
+
 /* Sets the schedule of later gp_batch_create calls: cfg.batch_order (0 or 1) and
  * cfg.batch_ctas_per_sm (0..2), as gp_create validates them (GP_ERR_INVALID_ARG otherwise). For a
  * schedule chosen earlier by gp_batch_autotune and kept by the caller (the Python binding's JSON

@@ -290,6 +290,15 @@ def _batch_descs(gps, want_cov: bool):
     return descs, inputs, means, covs
 
 
+def batch_predict(ctx: Context, gps, want_cov: bool = True):
+    """One-shot gp_batch_predict on entries (X, y, Xs, hyper[, tile]): returns (means, covs), covs
+    None per GP without want_cov. Waits for the GPU; device errors raise GPError."""
+    descs, inputs, means, covs = _batch_descs(gps, want_cov)
+    _check(ctx.lib.gp_batch_predict(ctx.h, len(gps), descs, int(bool(want_cov))), "gp_batch_predict")
+    del inputs
+    return means, covs
+
+
 def _pow2_ceil(x: int) -> int:
     return 1 << max(0, int(x) - 1).bit_length()
 

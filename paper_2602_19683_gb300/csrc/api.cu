@@ -936,6 +936,19 @@ gp_status gp_batch_free(gp_ctx* c, gp_batch* b) {
   return GP_OK;
 }
 
+gp_status gp_batch_predict(gp_ctx* c, int32_t B, const gp_batch_desc* descs, int32_t want_cov) {
+  if (!c || !descs || B < 1) return GP_ERR_INVALID_ARG;
+  std::vector<gp_batch_desc> d(descs, descs + B);
+  if (!want_cov)
+    for (gp_batch_desc& x : d) x.cov_out = nullptr;
+  gp_batch* b = nullptr;
+  GP_TRY(gp_batch_create(c, B, d.data(), &b));
+  const gp_status st = gp_batch_run(c, b);
+  gp_batch_free(c, b);  // waits for the stream
+  if (st != GP_OK) return st;
+  return gp_sync(c, nullptr);
+}
+
 }  // extern "C"
 
 namespace {

@@ -154,3 +154,21 @@ def test_batch_schedule_options(api, order, ctas):
         assert torch.equal(b.means[g], base.means[g]) and torch.equal(b.covs[g], base.covs[g])
     b.free()
     base.free()
+
+
+def test_one_shot_batch_predict(api):
+    """gp_batch_predict (create + run + free + status in one call) gives the Batch object's results
+    bit for bit, with and without the covariance."""
+    gps = make_gps(5, 30, seed0=4500)
+    dev = [(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(Xs).cuda(), h)
+           for X, y, Xs, h in gps]
+    ctx = api.Context(0)
+    b = api.Batch(ctx, dev, want_cov=True)
+    b.run()
+    api.gp_sync(ctx)
+    means, covs = api.batch_predict(ctx, dev, want_cov=True)
+    means_only, none = api.batch_predict(ctx, dev, want_cov=False)
+    for g in range(len(gps)):
+        assert torch.equal(means[g], b.means[g]) and torch.equal(covs[g], b.covs[g])
+        assert torch.equal(means_only[g], b.means[g]) and none[g] is None
+    b.free()
