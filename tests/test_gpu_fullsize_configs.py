@@ -61,9 +61,7 @@ def test_blocked_forward_matches_whole_substitution():
     assert rel(V, oracle.forward(L, rhs)) <= 1e-14
 
 
-@pytest.mark.gpu
-def test_large_gp_mixed_sampled(api):
-    n, m, D = 65536, 8192, 16
+def check_large_gp(api, to_dev, n, m, D, block):
     X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
     ctx = api.Context(0, precision="fp32")
     Xd, yd, Xsd = to_dev(X, y, Xs)
@@ -89,15 +87,13 @@ def test_large_gp_mixed_sampled(api):
     ks = oracle.assemble_cross(Xs[cols], X, H0)  # 8 x n
     assert rel(mean.cpu().numpy()[cols], ks @ alpha) <= 1e-10
     V = blocked_forward(lambda r0, nb: api.gp_factor_rows(ctx, f, r0, nb).cpu().numpy(), n,
-                        np.ascontiguousarray(ks.T), 4096)
+                        np.ascontiguousarray(ks.T), block)
     vref = H0.v - np.sum(V * V, axis=0)
     # what remains is the FP32-class error of the tensor-core V solve (the factor's own error cancels)
     assert np.max(np.abs(var.cpu().numpy()[cols] - vref)) <= 1e-3 * H0.v
 
 
-@pytest.mark.gpu
-def test_nlml_gradient_full_size(api):
-    n, D = 16384, 8
+def check_nlml_gradient(api, to_dev, n, D):
     X, y, _, _ = nfir.make_dataset(n, 1, D, 0)
     Xd, yd = to_dev(X, y)
     ctx = api.Context(0)
@@ -116,11 +112,9 @@ def test_nlml_gradient_full_size(api):
     assert np.max(np.abs(np.array(g32) - g)) <= 1e-4 * np.max(np.abs(g))
 
 
-@pytest.mark.gpu
-def test_batch_512_uneven_gps(api):
-    B, m = 512, 256
-    data = nfir.make_batch(B, m)
-    gps = [tuple(torch.from_numpy(a).cuda() for a in (X, y, Xs)) + (api.Hyper(*H0),) for X, y, Xs, _ in data]
+def check_batch(api, to_dev, B, m, n_hi):
+    data = nfir.make_batch(B, m, n_hi=n_hi)
+    gps = [tuple(to_dev(X, y, Xs)) + (api.Hyper(*H0),) for X, y, Xs, _ in data]
     out = {}
     for prec in ("fp64", "fp32"):
         ctx = api.Context(0, precision=prec)
@@ -146,3 +140,99 @@ def test_batch_512_uneven_gps(api):
     m32, c32 = out["fp32"]
     assert max(rel(a, r) for a, r in zip(m32, means)) <= 1e-2
     assert max(np.max(np.abs(a - r)) for a, r in zip(c32, covs)) <= 1e-2 * H0.v
+
+
+@pytest.mark.gpu
+def test_large_gp_mixed_sampled(api):
+    check_large_gp(api, to_dev, 65536, 8192, 16, 4096)
+
+
+@pytest.mark.gpu
+def test_nlml_gradient_full_size(api):
+    check_nlml_gradient(api, to_dev, 16384, 8)
+
+
+@pytest.mark.gpu
+def test_batch_512_uneven_gps(api):
+    check_batch(api, to_dev, 512, 256, 4096)
+
+
+# ---------------------------------------------------------------- the checks' own logic, on the CPU
+# The same checks run against a stand-in for the library built from the oracle (FP64 throughout), at
+# small sizes: this exercises their indexing, shapes and bounds without a GPU.
+
+class _OracleFactor:
+    def __init__(self, X, h):
+        self.X, self.h = X.numpy(), h
+        self.L = None
+        self.alpha = None
+
+
+class _OracleApi:
+    """The binding's calls used by the checks, computed by the oracle on CPU tensors."""
+    Hyper = Hyper
+
+    class Context:
+        def __init__(self, device=0, precision="fp64"):
+            self.precision = precision
+
+    class Batch:
+        def __init__(self, ctx, gps, want_cov=True):
+            self.means, self.covs = [], []
+            for X, y, Xs, h in gps:
+                r = oracle.gp_predict(X.numpy(), y.numpy(), Xs.numpy(), h)
+                self.means.append(torch.from_numpy(r["mean"]))
+                self.covs.append(torch.from_numpy(r["cov"]))
+
+        def run(self):
+            pass
+
+        def free(self):
+            pass
+
+    @staticmethod
+    def gp_assemble(ctx, X, h):
+        return _OracleFactor(X, h)
+
+    @staticmethod
+    def gp_cholesky(ctx, f):
+        f.L = oracle.cholesky(oracle.assemble_K(f.X, f.h))
+
+    @staticmethod
+    def gp_predict_mean(ctx, f, y, Xs, want_iters=False):
+        f.alpha = oracle.backward(f.L, oracle.forward(f.L, y.numpy()))
+        mean = torch.from_numpy(oracle.assemble_cross(Xs.numpy(), f.X, f.h) @ f.alpha)
+        return (mean, 1) if want_iters else mean
+
+    @staticmethod
+    def gp_alpha(ctx, f):
+        return torch.from_numpy(f.alpha)
+
+    @staticmethod
+    def gp_predict_var(ctx, f, Xs):
+        V = oracle.forward(f.L, np.ascontiguousarray(oracle.assemble_cross(Xs.numpy(), f.X, f.h).T))
+        return torch.from_numpy(f.h.v - np.sum(V * V, axis=0))
+
+    @staticmethod
+    def gp_factor_rows(ctx, f, row0=0, nrows=None):
+        nrows = f.L.shape[0] - row0 if nrows is None else nrows
+        return torch.from_numpy(np.ascontiguousarray(f.L[row0:row0 + nrows]))
+
+    @staticmethod
+    def gp_sync(ctx):
+        pass
+
+    @staticmethod
+    def gp_nlml_grad(ctx, X, y, h):
+        nl, g = oracle.nlml_and_grad(X.numpy(), y.numpy(), h)
+        return nl, list(g)
+
+
+def _cpu(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)) for a in arrs]
+
+
+def test_checks_on_the_oracle_stand_in():
+    check_large_gp(_OracleApi, _cpu, 700, 64, 16, 128)
+    check_nlml_gradient(_OracleApi, _cpu, 96, 8)
+    check_batch(_OracleApi, _cpu, 12, 16, 300)
