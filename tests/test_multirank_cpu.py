@@ -43,3 +43,12 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks([3.0, 4.0], 1, device="cpu") == [3.0, 4.0]
     assert bench.whole_job_tflops(2e12, 1, 1000.0) == pytest.approx(2.0)
+
+
+def test_host_lapack_point():
+    """The bench's secondary host point (numpy's LAPACK Cholesky of the same K) reports a positive
+    rate, or says why it could not run."""
+    import bench
+    r = bench.cpu_library_cholesky(256, 8)
+    assert r["kind"].startswith("numpy.linalg.cholesky")
+    assert "unavailable" in r or (r["n"] == 256 and r["s"] > 0 and r["tflops"] > 0 and r["cores"] >= 1)
