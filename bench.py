@@ -30,16 +30,53 @@ sys.path.insert(0, ROOT)
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~2 GHz on 152 SMs)
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one FP64 Cholesky launch of the task-DAG
-# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.072 GB read + 2.594 GB written
-# (profiles/dag_kernel_fp64_cholesky_n32768.md). Traffic follows the number of tile updates,
+# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.072 GB read + 2.594 GB written.
+# Traffic follows the number of tile updates,
 # (Mt^3 - Mt)/6, so a launch with Mt tile rows of edge 256 moves this times updates(Mt)/updates(32).
 FP64_CHOL_TRAFFIC_MT32_T256 = 2.072146688e9 + 2.593921536e9
 
 
+_TF32_MEASURED = {}
+
+
+def measure_tf32_tflops(dev, size: int = 8192, reps: int = 10):
+    """Dense TF32 tensor rate of this GPU, measured live: cuBLAS FP32 GEMM with TF32 tensor cores
+    allowed (torch.matmul, size^3, 2 size^3 flops), best of `reps` after warm-up, CUDA events. Kept for
+    the rest of the run; the denominator of the tensor-core rooflines."""
+    import torch
+    if dev in _TF32_MEASURED:
+        return _TF32_MEASURED[dev]
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = True
+        a = torch.randn(size, size, device=dev, dtype=torch.float32)
+        b = torch.randn(size, size, device=dev, dtype=torch.float32)
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        del a, b
+        torch.cuda.empty_cache()
+        _TF32_MEASURED[dev] = 2.0 * size ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return _TF32_MEASURED[dev]
+
+
 def tf32_peak_tflops():
-    """Dense TF32 tensor peak for the 3xTF32 products: the measured BF16 peak of this GPU pool
-    (MEASURED_PEAKS.json, burst) times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); without the
-    file, the profiling recipe's fallback BF16 figure (1.9 PFLOP/s)."""
+    """Dense TF32 tensor peak for the 3xTF32 products: the rate measured live in this run
+    (measure_tf32_tflops) when the bench took it; otherwise the measured BF16 peak of this GPU pool
+    (MEASURED_PEAKS.json, burst) times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s), or without the
+    file the profiling recipe's fallback BF16 figure (1.9 PFLOP/s)."""
+    if _TF32_MEASURED:
+        v = max(_TF32_MEASURED.values())
+        return v, f"measured in this run: cuBLAS TF32 GEMM 8192^3 (torch.matmul), {v:.0f} TFLOP/s"
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as fh:
@@ -292,6 +329,8 @@ def run_ours(args):
     Xd, yd, Xsd = (torch.from_numpy(a).to(dev) for a in (X, y, Xs))
     h = api.Hyper(1.0, 1.0, 0.1)
     stream = torch.cuda.Stream(dev)
+    if args.precision == "fp32":
+        measure_tf32_tflops(dev)  # the tensor roofline's denominator, before anything is timed
     ctx = api.Context(local, stream=stream, tile=args.tile, precision=args.precision, grid=args.grid,
                       locality_order=args.locality_order)
     mean = torch.empty(m, dtype=torch.float64, device=dev)
@@ -377,6 +416,7 @@ def run_ours(args):
         if not args.no_mixed and args.precision == "fp64":
             mean64, cov64 = mean.clone(), cov.clone()
             logdet64 = api.gp_logdet(ctx, fac[0])
+            measure_tf32_tflops(dev)  # the tensor roofline's denominator, before the timed leg
             ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32",
                                 locality_order=args.locality_order)
             fac32 = [None]

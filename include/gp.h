@@ -195,10 +195,13 @@ gp_status gp_batch_create(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, gp
 gp_status gp_batch_run(gp_ctx* ctx, gp_batch* b);
 gp_status gp_batch_free(gp_ctx* ctx, gp_batch* b);
 /* One-shot batch: gp_batch_create, one gp_batch_run and gp_batch_free, then the device status as
- * gp_sync returns it (and clears it; create/run/gp_sync separately give the error's detail). With
- * want_cov = 0 only the means are computed (the descriptors' cov_out are ignored). Synchronous;
- * for repeated solves of the same shapes keep a gp_batch instead (its graph is captured once). */
-gp_status gp_batch_predict(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, int32_t want_cov);
+ * gp_sync returns it (and clears it), its detail in *info (host, may be NULL; for GP_ERR_NOT_PD the GP
+ * index in the high 32 bits and the column in the low 32 bits). An error still pending from an earlier
+ * call on the context is returned first, with its detail, and then nothing of the batch runs. With
+ * want_cov = 0 only the means are computed (the descriptors' cov_out are ignored). Synchronous; for
+ * repeated solves of the same shapes keep a gp_batch instead (its graph is captured once). */
+gp_status gp_batch_predict(gp_ctx* ctx, int32_t B, const gp_batch_desc* descs, int32_t want_cov,
+                           int64_t* info);
 
 /* Sets the schedule of later gp_batch_create calls: cfg.batch_order (0 or 1) and
  * cfg.batch_ctas_per_sm (0..2), as gp_create validates them (GP_ERR_INVALID_ARG otherwise). For a
@@ -252,8 +255,10 @@ gp_status gp_batch_autotune(gp_ctx* ctx, int32_t B, gp_batch_desc* descs, const 
  * X (n x D), y (n), Xs (m x D) and mean_out (m) are the caller's device arrays; nothing else is
  * needed: no context, no factor. The library's workspace is one file-scope device array of about
  * 4.5 MB (tiles of edge 64, counters, task lists, status word) that every GPU loading the library
- * holds until the process exits; its address is looked up once per device, with that device
- * current, on the first call made on it. n must be <= 1024 (larger n returns GP_ERR_INVALID_ARG).
+ * holds until the process exits. Set-up: the first call made on a device (with that device current)
+ * looks the array's device address up and keeps it; a later call looks it up again only if the
+ * device's CUDA context has changed since (for example after cudaDeviceReset). Make that first call
+ * before any stream capture. n must be <= 1024 (larger n returns GP_ERR_INVALID_ARG).
  * Runs on `cuda_stream` of the current device and waits for it, then returns the device status
  * (GP_ERR_NOT_PD with *info = failing column, GP_ERR_TIMEOUT; info may be NULL). Every call shares
  * the one array and leaves its contents behind; each call clears what must start at zero, but calls

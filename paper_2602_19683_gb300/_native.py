@@ -63,7 +63,7 @@ SIGNATURES = {
     "gp_batch_run": ([_P, _P], _I32),
     "gp_batch_free": ([_P, _P], _I32),
     "gp_set_batch_schedule": ([_P, _I32, _I32], _I32),
-    "gp_batch_predict": ([_P, _I32, ctypes.POINTER(gp_batch_desc), _I32], _I32),
+    "gp_batch_predict": ([_P, _I32, ctypes.POINTER(gp_batch_desc), _I32, ctypes.POINTER(ctypes.c_int64)], _I32),
     "gp_batch_autotune": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(gp_autotune_opts),
                            ctypes.POINTER(gp_autotune_result)], _I32),
     "gp_factor_rows": ([_P, _P, _I64, _I64, _P], _I32),

@@ -255,11 +255,18 @@ def gp_predict_mean_noalloc(X: torch.Tensor, y: torch.Tensor, Xs: torch.Tensor, 
     _dev(y, "y", (n,))
     _dev(Xs, "Xs", (m, D))
     _dev(out, "mean_out", (m,))
+    for t, name in ((y, "y"), (Xs, "Xs"), (out, "mean_out")):
+        if t.device != X.device:
+            raise ValueError(f"{name} is on {t.device}, X on {X.device}: all arrays must share one device")
+    if stream is not None and stream.device != X.device:
+        raise ValueError(f"stream belongs to {stream.device}, the arrays to {X.device}")
     lib = N.load()
-    stream = stream if stream is not None else torch.cuda.current_stream(X.device)
-    info = ctypes.c_int64(0)
-    s = lib.gp_predict_mean_noalloc(X.data_ptr(), y.data_ptr(), n, D, Hyper(*hyper).c, Xs.data_ptr(), m,
-                                    out.data_ptr(), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(info))
+    # the C entry point works on the current device: make it the arrays' device for the call
+    with torch.cuda.device(X.device):
+        stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+        info = ctypes.c_int64(0)
+        s = lib.gp_predict_mean_noalloc(X.data_ptr(), y.data_ptr(), n, D, Hyper(*hyper).c, Xs.data_ptr(), m,
+                                        out.data_ptr(), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(info))
     if s != N.GP_OK:
         raise GPError(s, info.value, "gp_predict_mean_noalloc")
     return out
@@ -294,8 +301,11 @@ def batch_predict(ctx: Context, gps, want_cov: bool = True):
     """One-shot gp_batch_predict on entries (X, y, Xs, hyper[, tile]): returns (means, covs), covs
     None per GP without want_cov. Waits for the GPU; device errors raise GPError."""
     descs, inputs, means, covs = _batch_descs(gps, want_cov)
-    _check(ctx.lib.gp_batch_predict(ctx.h, len(gps), descs, int(bool(want_cov))), "gp_batch_predict")
+    info = ctypes.c_int64(0)
+    s = ctx.lib.gp_batch_predict(ctx.h, len(gps), descs, int(bool(want_cov)), ctypes.byref(info))
     del inputs
+    if s != N.GP_OK:
+        raise GPError(s, info.value, "gp_batch_predict")
     return means, covs
 
 

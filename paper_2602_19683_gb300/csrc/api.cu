@@ -289,7 +289,7 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
     ctx->cfg.tensor_cores = -1;
   }
   for (int mixed = 0; mixed < 2; ++mixed) {
-    const int occ = gpk::dag_max_ctas_per_sm(mixed != 0);
+    const int occ = gpk::dag_max_ctas_per_sm(mixed != 0, c.tensor_cores >= 0 ? 1 : 0);
     const int cap = mixed ? 1 : 2;
     ctx->ctas_per_sm[mixed] = occ >= cap ? cap : (occ > 0 ? occ : 1);
     ctx->grid[mixed] = c.grid > 0 ? c.grid : ctx->sms * ctx->ctas_per_sm[mixed];
@@ -848,7 +848,7 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     for (long long r = 0; r < e.m; r += 8) post.push_back(make_int4(0, g, (int)r, 0));
   }
   // persistent-kernel residency, then the task order over all GPs for that many workers
-  const int occ = gpk::dag_max_ctas_per_sm_batch(mixed);
+  const int occ = gpk::dag_max_ctas_per_sm_batch(mixed, (mixed && c->cfg.tensor_cores >= 0) ? 1 : 0);
   int per_sm = c->cfg.batch_ctas_per_sm > 0 ? c->cfg.batch_ctas_per_sm : (mixed ? 1 : 2);
   if (per_sm > occ) per_sm = occ > 0 ? occ : 1;
   const int grid = c->sms * per_sm;
@@ -936,8 +936,12 @@ gp_status gp_batch_free(gp_ctx* c, gp_batch* b) {
   return GP_OK;
 }
 
-gp_status gp_batch_predict(gp_ctx* c, int32_t B, const gp_batch_desc* descs, int32_t want_cov) {
+gp_status gp_batch_predict(gp_ctx* c, int32_t B, const gp_batch_desc* descs, int32_t want_cov, int64_t* info) {
+  if (info) *info = 0;
   if (!c || !descs || B < 1) return GP_ERR_INVALID_ARG;
+  // an error still pending from an earlier call on this context is returned as it is (with its
+  // detail), before anything of this batch runs, so it is never reported as this batch's failure
+  GP_TRY(gp_sync(c, info));
   std::vector<gp_batch_desc> d(descs, descs + B);
   if (!want_cov)
     for (gp_batch_desc& x : d) x.cov_out = nullptr;
@@ -946,7 +950,7 @@ gp_status gp_batch_predict(gp_ctx* c, int32_t B, const gp_batch_desc* descs, int
   const gp_status st = gp_batch_run(c, b);
   gp_batch_free(c, b);  // waits for the stream
   if (st != GP_OK) return st;
-  return gp_sync(c, nullptr);
+  return gp_sync(c, info);
 }
 
 }  // extern "C"

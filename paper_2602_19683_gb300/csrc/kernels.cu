@@ -1150,19 +1150,22 @@ cudaError_t dag_enable_umma() {
   return e;
 }
 
-int dag_max_ctas_per_sm_batch(bool mixed) {
+// Resident CTAs per SM of the forward kernels, with the dynamic shared memory launch_dag gives them.
+int dag_max_ctas_per_sm_batch(bool mixed, int use_umma) {
   int nb = 0;
   if (mixed)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, true>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, true>, kThreads,
+                                                  mixed_dyn_smem(use_umma));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false, false, true>, kThreads, 0);
   return nb;
 }
 
-int dag_max_ctas_per_sm(bool mixed) {
+int dag_max_ctas_per_sm(bool mixed, int use_umma) {
   int nb = 0;
   if (mixed)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<true, false, false>, kThreads,
+                                                  mixed_dyn_smem(use_umma));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<false, false, false>, kThreads, 0);
   return nb;

@@ -128,7 +128,7 @@ cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long r
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st);
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,
                        bool batch = false);
-int dag_max_ctas_per_sm_batch(bool mixed);
+int dag_max_ctas_per_sm_batch(bool mixed, int use_umma);
 // Allows the dynamic shared memory of the tensor-core path (once per device).
 cudaError_t dag_enable_umma();
 // Batched pre/post work, one CTA per work item {kind, gp, a, b}:
@@ -137,7 +137,7 @@ cudaError_t dag_enable_umma();
 //   post: 0 = mean rows [a, a+8) (fused K_{Xs,X} alpha); 1 = covariance rows [a, a+8) copied/mirrored
 cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs, bool noisy_prior, cudaStream_t st);
 cudaError_t launch_batch_post(const int4* items, int nitems, const GpDesc* descs, cudaStream_t st);
-int dag_max_ctas_per_sm(bool mixed);
+int dag_max_ctas_per_sm(bool mixed, int use_umma);
 // r = y - K alpha from packed lower FP64 tiles; norms = {||r||_2^2, ||y||_2^2, ||r||_inf, ||K||_inf,
 // ||alpha||_inf, ||y||_inf} (||K||_inf only with with_knorm, else 0). partial needs 6 * Mt * (T/32) doubles.
 cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const double* y, const double* alpha,

@@ -13,6 +13,8 @@
 // each call clears what must start at zero (counters, status word, padding of the solve vector), so
 // consecutive calls are independent, but calls that overlap on the GPU (two streams, two host threads)
 // race on the array and give wrong results.
+#include <cuda.h>
+
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -47,7 +49,39 @@ static __device__ __align__(256) unsigned char g_gp_noalloc_scratch[kScratchByte
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};  // device address of g_gp_noalloc_scratch, per device
+// Device address of g_gp_noalloc_scratch per device, and the id of the CUDA context it was looked up
+// in: a device whose context was replaced since (cudaDeviceReset, another context made current)
+// loads the module again at another address, so the lookup is redone there.
+void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Id of the CUDA context current on this thread (0 if none), through the driver entry points that
+// the runtime exposes (no link-time dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_setup_mutex
+    looked_up = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (CtxGetCurrentFn)f1;
+      get_id = (CtxGetIdFn)f2;
+    }
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 // Writes the in-order task lists (a topological order of Fig. 1's tasks, and of the two
 // substitutions) for Mt tile rows: one thread, a few hundred tasks.
@@ -73,18 +107,30 @@ __global__ void noalloc_tasks_kernel(int Mt, int4* chol, int4* mean) {
   }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device. Set-up, done by the first call made on
+// a device (with that device current): cudaGetSymbolAddress, its return code checked. Later calls
+// reuse the address while the device's context stays the same one.
 gp_status scratch_on(int device, Scratch** out) {
   if (device < 0 || device >= kMaxDevices) return GP_ERR_NO_DEVICE;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[device]) {
+  unsigned long long ctx = current_context_id();
+  if (ctx == 0) {  // no context yet on this thread: make the device's primary context current
+    if (cudaSetDevice(device) != cudaSuccess) {
+      cudaGetLastError();
+      return GP_ERR_NO_DEVICE;
+    }
+    ctx = current_context_id();
+  }
+  if (!g_scratch_ptr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_gp_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
+      g_scratch_ptr[device] = nullptr;
       return GP_ERR_CUDA;
     }
     g_scratch_ptr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = (Scratch*)g_scratch_ptr[device];
   return GP_OK;

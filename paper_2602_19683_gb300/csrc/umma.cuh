@@ -1,15 +1,19 @@
-// Tensor-core (tcgen05) trailing update of the mixed-precision factorisation: C (FP64) -= A B^T with
-// the product formed from three TF32 split products (3xTF32: a_hi b_hi + a_hi b_lo + a_lo b_hi,
-// a = a_hi + a_lo with a_hi the TF32 rounding of the FP32 value and a_lo the FP32 remainder),
-// accumulated in FP32 in tensor memory (TMEM).
+// Tensor-core (tcgen05) primitives of the mixed-precision mode and its FP32-in-TMEM epilogue:
+// TMEM allocation, mbarriers with bounded waits, shared-memory matrix and instruction descriptors,
+// the kind::tf32 MMA and its commit, and tcgen05.ld of the accumulator.
 //
-// Per 128 x 128 output block: K is walked in 32-wide chunks; for each chunk all threads load the FP64
-// operands (L2), split them, and store the four operand tiles (A_hi, A_lo, B_hi, B_lo; 128 rows x 128
-// bytes each) in the canonical K-major 128-byte-swizzled layout; one thread issues the 12 MMAs of the
-// chunk (4 K-steps of 8 x 3 products, M = N = 128) and commits them to the chunk's mbarrier. Two
-// operand stages let the next chunk's staging overlap the current chunk's MMAs. The epilogue reads
-// the accumulator with tcgen05.ld (warp w owns TMEM lanes 32(w%4).. and a 64-column half) and
-// subtracts it from C in FP64.
+// The mixed trailing updates form C (FP64) -= A B^T from three TF32 split products (3xTF32:
+// a_hi b_hi + a_hi b_lo + a_lo b_hi, a = a_hi + a_lo with a_hi the TF32 rounding of the FP32 value and
+// a_lo the TF32-rounded remainder), accumulated in FP32 in tensor memory. Their main path is the
+// packed-operand pipeline of umma_packed.cuh: every panel tile is split once into the exact
+// shared-memory image the MMA reads, and the products are fed by bulk copies through three 64 KB
+// stages, one thread issuing the MMAs of each landed 32-wide k chunk. The epilogue (umma_epilogue
+// below) reads TMEM with tcgen05.ld (warp w: lanes 32(w%4).., a 64-column half), stages the
+// accumulator in shared memory and read-modify-writes the FP64 C tile with coalesced double2 accesses.
+//
+// umma_block_sub / umma_gemm_sub below are the register-staged form of the same product (operands
+// loaded from FP64 and split by all threads, two stages): the path of tiles whose packed operands
+// do not exist (tile edges that are multiples of 128 but run without the packed buffers).
 //
 // Every mbarrier wait is bounded by the task's time limit; a wait that gives up reports
 // GP_ERR_TIMEOUT and the caller returns after freeing its TMEM.

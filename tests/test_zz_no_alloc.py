@@ -1,4 +1,4 @@
-"""The allocation-free entry point gp_predict_mean_noalloc, against the regular entry points.
+"""The allocation-free entry point gp_predict_mean_noalloc, against the regular entry points and the oracle.
 
 It serves callers that cannot call cudaMalloc (real-time loops, fixed device-memory budgets, hosts
 that own all device memory): its workspace is one static device array shared by every call. This
@@ -14,6 +14,7 @@ import torch
 
 import __graft_entry__
 import nfir
+import oracle
 from oracle import Hyper
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +46,9 @@ def test_noalloc_matches_regular_path_twice(api):
         api.gp_predict_mean_noalloc(Xd, yd, Xsd, api.Hyper(*h), out)
         got = out.cpu().numpy()
         assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+        # and against the FP64 oracle directly (the two library paths share kernels)
+        want = oracle.gp_predict(X, y, Xs, h)["mean"]
+        assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
 
 
 def test_noalloc_rejects_oversize_and_reports_not_pd(api):
