@@ -55,13 +55,26 @@ enum {
   GP_ERR_NO_DEVICE = 8        /* no usable sm_103 GPU                                            */
 };
 
-/* Precision of the trailing SYRK/GEMM updates and of the panel TRSMs after the first block column
- * (the diagonal POTRFs, the first block column's TRSMs and every residual stay FP64). */
+/* Precision of the trailing SYRK/GEMM updates, of the panel TRSMs after the first block column and of
+ * the covariance products (the diagonal POTRFs and every residual stay FP64). The reduced forms keep
+ * an FP64 copy of K and refine K^{-1} y in FP64 (classic iterative refinement); their covariance and
+ * log-determinant are not refined. The tensor-core forms other than GP_FP32 need tile edge 128 (the
+ * automatic choice; cfg.tile 0 or 128) and cfg.tensor_cores = 0. */
 enum {
-  GP_FP64 = 0,      /* everything FP64                                                          */
-  GP_FP32 = 1       /* FP32-class trailing updates with FP32 accumulation (tensor cores with 3xTF32
-                       split products, or FP32 FMAs); FP64 POTRF, first-column TRSM, FP64
-                       iterative refinement of K^{-1} y                                          */
+  GP_FP64 = 0,       /* everything FP64 on the FP64 pipe                                            */
+  GP_FP32 = 1,       /* FP32-class: tensor cores with three TF32 split products (3xTF32), or FP32
+                        FMAs (cfg.tensor_cores = -1); FP64 first-column TRSM                        */
+  GP_TF32X3 = 1,     /* the same form under its operand name                                       */
+  GP_BF16X3 = 2,     /* tensor cores, BF16 split of the FP32 value into two slices, three products,
+                        FP32 accumulation (about 16 significant bits per product)                   */
+  GP_BF16X6 = 3,     /* tensor cores, three BF16 slices, six products (FP32-class, 24 bits)          */
+  GP_TF32 = 4,       /* tensor cores, one TF32 product (about 11 bits): a factor for GMRES-based
+                        refinement; loses positive definiteness on ill-conditioned K               */
+  GP_BF16 = 5,       /* tensor cores, one BF16 product (about 8 bits): as GP_TF32, coarser            */
+  GP_FP64_OZAKI = 6  /* FP64-accurate products on the BF16 tensor cores: each FP64 value cut into
+                        seven 8-bit fixed-point digits (Ozaki-style error-free splitting), the 28
+                        digit products of weight >= 2^-64 accumulated exactly per weight and summed
+                        in 64-bit integers; FP64 POTRF and diagonal-tile inverses; no refinement    */
 };
 
 typedef struct {
@@ -72,7 +85,8 @@ typedef struct {
 
 typedef struct {
   int32_t tile;           /* tile edge T (multiple of 32, 32..1024); 0 = choose automatically        */
-  int32_t precision;      /* GP_FP64 or GP_FP32                                                       */
+  int32_t precision;      /* GP_FP64, GP_FP32 (= GP_TF32X3), GP_BF16X3, GP_BF16X6, GP_TF32, GP_BF16,
+                             GP_FP64_OZAKI (above)                                                    */
   double ir_tol;          /* refinement stops when the normwise backward error ||y - K alpha||_inf /
                              (||K||_inf ||alpha||_inf + ||y||_inf) <= ir_tol (0 = 1e-15), or when it
                              stagnates at <= 100 ir_tol; otherwise GP_ERR_NO_CONVERGENCE            */
@@ -303,6 +317,16 @@ int64_t gp_launch_count(const gp_ctx* ctx);
  * returns GP_ERR_OOM with its objects left valid (retry after freeing memory); k <= 0 turns it off.
  * Not thread-safe against concurrent calls into the library. */
 void gp_debug_fail_alloc(int64_t k);
+
+/* TEST HOOK (no counterpart in the paper): one tensor-core tile product through the same device
+ * routines the persistent kernel uses for the trailing updates (Sec. 3.2's SYRK/GEMM): A and B are
+ * device 128 x K row-major FP64 arrays (K a multiple of 32, at most 1024; at most 512 for
+ * GP_FP64_OZAKI), packed in the operand format of `precision` (GP_FP32 = 3xTF32, GP_TF32, GP_BF16,
+ * GP_BF16X3, GP_BF16X6, GP_FP64_OZAKI), then C (device 128 x 128 row-major FP64) -= A B^T (store != 0:
+ * C = A B^T; lower != 0: only entries with column <= row change), repeated `reps` times on the
+ * context's stream in one CTA. Needs cfg.tensor_cores = 0. Synchronous; returns the device status. */
+gp_status gp_debug_tile_product(gp_ctx* ctx, int32_t precision, const double* A, const double* B, double* C,
+                                int32_t K, int32_t store, int32_t lower, int32_t reps);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,11 @@ from . import build as _build
 
 GP_OK, GP_ERR_INVALID_ARG, GP_ERR_NOT_PD, GP_ERR_NONFINITE, GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, \
     GP_ERR_NO_CONVERGENCE, GP_ERR_NO_DEVICE = range(9)
-GP_FP64, GP_FP32 = 0, 1
+GP_FP64, GP_FP32, GP_BF16X3, GP_BF16X6, GP_TF32, GP_BF16, GP_FP64_OZAKI = 0, 1, 2, 3, 4, 5, 6
+GP_TF32X3 = GP_FP32
+# precision names accepted by the Python binding
+PRECISIONS = {"fp64": GP_FP64, "fp32": GP_FP32, "tf32x3": GP_TF32X3, "bf16x3": GP_BF16X3, "bf16x6": GP_BF16X6,
+              "tf32": GP_TF32, "bf16": GP_BF16, "fp64_ozaki": GP_FP64_OZAKI}
 
 # Every function declared in include/gp.h, with its ctypes signature.
 _P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -63,6 +67,7 @@ SIGNATURES = {
     "gp_batch_run": ([_P, _P], _I32),
     "gp_batch_free": ([_P, _P], _I32),
     "gp_set_batch_schedule": ([_P, _I32, _I32], _I32),
+    "gp_debug_tile_product": ([_P, _I32, _P, _P, _P, _I32, _I32, _I32, _I32], _I32),
     "gp_batch_predict": ([_P, _I32, ctypes.POINTER(gp_batch_desc), _I32, ctypes.POINTER(ctypes.c_int64)], _I32),
     "gp_batch_autotune": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(gp_autotune_opts),
                            ctypes.POINTER(gp_autotune_result)], _I32),

@@ -63,7 +63,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         cfg = N.gp_config()
         cfg.tile = tile
-        cfg.precision = {"fp64": N.GP_FP64, "fp32": N.GP_FP32}[precision]
+        cfg.precision = N.PRECISIONS[precision]
         cfg.ir_tol = ir_tol
         cfg.ir_maxit = ir_maxit
         cfg.noisy_prior = int(noisy_prior)
@@ -244,6 +244,19 @@ def gp_nlml_grad(ctx: Context, X: torch.Tensor, y: torch.Tensor, hyper: Hyper):
     _check(ctx.lib.gp_nlml_grad(ctx.h, X.data_ptr(), y.data_ptr(), n, D, Hyper(*hyper).c, ctypes.byref(nl), g),
            "gp_nlml_grad")
     return nl.value, [g[0], g[1], g[2]]
+
+
+def debug_tile_product(ctx: Context, precision: str, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
+                       store: bool = False, lower: bool = False, reps: int = 1) -> torch.Tensor:
+    """Test hook gp_debug_tile_product: C (128 x 128) -= A B^T (store: C = A B^T) with A, B 128 x K
+    through the tensor-core products of `precision`, in place on C."""
+    K = A.shape[1]
+    _dev(A, "A", (128, K))
+    _dev(B, "B", (128, K))
+    _dev(C, "C", (128, 128))
+    _check(ctx.lib.gp_debug_tile_product(ctx.h, N.PRECISIONS[precision], A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                         K, int(store), int(lower), reps), "gp_debug_tile_product")
+    return C
 
 
 def gp_predict_mean_noalloc(X: torch.Tensor, y: torch.Tensor, Xs: torch.Tensor, hyper: Hyper, out: torch.Tensor,

@@ -66,7 +66,7 @@ gp_status cuda_status(cudaError_t e) {
   } while (0)
 #define GP_CUDA(x) GP_TRY(cuda_status(x))
 
-using TaskKey = std::tuple<int, int, int, int, int, int>;  // graph kind, Mt, Mc, T, workers, mixed
+using TaskKey = std::tuple<int, int, int, int, int, int>;  // graph kind, Mt, Mc, T, workers, precision form
 
 struct TaskBuf {
   DevBuf buf;
@@ -88,6 +88,7 @@ struct gp_ctx {
   std::map<TaskKey, TaskBuf> tasks;
   gp_factor* grad_factor = nullptr;  // reused by gp_nlml_grad across calls of the same size
   DevBuf trace;                      // per-task timing records of the last launch (cfg.trace)
+  DevBuf debug_work;                 // packed operands of gp_debug_tile_product
   const void* trace_tasks = nullptr; // its task list (device)
   int trace_ntasks = 0;
 };
@@ -111,7 +112,9 @@ struct gp_factor {
   DevBuf xvec;                // second solve vector (the forward result of the chunked vector solves)
   DevBuf Linv;                // inverses of the diagonal tiles of L (written by the Cholesky launch)
   DevBuf Pk, PV;              // mixed mode with tensor cores: packed operands of the panel tiles and of V
-  DevBuf PLinv;               // mixed mode, T = 128: packed FP32 inverses of the diagonal tiles
+  DevBuf PLinv;               // mixed mode, T = 128: packed inverses of the diagonal tiles
+  DevBuf PLinvExp;            // GP_FP64_OZAKI: scale exponent of each packed inverse
+  int eL = 0, eV = 0;         // GP_FP64_OZAKI: scale exponents of the packed panels of L and blocks of V
   DevBuf alpha, rvec, part;   // alpha = K^{-1} y; refinement residual and reduction partials
   DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
                                   // sums, counters, L^{-1} y
@@ -124,6 +127,31 @@ namespace {
 
 void count_launch(gp_ctx* c, int k = 1) { c->launches += k; }
 
+// Precision forms (gp.h). Every form but GP_FP64 runs the mixed persistent kernel.
+bool is_mixed(int prec) { return prec != GP_FP64; }
+// Forms that keep an FP64 copy of K and refine K^{-1} y against it.
+bool refines(int prec) { return prec != GP_FP64 && prec != GP_FP64_OZAKI; }
+// Forms whose products exist only on the tensor cores with tile edge 128.
+bool slice_form(int prec) {
+  return prec == GP_BF16X3 || prec == GP_BF16X6 || prec == GP_BF16 || prec == GP_FP64_OZAKI;
+}
+// Bytes per value of a packed tensor-core operand of the form.
+int pk_bytes(int prec) {
+  switch (prec) {
+    case GP_BF16: return 2;
+    case GP_BF16X3: return 4;
+    case GP_BF16X6: return 6;
+    case GP_FP64_OZAKI: return 14;
+    default: return 8;  // TF32 high and low parts (GP_FP32; GP_TF32 reads the high parts only)
+  }
+}
+// Smallest k with x <= 2^k (x > 0): the scale exponent of a fixed-point operand bounded by x is k + 1.
+int pow2_exponent(double x) {
+  int k = 0;
+  std::frexp(x, &k);
+  return k;
+}
+
 // Default tile edge. FP64: 256 from n = 16384 (the FP64 pipe, not the critical path, bounds the
 // factorisation there). Mixed mode on the tensor cores: 128 from n = 2048, where the FP64 POTRF of a
 // diagonal tile (its cost grows as T^3 per step, T^2 over the whole critical path) dominates.
@@ -134,13 +162,33 @@ int auto_tile(long long n, bool mixed_tc) {
   return 32;
 }
 
-gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
+gpk::CostModel cost_model(const gp_ctx* c, int prec, int T = 0) {
   gpk::CostModel cm;
-  // Mixed tensor-core updates: group 8 columns per task (one FP64 C read-modify-write for eight).
-  cm.update_group = (mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0) ? 8 : 1;
-  cm.tensor_cores = cm.update_group > 1;
-  cm.pair_rows = cm.tensor_cores && T == 128;
+  const bool mixed = is_mixed(prec);
+  // Mixed tensor-core updates: group 8 columns per task (one FP64 C read-modify-write for eight); the
+  // FP64-emulating form groups 4, so that every FP32 level sum of a task (at most 512 digit products
+  // of each pair of digit positions) stays an exact integer (bslice.cuh).
+  const bool tc = mixed && c->cfg.tensor_cores >= 0 && T % 128 == 0 && T > 0;
+  cm.update_group = tc ? (prec == GP_FP64_OZAKI ? 4 : 8) : 1;
+  cm.tensor_cores = tc;
+  cm.pair_rows = tc && T == 128 && prec == GP_FP32;
   cm.locality_eps = (cm.tensor_cores && c->cfg.locality_order) ? 0.1 : 0.0;
+  if (tc && prec != GP_FP32) {
+    // starting points from the operand bytes and products of each form (the 3xTF32 figures are measured)
+    const double bytes = pk_bytes(prec) / 8.0;
+    const double prods = prec == GP_FP64_OZAKI ? 28.0 : prec == GP_BF16X6 ? 6.0 : prec == GP_BF16X3 ? 3.0 : 1.0;
+    cm.tc_gemm = std::max(6.6e-6 * bytes, 0.35e-6 * prods * (prec == GP_TF32 ? 2.0 : 1.0));
+    cm.tc_syrk = 0.8 * cm.tc_gemm;
+    cm.tc_vgemm = 0.85 * cm.tc_gemm;
+    if (prec == GP_FP64_OZAKI) {
+      cm.tc_gemm *= 2.0;  // two 64-column halves, the left operand copied for each
+      cm.tc_syrk = cm.tc_gemm;
+      cm.tc_vgemm = cm.tc_gemm;
+      cm.tc_potrf = 403e-6 + 170e-6;  // FP64 inverse of the tile instead of the FP32 one
+      cm.tc_trsm = cm.tc_trsm0 = 60e-6;
+      cm.tc_vtrsm = 60e-6;
+    }
+  }
   // ~2 FP64 FMAs per clock per SM shared by the CTAs resident on it; FP32 SIMT ~0.3 TFLOP/s per CTA.
   cm.sec_per_flop = (double)c->ctas_per_sm[mixed ? 1 : 0] / 7.8e9;
   cm.sec_per_flop32 = 1.0 / 3.0e11;
@@ -148,15 +196,16 @@ gpk::CostModel cost_model(const gp_ctx* c, bool mixed, int T = 0) {
   return cm;
 }
 
-// Returns the device task list of graph `kind` (0 Cholesky, 1 covariance, 2 mean), building and
-// uploading it on first use.
-gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, bool mixed, const TaskBuf** out) {
+// Returns the device task list of graph `kind` (0 Cholesky, 1 covariance, 2 mean) for precision form
+// `prec`, building and uploading it on first use.
+gp_status get_tasks(gp_ctx* c, int kind, int Mt, int Mc, int T, int prec, const TaskBuf** out) {
+  const bool mixed = is_mixed(prec);
   const int workers = c->grid[mixed ? 1 : 0];
-  TaskKey key{kind, Mt, Mc, T, workers, mixed ? 1 : 0};
+  TaskKey key{kind, Mt, Mc, T, workers, prec};
   auto it = c->tasks.find(key);
   if (it == c->tasks.end()) {
     std::vector<gpk::Task4> v;
-    const gpk::CostModel cm = cost_model(c, mixed, T);
+    const gpk::CostModel cm = cost_model(c, prec, T);
     if (kind == 0) v = gpk::cholesky_tasks(Mt, T, workers, cm);
     if (kind == 1) v = gpk::cov_tasks(Mt, Mc, T, workers, cm);  // grouped products when cm says so
     if (kind == 2) v = gpk::mean_tasks(Mt, T, workers, cm);
@@ -184,13 +233,18 @@ gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
   a.st = c->d_status;
   a.timeout_ns = c->cfg.timeout_ns;
   a.withhold_task = c->cfg.withhold_enable ? c->cfg.withhold_task : -1;
-  a.use_umma = (f->precision == GP_FP32 && c->cfg.tensor_cores >= 0) ? 1 : 0;
+  a.use_umma = (is_mixed(f->precision) && c->cfg.tensor_cores >= 0) ? 1 : 0;
+  a.prec = f->precision;
+  a.pkb = pk_bytes(f->precision);
+  a.eL = f->eL;
+  a.eV = f->eV;
+  a.PLinvExp = (int*)f->PLinvExp.p;
   return a;
 }
 
 // Mixed mode on the tensor cores keeps packed operands (tile edge a multiple of 128).
 bool packed_operands(const gp_ctx* c, const gp_factor* f) {
-  return f->precision == GP_FP32 && c->cfg.tensor_cores >= 0 && f->T % 128 == 0;
+  return is_mixed(f->precision) && c->cfg.tensor_cores >= 0 && f->T % 128 == 0;
 }
 
 gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb, bool mixed) {
@@ -218,7 +272,7 @@ gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
   const size_t ncnt = (size_t)Mt * nch * 2 + (size_t)Mt * 2;
   GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 2, Mt, 0, T, false, &tb));
+  GP_TRY(get_tasks(c, 2, Mt, 0, T, GP_FP64, &tb));
   GP_TRY(grow(f->xvec, (size_t)Mt * T * sizeof(double)));
   gpk::DagArgs a = base_args(c, f);
   a.bvec = (double*)f->bvec.p;
@@ -269,7 +323,10 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   gp_config c{};
   if (cfg) c = *cfg;
   if (c.tile != 0 && (c.tile < 32 || c.tile > 1024 || c.tile % 32)) return GP_ERR_INVALID_ARG;
-  if (c.precision != GP_FP64 && c.precision != GP_FP32) return GP_ERR_INVALID_ARG;
+  if (c.precision < GP_FP64 || c.precision > GP_FP64_OZAKI) return GP_ERR_INVALID_ARG;
+  if (c.precision != GP_FP64 && c.precision != GP_FP32 && c.tensor_cores < 0) return GP_ERR_INVALID_ARG;
+  if (slice_form(c.precision) && c.tile != 0 && c.tile != 128) return GP_ERR_INVALID_ARG;
+  if (c.precision == GP_TF32 && c.tile != 0 && c.tile % 128 != 0) return GP_ERR_INVALID_ARG;
   if (c.ir_tol <= 0) c.ir_tol = 1e-15;
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
@@ -321,6 +378,7 @@ gp_status gp_destroy(gp_ctx* c) {
   if (c->grad_factor) gp_factor_free(c, c->grad_factor);
   for (auto& kv : c->tasks) release(kv.second.buf);
   release(c->trace);
+  release(c->debug_work);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalar) cudaFree(c->d_scalar);
   delete c;
@@ -338,6 +396,21 @@ int64_t gp_launch_count(const gp_ctx* c) { return c ? c->launches : 0; }
 void gp_debug_fail_alloc(int64_t k) {
   g_alloc_count.store(0);
   g_fail_at.store(k > 0 ? k : 0);
+}
+
+gp_status gp_debug_tile_product(gp_ctx* c, int32_t precision, const double* A, const double* B, double* C, int32_t K,
+                                int32_t store, int32_t lower, int32_t reps) {
+  if (!c || !A || !B || !C || K < 32 || K % 32 || precision < GP_FP32 || precision > GP_FP64_OZAKI || reps < 1)
+    return GP_ERR_INVALID_ARG;
+  if (precision == GP_FP64_OZAKI ? K > 512 : K > 1024) return GP_ERR_INVALID_ARG;
+  if (c->cfg.tensor_cores < 0) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const size_t half = (size_t)128 * K * pk_bytes(precision);
+  GP_TRY(grow(c->debug_work, 2 * half));
+  GP_CUDA(gpk::launch_debug_product(precision, A, B, C, K, store ? 1 : 0, lower ? 1 : 0, (uint8_t*)c->debug_work.p,
+                                    half, reps, c->d_status, c->cfg.timeout_ns, c->stream));
+  count_launch(c);
+  return gp_sync(c, nullptr);
 }
 
 int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
@@ -437,7 +510,10 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
 gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper h, gp_factor** K_out) {
   if (!c || !K_out || !X || n < 1 || D < 1 || D > 4096 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
-  const int T = c->cfg.tile ? c->cfg.tile : auto_tile(n, c->cfg.precision == GP_FP32 && c->cfg.tensor_cores >= 0);
+  const int prec = c->cfg.precision;
+  const int T = c->cfg.tile ? c->cfg.tile
+                            : ((slice_form(prec) || prec == GP_TF32) ? 128
+                                                                     : auto_tile(n, prec == GP_FP32 && c->cfg.tensor_cores >= 0));
   const long long Mt = (n + T - 1) / T;
   if (Mt > 46340) return GP_ERR_INVALID_ARG;  // packed tile index must fit int arithmetic
   gp_factor* f = *K_out;
@@ -447,7 +523,7 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
     if (!f) return GP_ERR_OOM;
   }
   const size_t ntiles = (size_t)Mt * (Mt + 1) / 2;
-  const bool mixed = c->cfg.precision == GP_FP32;
+  const bool mixed = refines(prec);  // keeps the FP64 copy of K for the refinement
   f->factored = false;  // a reused factor holds neither L nor alpha from here on, even if growing fails
   f->alpha_valid = false;
   gp_status s = grow(f->Kt, ntiles * T * T * sizeof(double));
@@ -469,6 +545,10 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   f->Mt = (int)Mt;
   f->h = h;
   f->precision = c->cfg.precision;
+  // fixed-point scales: |L_ij| <= sqrt(K_ii) <= sqrt(max(v + s2, 1)) (the padding's diagonal is 1) and
+  // |V_ij| <= ||V_:,j|| <= sqrt(v) (the predictive variance v - ||V_:,j||^2 is not negative)
+  f->eL = pow2_exponent(std::sqrt(std::max(h.v + h.s2, 1.0))) + 1;
+  f->eV = pow2_exponent(std::sqrt(h.v)) + 1;
   f->X = X;
   f->factored = false;
   f->alpha_valid = false;
@@ -485,13 +565,15 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   if (!c || !f || !f->Kt.p) return GP_ERR_INVALID_ARG;
   if (f->factored) return GP_ERR_INVALID_ARG;  // already holds L
   GP_CUDA(cudaSetDevice(c->device));
-  const bool mixed = f->precision == GP_FP32;
+  const bool mixed = is_mixed(f->precision);
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, mixed, &tb));
+  GP_TRY(get_tasks(c, 0, f->Mt, 0, f->T, f->precision, &tb));
   const size_t ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
+  const size_t pkb = (size_t)pk_bytes(f->precision);
   GP_TRY(grow(f->Linv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
-  if (packed_operands(c, f)) GP_TRY(grow(f->Pk, ntiles * f->T * f->T * sizeof(double)));
-  if (packed_operands(c, f) && f->T == 128) GP_TRY(grow(f->PLinv, (size_t)f->Mt * f->T * f->T * sizeof(double)));
+  if (packed_operands(c, f)) GP_TRY(grow(f->Pk, ntiles * f->T * f->T * pkb));
+  if (packed_operands(c, f) && f->T == 128) GP_TRY(grow(f->PLinv, (size_t)f->Mt * f->T * f->T * pkb));
+  if (f->precision == GP_FP64_OZAKI) GP_TRY(grow(f->PLinvExp, (size_t)f->Mt * sizeof(int)));
   GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
   gpk::DagArgs a = base_args(c, f);
   a.Linv = (double*)f->Linv.p;
@@ -508,7 +590,7 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   GP_CUDA(cudaSetDevice(c->device));
   const int T = f->T, Mt = f->Mt, nch = T / 32;
   const size_t npad = (size_t)Mt * T;
-  const bool mixed = f->precision == GP_FP32;
+  const bool mixed = refines(f->precision);  // refined against the stored FP64 K
   f->alpha_valid = false;
   GP_TRY(grow(f->bvec, npad * sizeof(double)));
   GP_TRY(grow(f->alpha, npad * sizeof(double)));
@@ -603,9 +685,9 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
                                      (double*)f->S.p, (long long)ldv, (long long)ldv, (long long)ldv, c->stream));
   count_launch(c, 2);
   GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
-  const bool mixed = f->precision == GP_FP32;
+  const bool mixed = is_mixed(f->precision);
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 1, Mt, (int)Mc, T, mixed, &tb));
+  GP_TRY(get_tasks(c, 1, Mt, (int)Mc, T, f->precision, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.V = (double*)f->V.p;
   a.ldv = (long long)ldv;
@@ -615,7 +697,7 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   a.cV = (int*)f->cCov.p;
   a.cS = a.cV + (size_t)Mt * Mc;
   if (packed_operands(c, f) && f->Pk.p) {
-    GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
+    GP_TRY(grow(f->PV, npad * ldv * (size_t)pk_bytes(f->precision)));
     a.Pk = (uint8_t*)f->Pk.p;
     a.PV = (uint8_t*)f->PV.p;
     a.PLinv = f->T == 128 ? (uint8_t*)f->PLinv.p : nullptr;
@@ -643,16 +725,16 @@ gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, d
                                      (long long)npad, (long long)ldv, c->stream));
   count_launch(c);
   GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
-  const bool mixed = f->precision == GP_FP32;
+  const bool mixed = is_mixed(f->precision);
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 4, Mt, (int)Mc, T, mixed, &tb));
+  GP_TRY(get_tasks(c, 4, Mt, (int)Mc, T, f->precision, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.V = (double*)f->V.p;
   a.ldv = (long long)ldv;
   a.Mc = (int)Mc;
   a.cV = (int*)f->cCov.p;
   if (packed_operands(c, f) && f->Pk.p) {
-    GP_TRY(grow(f->PV, npad * ldv * sizeof(double)));
+    GP_TRY(grow(f->PV, npad * ldv * (size_t)pk_bytes(f->precision)));
     a.Pk = (uint8_t*)f->Pk.p;
     a.PV = (uint8_t*)f->PV.p;
     a.PLinv = f->T == 128 ? (uint8_t*)f->PLinv.p : nullptr;
@@ -700,6 +782,7 @@ gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, i
   gp_status st = gp_predict_mean(c, f, y, nullptr, 0, nullptr, nullptr);
   if (st != GP_OK && st != GP_ERR_NO_CONVERGENCE) return st;
   const int T = f->T, Mt = f->Mt, nch = T / 32;
+  // the reverse sweep runs in FP32 FMAs for GP_FP32 and in FP64 for every other form
   const bool mixed = f->precision == GP_FP32;
   const size_t ntiles = (size_t)Mt * (Mt + 1) / 2, npad = (size_t)Mt * T, TT = (size_t)T * T;
   GP_TRY(grow(f->Bt, ntiles * TT * sizeof(double)));
@@ -723,7 +806,7 @@ gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, i
   GP_CUDA(cudaMemsetAsync(f->cRev.p, 0, nrev * sizeof(int), c->stream));
   GP_CUDA(cudaMemsetAsync(f->Pt.p, 0, (size_t)Mt * gpk::kAdjParts * TT * sizeof(double), c->stream));
   const TaskBuf* tb;
-  GP_TRY(get_tasks(c, 3, Mt, 0, T, mixed, &tb));
+  GP_TRY(get_tasks(c, 3, Mt, 0, T, mixed ? GP_FP32 : GP_FP64, &tb));
   gpk::DagArgs a = base_args(c, f);
   a.Bt = (double*)f->Bt.p;
   a.Wt = (double*)f->Wt.p;
@@ -774,6 +857,8 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     if (d.tile != 0 && (d.tile < 32 || d.tile > 1024 || d.tile % 32)) return GP_ERR_INVALID_ARG;
     if (g >= (1 << 26)) return GP_ERR_INVALID_ARG;  // GP index above the 5 task-kind bits
   }
+  // batches run GP_FP64 or GP_FP32 (their tiles are not packed, so the other forms have no path here)
+  if (c->cfg.precision != GP_FP64 && c->cfg.precision != GP_FP32) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   const bool mixed = c->cfg.precision == GP_FP32;
   bool want_cov = false;
@@ -891,6 +976,8 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     a.timeout_ns = c->cfg.timeout_ns;
     a.withhold_task = -1;
     a.use_umma = (mixed && c->cfg.tensor_cores >= 0) ? 1 : 0;
+    a.prec = c->cfg.precision;
+    a.pkb = 8;
     gpk::launch_dag(a, grid < b->ntasks ? grid : b->ntasks, mixed, cs, false, true);
     gpk::launch_batch_post((const int4*)b->items.p + b->npre, b->npost, (const gpk::GpDesc*)b->descs.p, cs);
     cudaGraph_t graph = nullptr;

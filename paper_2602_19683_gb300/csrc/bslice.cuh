@@ -1,0 +1,456 @@
+// BF16-slice products on the 5th-generation tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
+// accumulation in tensor memory) for the reduced-precision and the FP64-emulating forms of the
+// trailing updates, the panel TRSMs and the covariance products (Sec. 3.2's SYRK/GEMM/TRSM tile
+// operations, Eq. 3's V and W products). A value x is represented by kS BF16 "slices":
+//
+//  * floating split (GP_BF16 kS = 1, GP_BF16X3 kS = 2, GP_BF16X6 kS = 3): x is rounded to FP32 f,
+//    s1 = bf16(f), s2 = bf16(f - s1), s3 = bf16(f - s1 - s2) (each remainder exact in FP32). A product
+//    a b^T is formed from the slice products s_p t_q with p + q <= kS + 1 (1, 3 or 6 of them), all
+//    accumulated into one FP32 accumulator.
+//  * fixed-point digits (GP_FP64_OZAKI, kS = 7; the error-free splitting of Ozaki et al. 2012 with
+//    BF16 digits, as in the tensor-core DGEMM emulations of Mukunoki et al. 2020 and Ootomo, Ozaki and
+//    Yokota 2024): with a power-of-two scale S = 2^e (|x| <= S/2), F = round(x 2^(56-e)) is cut into
+//    balanced base-256 digits, x ~ S sum_{p=1..7} d_p 2^(-8p), |d_1| <= 128, d_2..d_7 in [-128, 128).
+//    Every digit is an integer of at most 8 significant bits, so BF16 holds it exactly and every
+//    digit product (<= 2^14) and every FP32 sum of up to 2^10 of them is exact. The digit products
+//    of equal weight (level L = p + q, L = 2..8: 28 products) are accumulated in their own TMEM
+//    region; the epilogue turns the seven exact integer level sums into one 64-bit fixed-point sum
+//    sum_L A_L 2^(56 - 8L) on the integer pipe and that into an FP64 value scaled by S_A S_B 2^-56.
+//    Truncating at level 8 drops terms of weight 2^-72 (relative to S_A S_B): the product is FP64-
+//    accurate, at 28 BF16 tensor-core products instead of one FP64 product.
+//
+// Packed operand layout (global memory, written once by cta_pack_bs, copied verbatim into shared
+// memory by bulk copies): an R x Kd operand (R a multiple of 128, Kd of 32) is a sequence of chunks,
+// one per (128-row block rb, 32-wide k block kc) in the order rb (Kd / 32) + kc; a chunk holds the kS
+// slices one after the other, each 128 rows x 32 BF16 (8 KB) in the K-major 64-byte-swizzled layout
+// the MMA reads (8-row groups 512 B apart, the 16-byte unit u of row r stored at u ^ ((r >> 1) & 3)).
+// Rows 64h..64h+63 of a slice are the contiguous 4 KB at 4096 h, themselves a valid 64-row operand.
+//
+// Every wait is bounded (DevStatus time-out); after a time-out the issuing thread waits, bounded, for
+// its own copies and MMAs in flight before the CTA leaves, so shared memory and TMEM are quiet.
+#pragma once
+#include "umma_packed.cuh"
+
+namespace gpk {
+
+constexpr int kBsKChunk = 32;                          // k per chunk (64 bytes of BF16 per row)
+constexpr int kBsSliceBytes = kUmmaM * kBsKChunk * 2;  // 8 KB: one slice of a 128-row chunk
+constexpr int kBsMaxStages = 6;
+constexpr int kBsStageMem = 192 * 1024;                // stage memory (inside kUmmaSmemBytes)
+constexpr int kOzSlices = 7, kOzLevels = 7;            // digits 1..7, levels 2..8
+constexpr int kOzLsb = 56;                             // fixed-point sum in units of 2^-56 S_A S_B
+static_assert(kBsStageMem + 1024 <= kUmmaSmemBytes, "slice stages must fit the dynamic smem");
+static_assert(kOzLevels * 64 <= kUmmaTmemCols, "seven 64-column level accumulators must fit TMEM");
+
+// Byte offset of BF16 element (r, k), r < 128 (or < 64 for a half), k < 32, in a 64-byte-swizzled slice.
+__device__ __forceinline__ uint32_t sw64_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// Instruction descriptor: kind::f16, FP32 accumulator, A and B BF16, both K-major, M = 128, N given.
+__device__ __forceinline__ uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kUmmaM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// BF16 bits (round to nearest, ties to even) of an FP32 value; finite inputs of ordinary size.
+__device__ __forceinline__ uint32_t bf16_rn_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_to_f32(uint32_t h) { return __uint_as_float(h << 16); }
+
+// Floating split of an FP32 value into kS BF16 slices (kS <= 3); each remainder is exact in FP32.
+template <int kS>
+__device__ __forceinline__ void split_float(float f, uint32_t (&h)[kS]) {
+#pragma unroll
+  for (int s = 0; s < kS; ++s) {
+    h[s] = bf16_rn_bits(f);
+    f -= bf16_to_f32(h[s]);
+  }
+}
+
+// Exact FP32 value of a small integer d (|d| < 2^22) with an FP32 add (magic-number conversion).
+__device__ __forceinline__ float small_int_to_f32(int d) {
+  return __uint_as_float(0x4B400000u + (uint32_t)d) - 12582912.0f;
+}
+
+// Fixed-point digits of x at scale 2^e (|x| <= 2^(e-1)): F = round(x 2^(56-e)) (ties away from zero),
+// cut into balanced base-256 digits d_1..d_7 (most significant first), returned as BF16 bits. Integer
+// operations on the bits of x only.
+__device__ __forceinline__ void split_fixed(double x, int e, uint32_t (&h)[kOzSlices]) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long F = 0;
+  if (ex != 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;  // 53-bit integer
+    const int sh = (ex - 1023) + 4 - e;  // x = m 2^(ex-1023-52); F = m 2^(ex-1023-52+56-e)
+    if (sh >= 0)
+      F = m << (sh < 10 ? sh : 10);  // |x| <= 2^(e-1) keeps sh <= 2; the clamp only guards the shift
+    else if (sh > -54)
+      F = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) F = -F;
+  }
+#pragma unroll
+  for (int p = kOzSlices - 1; p >= 1; --p) {
+    const int d = (int)((F + 128) & 255) - 128;
+    F = (F - d) >> 8;
+    h[p] = __float_as_uint(small_int_to_f32(d)) >> 16;
+  }
+  h[0] = __float_as_uint(small_int_to_f32((int)F)) >> 16;
+}
+
+__device__ __forceinline__ size_t bs_chunk_off(int rb, int kc, int Kd, int kS) {
+  return ((size_t)rb * (Kd / kBsKChunk) + kc) * (size_t)kS * kBsSliceBytes;
+}
+
+// Writes the packed kS-slice operand of an R x Kd FP64 block: Op[r][k] = src[r * ld + k] (trans = false)
+// or src[k * ld + r] (trans = true). kOz: fixed-point digits at scale 2^e; otherwise floating split.
+// R a multiple of 128, Kd of 32. Loads coalesced in both forms.
+template <int kS, bool kOz>
+__device__ void cta_pack_bs(const double* src, int ld, bool trans, int R, int Kd, uint8_t* dst, int e) {
+  const int t = threadIdx.x;
+  for (int rb = 0; rb < R / kUmmaM; ++rb)
+    for (int kc = 0; kc < Kd / kBsKChunk; ++kc) {
+      uint8_t* ch = dst + bs_chunk_off(rb, kc, Kd, kS);
+      if (!trans) {  // thread: k pair 2 kp (kp = t & 15), rows t >> 4 + 16 pass
+        const int kp = t & 15, rr = t >> 4;
+        double2 d[8];
+#pragma unroll
+        for (int pass = 0; pass < 8; ++pass)
+          d[pass] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(rb * kUmmaM + rr + 16 * pass) * ld +
+                                                            kc * kBsKChunk) + kp);
+#pragma unroll
+        for (int pass = 0; pass < 8; ++pass) {
+          const uint32_t off = sw64_offset(rr + 16 * pass, 2 * kp);
+          uint32_t h0[kS], h1[kS];
+          if constexpr (kOz) {
+            split_fixed(d[pass].x, e, h0);
+            split_fixed(d[pass].y, e, h1);
+          } else {
+            split_float<kS>(f64_to_f32_rn(d[pass].x), h0);
+            split_float<kS>(f64_to_f32_rn(d[pass].y), h1);
+          }
+#pragma unroll
+          for (int s = 0; s < kS; ++s)
+            *reinterpret_cast<uint32_t*>(ch + s * kBsSliceBytes + off) = h0[s] | (h1[s] << 16);
+        }
+      } else {  // thread: k = lane, rows 16 w .. 16 w + 15 (two per double2 load)
+        const int k = t & 31, w = t >> 5;
+        double2 d[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          d[q] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(kc * kBsKChunk + k) * ld + rb * kUmmaM +
+                                                         w * 16) + q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            uint32_t hv[kS];
+            if constexpr (kOz)
+              split_fixed(c ? d[q].y : d[q].x, e, hv);
+            else
+              split_float<kS>(f64_to_f32_rn(c ? d[q].y : d[q].x), hv);
+            const uint32_t off = sw64_offset(w * 16 + 2 * q + c, k);
+#pragma unroll
+            for (int s = 0; s < kS; ++s)
+              *reinterpret_cast<uint16_t*>(ch + s * kBsSliceBytes + off) = (uint16_t)hv[s];
+          }
+        }
+      }
+    }
+  fence_proxy_async_global();  // read later by bulk copies (async proxy)
+  __syncthreads();
+}
+
+// Packed kS-slice operand of an FP32 nb x nb matrix in shared memory (leading dimension ld; rows and
+// columns beyond nb are zero), floating split (the mixed forms' FP32 inverse of a diagonal tile).
+template <int kS>
+__device__ void cta_pack_bs_f32(const float* Xs, int ld, int nb, uint8_t* dst) {
+  for (int kc = 0; kc < nb / kBsKChunk; ++kc) {
+    uint8_t* ch = dst + bs_chunk_off(0, kc, nb, kS);
+    for (int e2 = threadIdx.x; e2 < kUmmaM * 16; e2 += kThreads) {
+      const int r = e2 >> 4, kp = e2 & 15;
+      float f0 = 0.f, f1 = 0.f;
+      if (r < nb) {
+        f0 = Xs[r * ld + kc * kBsKChunk + 2 * kp];
+        f1 = Xs[r * ld + kc * kBsKChunk + 2 * kp + 1];
+      }
+      uint32_t h0[kS], h1[kS];
+      split_float<kS>(f0, h0);
+      split_float<kS>(f1, h1);
+      const uint32_t off = sw64_offset(r, 2 * kp);
+#pragma unroll
+      for (int s = 0; s < kS; ++s) *reinterpret_cast<uint32_t*>(ch + s * kBsSliceBytes + off) = h0[s] | (h1[s] << 16);
+    }
+  }
+  fence_proxy_async_global();
+  __syncthreads();
+}
+
+// Smallest e with max |src| <= 2^(e-1) over an R x C FP64 block (row-major, ld): the per-tile scale
+// of a fixed-point operand used in a single-tile product. Returns -1022 for an all-zero block.
+__device__ int cta_scale_exp(const double* src, int ld, int R, int C, int* s_flag) {
+  int mx = 0;  // largest biased exponent field; a value with field ex is < 2^(ex - 1022)
+  for (int e2 = threadIdx.x; e2 < R * C; e2 += kThreads) {
+    const long long b = __double_as_longlong(__ldcg(src + (size_t)(e2 / C) * ld + e2 % C));
+    const int ex = (int)((b >> 52) & 0x7FF);
+    mx = ex > mx ? ex : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x == 0) *s_flag = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicMax(s_flag, mx);
+  __syncthreads();
+  const int ex = *s_flag;
+  __syncthreads();
+  return ex == 0 ? -1022 : ex - 1022 + 1;  // |x| < 2^(ex-1022) = 2^(e-1)
+}
+
+// x 2^e as an FP64 value, rounded to nearest (ties to even), on the integer pipe (|x| < 2^63, the
+// result in the normal range or flushed to a signed zero below it).
+__device__ __forceinline__ double i64_to_f64_scaled(long long x, int e) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned long long u = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int lz = __clzll((long long)u);
+  u <<= lz;  // leading one at bit 63
+  unsigned long long mant = u >> 11;
+  const unsigned long long rem = u & 0x7FFULL;
+  if (rem > 0x400ULL || (rem == 0x400ULL && (mant & 1ULL))) ++mant;
+  int E = 63 - lz + e;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++E;
+  }
+  if (E + 1023 <= 0) return __longlong_as_double((long long)sign);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+}
+
+// Epilogue of one 128 x 64 half of a fixed-point product whose MMAs are all complete: the seven
+// level sums (TMEM columns 64 (L - 2) + c, L = 2..8; exact integers in FP32) of every entry are
+// combined into sum_L A_L 2^(56 - 8L) in 64-bit integers, converted to FP64 with the factor 2^e2
+// (e2 = eA + eB - 56), staged in shared memory and applied to C with coalesced accesses:
+// C -= result (kStore: C = result); lower: entries with column > row are left as they are.
+// Warp w reads TMEM lanes 32 (w % 4).. and the 32-column quarter (w / 4) of the half.
+template <bool kStore>
+__device__ void oz_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int e2) {
+  umma_fence_after();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int ldS = 65;
+  double* sC = reinterpret_cast<double*>(u.smem);  // 128 x 65 doubles (the stages are free now)
+  const int row = (w & 3) * 32 + lane, cb = (w >> 2) * 32;
+  const uint32_t tl = u.tmem + ((uint32_t)((w & 3) * 32) << 16);
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    long long acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0;
+#pragma unroll
+    for (int L = 2; L <= 8; ++L) {
+      uint32_t v[8];
+      tmem_ld8(tl + (uint32_t)((L - 2) * 64 + cb + 8 * g), v);
+      tmem_wait_ld();
+      const int sh = kOzLsb - 8 * L;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int a = __float2int_rn(__uint_as_float(v[j]));
+        acc[j] += sh >= 0 ? ((long long)a << sh) : (long long)(a >> (-sh));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sC[row * ldS + cb + 8 * g + j] = i64_to_f64_scaled(acc[j], e2);
+  }
+  umma_fence_before();
+  __syncthreads();
+  for (int r = w; r < kUmmaM; r += kThreads / 32) {
+    const int m = m0 + r, n = n0 + 2 * lane;
+    double2* c2 = reinterpret_cast<double2*>(C + (size_t)m * ldc + n);
+    const double x0 = sC[r * ldS + 2 * lane], x1 = sC[r * ldS + 2 * lane + 1];
+    double2 c;
+    if (kStore) {
+      c = make_double2(x0, x1);
+    } else {
+      c = __ldcg(c2);
+      if (!lower || n <= m) c.x -= x0;
+      if (!lower || n + 1 <= m) c.y -= x1;
+    }
+    *c2 = c;
+  }
+  __syncthreads();  // smem and TMEM are reused next
+}
+
+// Pipeline state of the slice products (barriers in smem; thread 0 drives it).
+struct BsPipe {
+  uint64_t* full;   // kBsMaxStages: completed by the bulk copies' transaction bytes
+  uint64_t* empty;  // kBsMaxStages: completed by the MMA commit
+  uint32_t fph[kBsMaxStages], eph[kBsMaxStages];
+  uint32_t fpend[kBsMaxStages], epend[kBsMaxStages];
+};
+
+// Product C[128 x 128 tile at (m0, n0)] (FP64, ldc) -= (or, kStore, =) sum_j A_j[m0..] B_j[n0..]^T over
+// Kd from packed kS-slice operands (pairs j < pr.n, each A_j / B_j a packed operand whose 128-row blocks
+// rb = m0 / 128, n0 / 128 are used). kOz: fixed-point digits, scale exponents eA, eB; else floating
+// split. lower: only entries with column <= row of the tile are written (diagonal tiles).
+// Thread 0 runs copies and MMAs; all threads run the epilogue. False (error raised, copies and MMAs
+// drained) on a time-out.
+template <int kS, bool kOz, bool kStore = false>
+__device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const PkPairs& pr, int Kd, int m0,
+                             int n0, bool lower, int eA, int eB, DevStatus* st, long long timeout_ns,
+                             long long where) {
+  constexpr int kRowsB = kOz ? 64 : 128;  // B rows per pass (the fixed-point form runs two 64-column halves)
+  constexpr int kABytes = kS * kBsSliceBytes, kBBytes = kS * kRowsB * kBsKChunk * 2;
+  constexpr int kStage = kABytes + kBBytes;
+  constexpr int kStages = (kBsStageMem / kStage) < kBsMaxStages ? (kBsStageMem / kStage) : kBsMaxStages;
+  static_assert(kStages >= 2, "at least two stages");
+  static_assert(kStage % 1024 == 0, "stages stay 1024-byte aligned");
+  const int nkp = Kd / kBsKChunk, nk = nkp * pr.n;
+  const int rbA = m0 / kUmmaM, rbB = n0 / kUmmaM;
+  constexpr int kHalves = kOz ? 2 : 1;
+  for (int half = 0; half < kHalves; ++half) {
+    bool ok = true;
+    fence_async_smem();  // earlier generic use of the stage memory before the copies
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_proxy_async_global();  // packed tiles acquired through the dependency counters
+      auto load = [&](int i) {
+        const int s = i % kStages, p = i / nkp, kc = i % nkp;
+        uint8_t* base = u.smem + s * kStage;
+        mbar_expect_tx(&bp.full[s], kStage);
+        tma_bulk_g2s(base, pr.A[p] + bs_chunk_off(rbA, kc, Kd, kS), kABytes, &bp.full[s]);
+        const uint8_t* bsrc = pr.B[p] + bs_chunk_off(rbB, kc, Kd, kS);
+        if (kOz) {
+#pragma unroll
+          for (int q = 0; q < kS; ++q)
+            tma_bulk_g2s(base + kABytes + q * (kRowsB * kBsKChunk * 2), bsrc + q * kBsSliceBytes + half * 4096, 4096,
+                         &bp.full[s]);
+        } else {
+          tma_bulk_g2s(base + kABytes, bsrc, kBBytes, &bp.full[s]);
+        }
+        bp.fpend[s] = 1;
+      };
+      for (int i = 0; i < nk && i < kStages; ++i) load(i);
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i % kStages;
+        if (!mbar_wait(&bp.full[s], bp.fph[s], st, timeout_ns, where)) {
+          ok = false;
+          break;
+        }
+        bp.fph[s] ^= 1u;
+        bp.fpend[s] = 0;
+        umma_fence_after();
+        const uint32_t a0 = smem_u32(u.smem + s * kStage), b0 = a0 + kABytes;
+#pragma unroll
+        for (int ks = 0; ks < kBsKChunk / 16; ++ks) {
+          const uint32_t o = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzled row
+          if constexpr (kOz) {
+            // slice p of A against slices q = 1 .. 8 - p of B, stacked along N (64 columns each), into
+            // the level regions L = p + q (TMEM columns 64 (L - 2)); at most 4 levels per instruction
+#pragma unroll
+            for (int p = 1; p <= kOzSlices; ++p) {
+              const int nq = kOzSlices + 1 - p;
+#pragma unroll
+              for (int q0 = 1; q0 <= nq; q0 += 4) {
+                const int q1 = (q0 + 3 < nq) ? q0 + 3 : nq;
+                const int N = (q1 - q0 + 1) * 64;
+                const uint32_t acc = (i > 0 || ks > 0 || p > 1) ? 1u : 0u;  // p = 1 opens every level
+                umma_bf16(u.tmem + (uint32_t)((p + q0 - 2) * 64),
+                          umma_desc_sw64(a0 + (p - 1) * kBsSliceBytes + o),
+                          umma_desc_sw64(b0 + (q0 - 1) * (kRowsB * kBsKChunk * 2) + o), idesc_bf16(N), acc);
+              }
+            }
+          } else {
+            // products s_p t_q with p + q <= kS + 1, accumulated in one 128-column accumulator; pairs
+            // j >= 4 go to a second one (TMEM columns 128..255), so no FP32 chain spans more than four
+            const int acc_i = (i / nkp) >= kPairsPerAcc ? 1 : 0;
+            const bool first = (i % (kPairsPerAcc * nkp)) == 0 && ks == 0;
+            const uint32_t d = u.tmem + (uint32_t)(acc_i * kUmmaN);
+            bool opened = false;
+#pragma unroll
+            for (int p = 1; p <= kS; ++p)
+#pragma unroll
+              for (int q = 1; q + p <= kS + 1; ++q) {
+                umma_bf16(d, umma_desc_sw64(a0 + (p - 1) * kBsSliceBytes + o),
+                          umma_desc_sw64(b0 + (q - 1) * kBsSliceBytes + o), idesc_bf16(kUmmaN),
+                          (first && !opened) ? 0u : 1u);
+                opened = true;
+              }
+          }
+        }
+        umma_commit(&bp.empty[s]);
+        bp.epend[s] = 1;
+        if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
+          const int sp = (i - 1) % kStages, j = i - 1 + kStages;
+          if (j < nk) {
+            if (!mbar_wait(&bp.empty[sp], bp.eph[sp], st, timeout_ns, where)) {
+              ok = false;
+              break;
+            }
+            bp.eph[sp] ^= 1u;
+            bp.epend[sp] = 0;
+            load(j);
+          }
+        }
+      }
+      // every MMA complete before TMEM is read and the stages are reused
+      for (int i = 0; i < kStages; ++i) {
+        const int s = (nk + i) % kStages;  // oldest outstanding commit first
+        if (bp.epend[s]) {
+          if (ok)
+            ok = mbar_wait(&bp.empty[s], bp.eph[s], st, timeout_ns, where);
+          else
+            mbar_drain(&bp.empty[s], bp.eph[s], timeout_ns);
+          bp.eph[s] ^= 1u;
+          bp.epend[s] = 0;
+        }
+      }
+      if (!ok) {
+        for (int s = 0; s < kStages; ++s)
+          if (bp.fpend[s]) {
+            mbar_drain(&bp.full[s], bp.fph[s], timeout_ns);
+            bp.fph[s] ^= 1u;
+            bp.fpend[s] = 0;
+          }
+        for (int s = 0; s < kStages; ++s)
+          if (bp.epend[s]) {
+            mbar_drain(&bp.empty[s], bp.eph[s], timeout_ns);
+            bp.eph[s] ^= 1u;
+            bp.epend[s] = 0;
+          }
+      }
+    }
+    if (__syncthreads_or(!ok)) return false;
+    if constexpr (kOz) {
+      oz_epilogue<kStore>(u, C, ldc, m0, n0 + 64 * half, lower, eA + eB - kOzLsb);
+    } else {
+      umma_epilogue<kStore>(u, C, ldc, m0, n0, lower, pr.n > kPairsPerAcc ? 2 : 1);
+    }
+    fence_async_smem();  // generic smem traffic of the epilogue before the next bulk copies
+    __syncthreads();
+  }
+  return true;
+}
+
+}  // namespace gpk

@@ -3,10 +3,52 @@
 // cross-covariance GEMV of the predictive mean.
 #include <climits>
 
+#include "bslice.cuh"
 #include "kernels.h"
-#include "umma_packed.cuh"
 
 namespace gpk {
+
+// ---------------------------------------------------------------- tensor-core forms
+
+// Packs an R x Kd FP64 block (Op[r][k] = src[r ld + k], or src[k ld + r] when trans) in the operand
+// format of precision form `prec` (scale exponent e for the fixed-point digits of GP_FP64_OZAKI).
+__device__ __noinline__ void form_pack(int prec, const double* src, int ld, bool trans, int R, int Kd, uint8_t* dst,
+                                       int e) {
+  switch (prec) {
+    case GP_BF16: cta_pack_bs<1, false>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_BF16X3: cta_pack_bs<2, false>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_BF16X6: cta_pack_bs<3, false>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_FP64_OZAKI: cta_pack_bs<kOzSlices, true>(src, ld, trans, R, Kd, dst, e); break;
+    default: cta_pack_operand(src, ld, trans, R, Kd, dst); break;  // GP_FP32 (3xTF32), GP_TF32
+  }
+}
+
+// Packs an FP32 nb x nb matrix in shared memory (leading dimension ldx) in the form's operand format.
+__device__ __noinline__ void form_pack_f32(int prec, const float* Xs, int ldx, int nb, uint8_t* dst) {
+  switch (prec) {
+    case GP_BF16: cta_pack_bs_f32<1>(Xs, ldx, nb, dst); break;
+    case GP_BF16X3: cta_pack_bs_f32<2>(Xs, ldx, nb, dst); break;
+    case GP_BF16X6: cta_pack_bs_f32<3>(Xs, ldx, nb, dst); break;
+    default: cta_pack_tf32_f32(Xs, ldx, nb, dst); break;
+  }
+}
+
+// C (T x T tile, ldc) -= (kStore: =) sum_j A_j B_j^T from packed operands of precision form `prec`.
+// The BF16-slice forms take T = 128; eA, eB: scale exponents of the fixed-point form.
+template <bool kStore>
+__device__ __noinline__ bool form_product(UmmaState& u, BsPipe& bp, int prec, double* C, int ldc, const PkPairs& pr,
+                                          int T, bool lower, int eA, int eB, DevStatus* st, long long to,
+                                          long long where) {
+  switch (prec) {
+    case GP_BF16: return bs_block_sub<1, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
+    case GP_BF16X3: return bs_block_sub<2, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
+    case GP_BF16X6: return bs_block_sub<3, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
+    case GP_FP64_OZAKI:
+      return bs_block_sub<kOzSlices, true, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, eA, eB, st, to, where);
+    case GP_TF32: return umma_pk_gemm_sub<kStore, 1>(u, C, ldc, pr, T, T, T, lower, st, to, where);
+    default: return umma_pk_gemm_sub<kStore, 3>(u, C, ldc, pr, T, T, T, lower, st, to, where);
+  }
+}
 
 // ---------------------------------------------------------------- Eq. (1)
 
@@ -262,8 +304,10 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
   __shared__ double s_red[kThreads / 32][32];
   TileSmem& s = u.d;
   __shared__ uint64_t s_bar[2 + 2 * kPkStages];
+  __shared__ uint64_t s_bsbar[2 * kBsMaxStages];
   __shared__ uint32_t s_tmem;
   UmmaState um;
+  BsPipe bp;
   const bool use_umma = kUmma && a0.use_umma;
   if (kUmma && use_umma) {
     if (threadIdx.x < 32) {
@@ -272,6 +316,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     }
     if (threadIdx.x == 0) {
       for (int b = 0; b < 2 + 2 * kPkStages; ++b) mbar_init(&s_bar[b], 1);
+      for (int b = 0; b < 2 * kBsMaxStages; ++b) mbar_init(&s_bsbar[b], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     umma_fence_before();
@@ -285,6 +330,9 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     um.pfull = s_bar + 2;
     um.pempty = s_bar + 2 + kPkStages;
     for (int b = 0; b < kPkStages; ++b) um.fph[b] = um.eph[b] = um.fpend[b] = um.epend[b] = 0;
+    bp.full = s_bsbar;
+    bp.empty = s_bsbar + kBsMaxStages;
+    for (int b = 0; b < kBsMaxStages; ++b) bp.fph[b] = bp.eph[b] = bp.fpend[b] = bp.epend[b] = 0;
   }
   while (true) {
     if (threadIdx.x == 0) s_task = ld_relaxed(&a0.st->abort) ? INT_MAX : (int)atomicAdd(&a0.st->next_task, 1ull);
@@ -346,23 +394,40 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           aborted = true;
           break;
         }
-        if (kUmma && use_umma && a.PLinv && T == kUmmaM)  // FP32 inverse for the column's TRSMs and V solves,
-          cta_inverse_pack_smem(um.smem, T, a.PLinv + p * TT * 8);  // from the factor left in shared memory
+        if (kUmma && use_umma && a.PLinv && T == kUmmaM) {
+          uint8_t* dst = a.PLinv + (size_t)p * TT * a.pkb;
+          if (a.prec == GP_FP64_OZAKI) {
+            // FP64 inverse of the factored tile (also the vector solves' Linv), packed as fixed-point
+            // digits at its own scale for the column's TRSMs and V solves
+            __syncthreads();
+            double* Li = a.Linv + (size_t)p * TT;
+            cta_trtri(a.Kt + tri(p, p) * TT, T, Li, T, s);
+            const int e = cta_scale_exp(Li, T, T, T, &s_flag);
+            if (threadIdx.x == 0) a.PLinvExp[p] = e;
+            form_pack(a.prec, Li, T, false, T, T, dst, e);
+          } else {  // FP32 inverse from the factor left in shared memory, packed in the form's format
+            const float* Xs = cta_inverse_f32_smem(um.smem, T);
+            form_pack_f32(a.prec, Xs, T + 1, T, dst);
+          }
+        }
         cta_publish(a.cK + tri(p, p), p + 1);
         break;
       }
       case TASK_TRSM:
-        if (kUmma && use_umma && q > 0 && a.PLinv && a.Pk && T == kUmmaM) {
+        if (kUmma && use_umma && (q > 0 || a.prec == GP_FP64_OZAKI) && a.PLinv && a.Pk && T == kUmmaM) {
           // L_IJ = K_IJ X_J^T on the tensor cores, X_J the packed inverse of L_JJ (K_IJ packed first,
-          // in the slot that then receives L_IJ)
+          // in the slot that then receives L_IJ; the FP64-emulating form also for the first column)
           double* Kij = a.Kt + tri(p, q) * TT;
-          uint8_t* Pij = a.Pk + tri(p, q) * TT * 8;
-          cta_pack_operand(Kij, T, false, T, T, Pij);
+          uint8_t* Pij = a.Pk + tri(p, q) * TT * a.pkb;
+          const bool oz = a.prec == GP_FP64_OZAKI;
+          const int eK = oz ? cta_scale_exp(Kij, T, T, T, &s_flag) : 0;
+          form_pack(a.prec, Kij, T, false, T, T, Pij, eK);
           PkPairs pr;
           pr.n = 1;
           pr.A[0] = Pij;
-          pr.B[0] = a.PLinv + (size_t)q * TT * 8;
-          if (!umma_pk_gemm_sub<true>(um, Kij, T, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+          pr.B[0] = a.PLinv + (size_t)q * TT * a.pkb;
+          const int eX = oz ? __ldcg(a.PLinvExp + q) : 0;
+          if (!form_product<true>(um, bp, a.prec, Kij, T, pr, T, false, eK, eX, a.st, a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
@@ -372,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsm_right(a.Kt + tri(q, q) * TT, T, a.Kt + tri(p, q) * TT, T, T, T, s);
         if (kUmma && a.Pk && T % kUmmaM == 0) {  // the panel tile in the operand format of its readers
           __syncthreads();
-          cta_pack_operand(a.Kt + tri(p, q) * TT, T, false, T, T, a.Pk + tri(p, q) * TT * 8);
+          form_pack(a.prec, a.Kt + tri(p, q) * TT, T, false, T, T, a.Pk + tri(p, q) * TT * a.pkb, a.eL);
         }
         cta_publish(a.cK + tri(p, q), q + 1);
         break;
@@ -380,13 +445,14 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
       case TASK_UPD2: {  // the same for tiles (I, K) and (I + 1, K) together
         const int J0 = r & 0xFFFF, J1 = (r >> 16) ? (r >> 16) : J0 + 1;
         const int rows = tk.x == TASK_UPD2 ? 2 : 1;
-        if (rows == 2 && kUmma && use_umma && a.Pk && T == kUmmaM && J1 - J0 <= kUmmaMaxPairs) {
+        if (rows == 2 && kUmma && use_umma && a.Pk && T == kUmmaM && J1 - J0 <= kUmmaMaxPairs &&
+            a.prec == GP_FP32) {
           PkPairs2 pr;
           pr.n = J1 - J0;
           for (int J = J0; J < J1; ++J) {
-            pr.A0[J - J0] = a.Pk + tri(p, J) * TT * 8;
-            pr.A1[J - J0] = a.Pk + tri(p + 1, J) * TT * 8;
-            pr.B[J - J0] = a.Pk + tri(q, J) * TT * 8;
+            pr.A0[J - J0] = a.Pk + tri(p, J) * TT * a.pkb;
+            pr.A1[J - J0] = a.Pk + tri(p + 1, J) * TT * a.pkb;
+            pr.B[J - J0] = a.Pk + tri(q, J) * TT * a.pkb;
           }
           if (!umma_pk_block2_sub(um, a.Kt + tri(p, q) * TT, a.Kt + tri(p + 1, q) * TT, T, pr, T, p == q, a.st,
                                   a.timeout_ns, ti)) {
@@ -400,10 +466,11 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
               PkPairs pr;
               pr.n = J1 - J0;
               for (int J = J0; J < J1; ++J) {
-                pr.A[J - J0] = a.Pk + tri(I, J) * TT * 8;
-                pr.B[J - J0] = a.Pk + tri(q, J) * TT * 8;
+                pr.A[J - J0] = a.Pk + tri(I, J) * TT * a.pkb;
+                pr.B[J - J0] = a.Pk + tri(q, J) * TT * a.pkb;
               }
-              if (!umma_pk_gemm_sub(um, C, T, pr, T, T, T, I == q, a.st, a.timeout_ns, ti)) aborted = true;
+              if (!form_product<false>(um, bp, a.prec, C, T, pr, T, I == q, a.eL, a.eL, a.st, a.timeout_ns, ti))
+                aborted = true;
             } else if (kUmma && use_umma && T % kUmmaM == 0 && J1 - J0 <= kUmmaMaxPairs) {
               UmmaPairs pr;
               pr.n = J1 - J0;
@@ -434,13 +501,16 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         if (kUmma && use_umma && a.PLinv && a.PV && T == kUmmaM) {
           // V_Jc = X_J V_Jc on the tensor cores (V_Jc packed transposed first, in the slot that then
           // receives the solved block)
-          uint8_t* Pjc = a.PV + ((size_t)p * a.Mc + q) * TT * 8;
-          cta_pack_operand(B, (int)a.ldv, true, T, T, Pjc);
+          uint8_t* Pjc = a.PV + ((size_t)p * a.Mc + q) * TT * a.pkb;
+          const bool oz = a.prec == GP_FP64_OZAKI;
+          const int eB = oz ? cta_scale_exp(B, (int)a.ldv, T, T, &s_flag) : 0;
+          form_pack(a.prec, B, (int)a.ldv, true, T, T, Pjc, eB);
           PkPairs pr;
           pr.n = 1;
-          pr.A[0] = a.PLinv + (size_t)p * TT * 8;
+          pr.A[0] = a.PLinv + (size_t)p * TT * a.pkb;
           pr.B[0] = Pjc;
-          if (!umma_pk_gemm_sub<true>(um, B, (int)a.ldv, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+          const int eX = oz ? __ldcg(a.PLinvExp + p) : 0;
+          if (!form_product<true>(um, bp, a.prec, B, (int)a.ldv, pr, T, false, eX, eB, a.st, a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
@@ -450,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           cta_trsm_left(a.Kt + tri(p, p) * TT, T, B, (int)a.ldv, T, T, s);
         if (kUmma && a.PV && T % kUmmaM == 0) {  // V_Jc is final: its transposed operand for V and W
           __syncthreads();
-          cta_pack_operand(B, (int)a.ldv, true, T, T, a.PV + ((size_t)p * a.Mc + q) * TT * 8);
+          form_pack(a.prec, B, (int)a.ldv, true, T, T, a.PV + ((size_t)p * a.Mc + q) * TT * a.pkb, a.eV);
         }
         cta_publish(a.cV + (size_t)p * a.Mc + q, p + 1);
         break;
@@ -461,9 +531,9 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         if (kUmma && use_umma && a.Pk && a.PV && T % kUmmaM == 0) {  // V_Ic -= L_IJ V_Jc, packed operands
           PkPairs pr;
           pr.n = 1;
-          pr.A[0] = a.Pk + tri(p, q) * TT * 8;
-          pr.B[0] = a.PV + ((size_t)q * a.Mc + r) * TT * 8;
-          if (!umma_pk_gemm_sub(um, C, (int)a.ldv, pr, T, T, T, false, a.st, a.timeout_ns, ti)) {
+          pr.A[0] = a.Pk + tri(p, q) * TT * a.pkb;
+          pr.B[0] = a.PV + ((size_t)q * a.Mc + r) * TT * a.pkb;
+          if (!form_product<false>(um, bp, a.prec, C, (int)a.ldv, pr, T, false, a.eL, a.eV, a.st, a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
@@ -481,9 +551,9 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         if (kUmma && use_umma && a.PV && T % kUmmaM == 0) {  // S_ab -= V_Ja^T V_Jb, packed operands
           PkPairs pr;
           pr.n = 1;
-          pr.A[0] = a.PV + ((size_t)r * a.Mc + p) * TT * 8;
-          pr.B[0] = a.PV + ((size_t)r * a.Mc + q) * TT * 8;
-          if (!umma_pk_gemm_sub(um, C, (int)a.lds, pr, T, T, T, p == q, a.st, a.timeout_ns, ti)) {
+          pr.A[0] = a.PV + ((size_t)r * a.Mc + p) * TT * a.pkb;
+          pr.B[0] = a.PV + ((size_t)r * a.Mc + q) * TT * a.pkb;
+          if (!form_product<false>(um, bp, a.prec, C, (int)a.lds, pr, T, p == q, a.eV, a.eV, a.st, a.timeout_ns, ti)) {
             aborted = true;
             break;
           }
@@ -511,18 +581,20 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
           C = a.V + (size_t)p * T * a.ldv + (size_t)q * T;
           ldc = (int)a.ldv;
           for (int J = J0; J < J1; ++J) {
-            pr.A[J - J0] = a.Pk + tri(p, J) * TT * 8;
-            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * 8;
+            pr.A[J - J0] = a.Pk + tri(p, J) * TT * a.pkb;
+            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * a.pkb;
           }
         } else {
           C = a.S + (size_t)p * T * a.lds + (size_t)q * T;
           ldc = (int)a.lds;
           for (int J = J0; J < J1; ++J) {
-            pr.A[J - J0] = a.PV + ((size_t)J * a.Mc + p) * TT * 8;
-            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * 8;
+            pr.A[J - J0] = a.PV + ((size_t)J * a.Mc + p) * TT * a.pkb;
+            pr.B[J - J0] = a.PV + ((size_t)J * a.Mc + q) * TT * a.pkb;
           }
         }
-        if (!umma_pk_gemm_sub(um, C, ldc, pr, T, T, T, tk.x == TASK_WSYRK_G && p == q, a.st, a.timeout_ns, ti)) {
+        const bool wg = tk.x == TASK_WSYRK_G;
+        if (!form_product<false>(um, bp, a.prec, C, ldc, pr, T, wg && p == q, wg ? a.eV : a.eL, a.eV, a.st,
+                                 a.timeout_ns, ti)) {
           aborted = true;
           break;
         }
@@ -562,7 +634,8 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
         cta_publish(a.dB + p, 1);
         break;
       case TASK_TRTRI:  // read by later launches only: nothing to publish
-        cta_trtri(a.Kt + tri(p, p) * TT, T, a.Linv + (size_t)p * TT, T, s);
+        if (!(kUmma && use_umma && a.PLinv && T == kUmmaM && a.prec == GP_FP64_OZAKI))  // else done by POTRF
+          cta_trtri(a.Kt + tri(p, p) * TT, T, a.Linv + (size_t)p * TT, T, s);
         break;
       case TASK_BGEMV:  // b_J[ch] -= L_IJ[:, ch]^T x_I; chunked solves: xvec_J[ch] -= L_IJ[:, ch]^T bvec_I
         cta_gemv_T_sub(a.Kt + tri(q, p) * TT + (size_t)r * 32, T, a.bvec + (size_t)q * T,
@@ -636,6 +709,88 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
     __syncthreads();
     if (threadIdx.x < 32) tmem_dealloc(um.tmem, kUmmaTmemCols);
   }
+}
+
+// Test hook behind gp_debug_tile_product: one CTA packs A and B (128 x K FP64, row-major) in the operand
+// format of precision form `prec` into `work` and forms C (128 x 128, ldc 128) -= A B^T (store: C =
+// A B^T) with the same device routines as the persistent kernel, `reps` times (the product is timed
+// by the caller). The fixed-point form takes each operand's own scale (cta_scale_exp).
+__global__ void __launch_bounds__(kThreads, 1) debug_product_kernel(int prec, const double* A, const double* B,
+                                                                    double* C, int K, int store, int lower,
+                                                                    uint8_t* work, size_t half_bytes, int reps,
+                                                                    DevStatus* st, long long timeout_ns) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ uint64_t s_bar[2 + 2 * kPkStages];
+  __shared__ uint64_t s_bsbar[2 * kBsMaxStages];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_flag;
+  UmmaState um;
+  BsPipe bp;
+  if (threadIdx.x < 32) {
+    tmem_alloc(&s_tmem, kUmmaTmemCols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 + 2 * kPkStages; ++b) mbar_init(&s_bar[b], 1);
+    for (int b = 0; b < 2 * kBsMaxStages; ++b) mbar_init(&s_bsbar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  umma_fence_before();
+  __syncthreads();
+  umma_fence_after();
+  um.smem = reinterpret_cast<uint8_t*>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+  um.bar = s_bar;
+  um.tmem = s_tmem;
+  um.phase[0] = um.phase[1] = 0;
+  um.pending[0] = um.pending[1] = 0;
+  um.pfull = s_bar + 2;
+  um.pempty = s_bar + 2 + kPkStages;
+  for (int b = 0; b < kPkStages; ++b) um.fph[b] = um.eph[b] = um.fpend[b] = um.epend[b] = 0;
+  bp.full = s_bsbar;
+  bp.empty = s_bsbar + kBsMaxStages;
+  for (int b = 0; b < kBsMaxStages; ++b) bp.fph[b] = bp.eph[b] = bp.fpend[b] = bp.epend[b] = 0;
+  const bool oz = prec == GP_FP64_OZAKI;
+  const int eA = oz ? cta_scale_exp(A, K, kUmmaM, K, &s_flag) : 0;
+  const int eB = oz ? cta_scale_exp(B, K, kUmmaM, K, &s_flag) : 0;
+  form_pack(prec, A, K, false, kUmmaM, K, work, eA);
+  form_pack(prec, B, K, false, kUmmaM, K, work + half_bytes, eB);
+  PkPairs pr;
+  pr.n = 1;
+  pr.A[0] = work;
+  pr.B[0] = work + half_bytes;
+  bool ok = true;
+  for (int it = 0; it < reps && ok; ++it) {
+    switch (prec) {
+      case GP_BF16:
+        ok = store ? bs_block_sub<1, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<1, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        break;
+      case GP_BF16X3:
+        ok = store ? bs_block_sub<2, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<2, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        break;
+      case GP_BF16X6:
+        ok = store ? bs_block_sub<3, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<3, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        break;
+      case GP_FP64_OZAKI:
+        ok = store ? bs_block_sub<kOzSlices, true, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, eA, eB, st, timeout_ns, -2)
+                   : bs_block_sub<kOzSlices, true, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, eA, eB, st,
+                                                          timeout_ns, -2);
+        break;
+      case GP_TF32:
+        ok = store ? umma_pk_block_sub<true, 1>(um, C, kUmmaN, pr, K, 0, 0, false, st, timeout_ns, -2)
+                   : umma_pk_block_sub<false, 1>(um, C, kUmmaN, pr, K, 0, 0, lower, st, timeout_ns, -2);
+        break;
+      default:
+        ok = store ? umma_pk_block_sub<true, 3>(um, C, kUmmaN, pr, K, 0, 0, false, st, timeout_ns, -2)
+                   : umma_pk_block_sub<false, 3>(um, C, kUmmaN, pr, K, 0, 0, lower, st, timeout_ns, -2);
+        break;
+    }
+  }
+  umma_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tmem_dealloc(um.tmem, kUmmaTmemCols);
 }
 
 // r = y - K alpha for the 32 rows (tile row I = blockIdx.x / nch, chunk ch) from the packed lower
@@ -1138,6 +1293,17 @@ cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, 
     else
       dag_kernel<false, false, false><<<grid, kThreads, 0, st>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_product(int prec, const double* A, const double* B, double* C, int K, int store, int lower,
+                                 uint8_t* work, size_t half_bytes, int reps, DevStatus* st, long long timeout_ns,
+                                 cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(debug_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kUmmaSmemBytes);
+  if (e != cudaSuccess) return e;
+  debug_product_kernel<<<1, kThreads, kUmmaSmemBytes, stream>>>(prec, A, B, C, K, store, lower, work, half_bytes,
+                                                                 reps, st, timeout_ns);
   return cudaGetLastError();
 }
 

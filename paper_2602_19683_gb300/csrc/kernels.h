@@ -109,7 +109,14 @@ struct DagArgs {
   DevStatus* st;
   long long timeout_ns;
   int withhold_task;  // test hook (-1 = off): this task's completion is never published
-  int use_umma;       // mixed mode: trailing updates on the tensor cores (tcgen05, 3xTF32)
+  int use_umma;       // mixed mode: trailing updates on the tensor cores (tcgen05)
+  int prec;           // precision form of the tensor-core products (GP_FP32 = 3xTF32, GP_TF32, GP_BF16,
+                      // GP_BF16X3, GP_BF16X6, GP_FP64_OZAKI; gp.h)
+  int pkb;            // bytes per value of a packed operand of that form (8, 8, 2, 4, 6, 14)
+  int eL, eV;         // GP_FP64_OZAKI: scale exponents of the packed panel tiles of L and of the blocks of V
+                      // (|L_ij| <= 2^(eL-1), |V_ij| <= 2^(eV-1): L's rows have norm sqrt(K_ii), V's columns
+                      // norm <= sqrt(v))
+  int* PLinvExp;      // GP_FP64_OZAKI: scale exponent of each packed diagonal-tile inverse (per tile J)
   long long* trace;   // optional: per task {CTA, t_taken, t_ready, t_done} (%globaltimer ns), 4 x int64
 };
 
@@ -129,6 +136,11 @@ cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cud
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,
                        bool batch = false);
 int dag_max_ctas_per_sm_batch(bool mixed, int use_umma);
+// Test hook: C (128 x 128) (-)= A B^T (A, B: 128 x K row-major FP64) through the packed products of
+// precision form prec, in one CTA, reps times; work: 2 half_bytes of device memory for the operands.
+cudaError_t launch_debug_product(int prec, const double* A, const double* B, double* C, int K, int store, int lower,
+                                 uint8_t* work, size_t half_bytes, int reps, DevStatus* st, long long timeout_ns,
+                                 cudaStream_t stream);
 // Allows the dynamic shared memory of the tensor-core path (once per device).
 cudaError_t dag_enable_umma();
 // Batched pre/post work, one CTA per work item {kind, gp, a, b}:

@@ -141,11 +141,11 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
   if (cm.tensor_cores) {  // measured at T = 128: POTRF + FP32 inverse 403 us, FP64 TRSM 440 us, tensor
                           // TRSM 30 us, one column pair of a grouped update 6.6 us (5 us on the diagonal)
     const double s3 = t3 / (128.0 * 128.0 * 128.0), s2 = (double)T * T / (128.0 * 128.0);
-    c_potrf = 403e-6 * s3;
-    c_trsm0 = 440e-6 * s3;
-    c_trsm = 30e-6 * s2;
-    c_gemm = 6.6e-6 * s2;
-    c_syrk = 5.0e-6 * s2;
+    c_potrf = cm.tc_potrf * s3;
+    c_trsm0 = cm.tc_trsm0 * s3;
+    c_trsm = cm.tc_trsm * s2;
+    c_gemm = cm.tc_gemm * s2;
+    c_syrk = cm.tc_syrk * s2;
   }
   // Updates of a tile whose critical use is still far away are grouped: columns [J0, J1) in one task
   // (one pass over the tile's C instead of J1 - J0); the last kTail columns before the tile is needed
@@ -226,8 +226,8 @@ std::vector<Task4> cov_tasks(int Mt, int Mc, int T, int workers, const CostModel
   double c_gemm = cm.task_overhead + spf * 2.0 * t3 / cm.gemm_eff;
   if (cm.tensor_cores) {  // measured at T = 128: V solve 35 us, one column pair of a grouped product 5.5 us
     const double s2 = (double)T * T / (128.0 * 128.0);
-    c_trsm = 35e-6 * s2;
-    c_gemm = 5.5e-6 * s2;
+    c_trsm = cm.tc_vtrsm * s2;
+    c_gemm = cm.tc_vgemm * s2;
   }
   // Mixed mode on the tensor cores groups the products into one output tile: V_Ic takes columns
   // [J0, J1) together while they are far from its own solve (the last kTail one by one, as they

@@ -24,6 +24,12 @@ struct CostModel {
   bool pair_rows = false;
   // > 0: the grouped updates are ordered with operand locality (LocalityKeys, this eps).
   double locality_eps = 0.0;
+  // Task costs of the tensor-core path at T = 128 (seconds; measured for the 3xTF32 form, per-task trace
+  // at n = 32768): POTRF with the diagonal-tile inverse, first-column FP64 TRSM, tensor-core TRSM, one
+  // column of a grouped update (off the diagonal / on it), V solve, one column of a grouped V/W product.
+  // Other precision forms set their own (api.cu).
+  double tc_potrf = 403e-6, tc_trsm0 = 440e-6, tc_trsm = 30e-6, tc_gemm = 6.6e-6, tc_syrk = 5.0e-6;
+  double tc_vtrsm = 35e-6, tc_vgemm = 5.5e-6;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
 };

@@ -117,7 +117,8 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long 
 // C[128 x 128 block at (m0, n0)] (FP64, ldc) -= sum_p A_p[m0..] B_p[n0..]^T over Kd, from packed
 // operands. Thread 0 runs the copy/MMA pipeline; all threads run the epilogue. Returns false (error
 // raised, copies and MMAs drained) on a time-out.
-template <bool kStore = false>
+// kProd: 3 = the three split products (3xTF32); 1 = the high parts only (plain TF32, GP_TF32).
+template <bool kStore = false, int kProd = 3>
 __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int m0, int n0,
                                   bool lower, DevStatus* st, long long timeout_ns, long long where) {
   const int nkp = Kd / kUmmaKChunk, nk = nkp * pr.n;
@@ -156,8 +157,10 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
       for (int ks = 0; ks < kUmmaKChunk / 8; ++ks) {
         const uint32_t o = ks * 32;
         umma_tf32(d_tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_hi + o), (!first || ks > 0) ? 1u : 0u);
-        umma_tf32(d_tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
-        umma_tf32(d_tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
+        if (kProd == 3) {
+          umma_tf32(d_tmem, umma_desc_sw128(a_hi + o), umma_desc_sw128(b_lo + o), 1u);
+          umma_tf32(d_tmem, umma_desc_sw128(a_lo + o), umma_desc_sw128(b_hi + o), 1u);
+        }
       }
       umma_commit(&u.pempty[s]);
       u.epend[s] = 1;
@@ -328,13 +331,14 @@ __device__ bool umma_pk_block2_sub(UmmaState& u, double* C0, double* C1, int ldc
 // C[M x N] -= sum_p A_p B_p^T from packed operands (M, N multiples of 128; Kd of 32); lower skips the
 // blocks above the diagonal and masks the diagonal blocks. kStore: C = sum_p A_p B_p^T instead (every
 // entry written; lower must be false). False on a time-out.
-template <bool kStore = false>
+template <bool kStore = false, int kProd = 3>
 __device__ bool umma_pk_gemm_sub(UmmaState& u, double* C, int ldc, const PkPairs& pr, int Kd, int M, int N, bool lower,
                                  DevStatus* st, long long timeout_ns, long long where) {
   for (int m0 = 0; m0 < M; m0 += kUmmaM)
     for (int n0 = 0; n0 < N; n0 += kUmmaN) {
       if (lower && n0 > m0) continue;
-      if (!umma_pk_block_sub<kStore>(u, C, ldc, pr, Kd, m0, n0, lower && n0 == m0, st, timeout_ns, where)) return false;
+      if (!umma_pk_block_sub<kStore, kProd>(u, C, ldc, pr, Kd, m0, n0, lower && n0 == m0, st, timeout_ns, where))
+        return false;
     }
   return true;
 }
@@ -348,7 +352,38 @@ __device__ bool umma_pk_gemm_sub(UmmaState& u, double* C, int ldc, const PkPairs
 // block rows i = 1.. follow X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
 // Ls: the factor's lower triangle in FP32 (leading dimension lds, upper triangle zero); Xs: zeroed
 // FP32 workspace (leading dimension ldx).
+__device__ void cta_inverse_compute(const float* Ls, int lds, float* Xs, int ldx, int nb);
+
+// Packs an FP32 nb x nb matrix held in shared memory (leading dimension ldx) as the TF32 hi/lo operand
+// (rows and columns beyond nb zero).
+__device__ void cta_pack_tf32_f32(const float* Xs, int ldx, int nb, uint8_t* dst) {
+  const int t = threadIdx.x;
+  for (int kc = 0; kc < nb / kUmmaKChunk; ++kc) {
+    uint8_t* hi = dst + pk_chunk_off(0, kc, nb);
+    uint8_t* lo = hi + kUmmaTileBytes;
+    for (int e = t; e < kUmmaM * 16; e += kThreads) {  // pairs (r, 2 kp), rows beyond nb are zero
+      const int r = e >> 4, kp = e & 15;
+      float f0 = 0.f, f1 = 0.f;
+      if (r < nb) {
+        f0 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp];
+        f1 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp + 1];
+      }
+      const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
+      const uint32_t off = sw128_offset(r, 2 * kp);
+      *reinterpret_cast<float2*>(hi + off) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(lo + off) = make_float2(tf32_rn(f0 - h0), tf32_rn(f1 - h1));
+    }
+  }
+  fence_proxy_async_global();
+  __syncthreads();
+}
+
 __device__ void cta_inverse_core(const float* Ls, int lds, float* Xs, int ldx, int nb, uint8_t* dst) {
+  cta_inverse_compute(Ls, lds, Xs, ldx, nb);
+  cta_pack_tf32_f32(Xs, ldx, nb, dst);
+}
+
+__device__ void cta_inverse_compute(const float* Ls, int lds, float* Xs, int ldx, int nb) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int nblk = nb / 32;
   if (w < nblk) {  // diagonal blocks
@@ -400,32 +435,15 @@ __device__ void cta_inverse_core(const float* Ls, int lds, float* Xs, int ldx, i
     }
     __syncthreads();
   }
-  // packed operand rows r, k-chunks of 32 (one 128-row block)
-  for (int kc = 0; kc < nb / kUmmaKChunk; ++kc) {
-    uint8_t* hi = dst + pk_chunk_off(0, kc, nb);
-    uint8_t* lo = hi + kUmmaTileBytes;
-    for (int e = t; e < kUmmaM * 16; e += kThreads) {  // pairs (r, 2 kp), rows beyond nb are zero
-      const int r = e >> 4, kp = e & 15;
-      float f0 = 0.f, f1 = 0.f;
-      if (r < nb) {
-        f0 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp];
-        f1 = Xs[r * ldx + kc * kUmmaKChunk + 2 * kp + 1];
-      }
-      const float h0 = tf32_rn(f0), h1 = tf32_rn(f1);
-      const uint32_t off = sw128_offset(r, 2 * kp);
-      *reinterpret_cast<float2*>(hi + off) = make_float2(h0, h1);
-      *reinterpret_cast<float2*>(lo + off) = make_float2(tf32_rn(f0 - h0), tf32_rn(f1 - h1));
-    }
-  }
-  fence_proxy_async_global();
-  __syncthreads();
 }
 
 // The inverse of a factored diagonal tile still held in shared memory as FP64 (sL, leading dimension
 // nb + 1, the layout cta_potrf_smem leaves behind at the start of `smem`): converted to FP32 beside it
 // (smem + nb (nb + 1) 8 bytes, leading dimension nb), then the FP32 workspace takes the FP64 tile's
 // place. Needs nb (nb + 1) 8 + nb nb 4 bytes of shared memory; no global reads.
-__device__ void cta_inverse_pack_smem(uint8_t* smem, int nb, uint8_t* dst) {
+// The same FP32 inverse without the packing: returns the shared-memory FP32 result (leading dimension
+// nb + 1, at the start of `smem`) for the caller to pack in the operand format it needs.
+__device__ float* cta_inverse_f32_smem(uint8_t* smem, int nb) {
   const int t = threadIdx.x, ldl = nb + 1;
   const double* sL = reinterpret_cast<const double*>(smem);
   float* Ls = reinterpret_cast<float*>(smem + (size_t)nb * ldl * 8);
@@ -437,7 +455,13 @@ __device__ void cta_inverse_pack_smem(uint8_t* smem, int nb, uint8_t* dst) {
   __syncthreads();  // the FP64 tile is dead from here: Xs reuses its bytes
   for (int e = t; e < nb * ldl; e += kThreads) Xs[e] = 0.f;
   __syncthreads();
-  cta_inverse_core(Ls, nb, Xs, ldl, nb, dst);
+  cta_inverse_compute(Ls, nb, Xs, ldl, nb);
+  return Xs;
+}
+
+__device__ void cta_inverse_pack_smem(uint8_t* smem, int nb, uint8_t* dst) {
+  const float* Xs = cta_inverse_f32_smem(smem, nb);
+  cta_pack_tf32_f32(Xs, nb + 1, nb, dst);
 }
 
 }  // namespace gpk

@@ -1,0 +1,114 @@
+"""GPU parity of the tensor-core precision forms beyond GP_FP32 against the FP64 oracle, end to end
+(assembly, tiled Cholesky of Sec. 3.2, the mean of Eq. 2 and the covariance of Eq. 3), tile edge 128.
+
+* GP_FP64_OZAKI: every trailing update, panel TRSM and covariance product from seven 8-bit
+  fixed-point digits per value on the BF16 tensor cores, recombined exactly: the FP64 bars
+  (factor 1e-13, mean 1e-10, covariance 1e-9, log-determinant 1e-12), no refinement.
+* GP_BF16X6 (three BF16 slices, six products, FP32-class) and GP_BF16X3 (two slices, three products):
+  the mean refined to the FP64 bar 1e-10; factor, covariance and log-determinant within the bounds
+  stated per form below (max-abs error / max-abs oracle value; factor ||LL^T - K||_F / ||K||_F).
+* GP_TF32 / GP_BF16 (one product): too coarse for this K at these sizes without a shifted factor
+  (kappa ~ 3.4 n): the call either reports GP_ERR_NOT_PD or refines the mean to the bar.
+"""
+import warnings
+
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import nfir
+import oracle
+from oracle import Hyper
+
+pytestmark = pytest.mark.gpu
+
+H0 = Hyper(1.0, 1.0, 0.1)
+
+FORMS = {
+    "fp64_ozaki": {"factor": 1e-13, "mean": 1e-10, "cov": 1e-9, "logdet": 1e-12},
+    "bf16x6": {"factor": 2e-5, "mean": 1e-10, "cov": 2e-4, "logdet": 2e-5},
+    "bf16x3": {"factor": 1e-3, "mean": 1e-10, "cov": 2e-2, "logdet": 1e-3},
+}
+CASES = [(1024, 256, 8, 0), (2000, 300, 8, 1), (4096, 512, 8, 3)]
+
+
+@pytest.fixture(scope="module")
+def api():
+    __graft_entry__.build()
+    from paper_2602_19683_gb300 import api as A
+    return A
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    d = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (d if d > 0 else 1.0))
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to("cuda") for a in arrs]
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("n,m,D,seed", CASES)
+def test_form_matches_oracle(api, form, n, m, D, seed):
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, seed)
+    ref = oracle.gp_predict(X, y, Xs, H0, tile=256)
+    ctx = api.Context(0, precision=form, timeout_s=20)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    mean, iters = api.gp_predict_mean(ctx, f, yd, Xsd, want_iters=True)
+    cov = api.gp_predict_full_cov(ctx, f, Xsd).cpu().numpy()
+    logdet = api.gp_logdet(ctx, f)
+    api.gp_sync(ctx)
+    b = FORMS[form]
+    fe = np.linalg.norm(L @ L.T - ref["K"]) / np.linalg.norm(ref["K"])
+    em, ec = rel(mean.cpu().numpy(), ref["mean"]), rel(cov, ref["cov"])
+    el = abs(logdet - ref["logdet"]) / abs(ref["logdet"])
+    print(f"{form} n={n}: factor {fe:.2e} mean {em:.2e} ({iters} IR iterations) cov {ec:.2e} logdet {el:.2e}")
+    assert np.all(np.triu(L, 1) == 0)
+    assert fe <= b["factor"]
+    assert em <= b["mean"]
+    assert ec <= b["cov"]
+    assert np.array_equal(cov, cov.T)
+    assert el <= b["logdet"]
+    if form == "fp64_ozaki":
+        assert iters == 0
+        assert rel(L, ref["L"]) <= 1e-11
+    else:
+        assert 1 <= iters <= 10
+    f.free()
+
+
+@pytest.mark.parametrize("form", ["tf32", "bf16"])
+def test_single_product_forms_refine_or_report_not_pd(api, form):
+    X, y, Xs, _ = nfir.make_dataset(1024, 128, 8, 4)
+    ref = oracle.gp_predict(X, y, Xs, H0)
+    ctx = api.Context(0, precision=form, timeout_s=20)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    with warnings.catch_warnings(record=True) as caught:
+        warnings.simplefilter("always")
+        try:
+            mean, iters = api.gp_predict_mean(ctx, f, yd, Xsd, want_iters=True)
+            api.gp_sync(ctx)
+        except api.GPError as e:
+            print(f"{form}: {e}")
+            assert e.status == 2  # GP_ERR_NOT_PD
+            return
+    em = rel(mean.cpu().numpy(), ref["mean"])
+    stalled = any("refinement" in str(w.message) for w in caught)
+    print(f"{form}: mean {em:.2e} after {iters} IR iterations{' (reported: did not converge)' if stalled else ''}")
+    if not stalled:
+        assert em <= 1e-10
+
+
+def test_forms_reject_other_tiles(api):
+    with pytest.raises(api.GPError):
+        api.Context(0, precision="fp64_ozaki", tile=256)
+    with pytest.raises(api.GPError):
+        api.Context(0, precision="bf16x3", tensor_cores=False)
