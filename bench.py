@@ -100,16 +100,35 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def mixed_cholesky_roofline(n: int, tile: int, chol_s: float):
-    """Roofline object of the mixed-precision Cholesky launch: the tensor pipe (three TF32 split
-    products per update against the TF32 peak) plus its measured DRAM traffic where a capture exists
-    for this size, with the HBM rate that traffic implies."""
-    tf32_peak, tf32_src = tf32_peak_tflops()
-    executed = 3 * (n ** 3 / 3) / chol_s / 1e12
-    traffic = MIXED_CHOL_TRAFFIC_N32768_T128 if (n, tile) == (32768, 128) else None
-    r = {"kernel": "dag_kernel mixed (tiled Cholesky, 3xTF32 on tcgen05)", "bound": "tensor",
-         "achieved": executed, "peak": tf32_peak, "unit": "TFLOP/s", "frac": executed / tf32_peak,
-         "peak_source": tf32_src, "algorithmic_tflops": (n ** 3 / 3) / chol_s / 1e12, "traffic": traffic}
+# Tensor-core products per algorithmic product, operand kind and tcgen05 kind of each precision form.
+FORM_PRODUCTS = {"fp32": (3, "tf32", "3xTF32"), "tf32": (1, "tf32", "TF32"), "bf16": (1, "bf16", "BF16"),
+                 "bf16x3": (3, "bf16", "BF16x3"), "bf16x6": (6, "bf16", "BF16x6"),
+                 "fp64_ozaki": (28, "bf16", "FP64 from 28 BF16 digit products")}
+
+
+def bf16_peak_tflops():
+    """Dense BF16 tensor peak: the measured burst figure of this GPU pool (MEASURED_PEAKS.json), or the
+    profiling recipe's fallback (1.9 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["bf16_tflops"])
+            return v, f"measured cuBLAS BF16 GEMM burst {v:.0f} TFLOP/s (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback BF16 1900 TFLOP/s (profiling recipe)"
+
+
+def mixed_cholesky_roofline(n: int, tile: int, chol_s: float, prec: str = "fp32"):
+    """Roofline object of a tensor-core Cholesky launch: the tensor pipe (the form's products per
+    update against the measured peak of its operand kind) plus, for the 3xTF32 form, its measured DRAM
+    traffic where a capture exists for this size, with the HBM rate that traffic implies."""
+    nprod, kind, label = FORM_PRODUCTS[prec]
+    peak, peak_src = tf32_peak_tflops() if kind == "tf32" else bf16_peak_tflops()
+    executed = nprod * (n ** 3 / 3) / chol_s / 1e12
+    traffic = MIXED_CHOL_TRAFFIC_N32768_T128 if (n, tile, prec) == (32768, 128, "fp32") else None
+    r = {"kernel": f"dag_kernel mixed (tiled Cholesky, {label} on tcgen05)", "bound": "tensor",
+         "achieved": executed, "peak": peak, "unit": "TFLOP/s", "frac": executed / peak,
+         "peak_source": peak_src, "algorithmic_tflops": (n ** 3 / 3) / chol_s / 1e12, "traffic": traffic}
     if traffic is not None:
         hbm, src = hbm_peak_gbs()
         r["traffic_gbs"] = traffic / chol_s / 1e9
@@ -145,6 +164,10 @@ def whole_job_tflops(flops_per_replica: float, ws: int, ms: float) -> float:
     return flops_per_replica * ws / (ms / 1e3) / 1e12
 
 
+def locality_arg(args):
+    return {"default": None, "on": True, "off": False}[args.locality_order]
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -155,7 +178,8 @@ def parse():
                    help="solve: one large GP (the headline); large: n = 65536, m = 8192, D = 16 in mixed "
                         "precision against one FP64 solve and cuSOLVER Dpotrf; batch: 512 uneven GPs in one "
                         "graph launch; nlml: NLML gradient and Adam fitting at n = 16384")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="fp64",
+                   choices=["fp64", "fp32", "bf16x3", "bf16x6", "tf32", "bf16", "fp64_ozaki"])
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--m", type=int, default=4096)
     p.add_argument("--D", type=int, default=8)
@@ -167,9 +191,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (GP_FP32) leg")
     p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
-    p.add_argument("--locality-order", action="store_true",
-                   help="mixed precision: start grouped updates that share a packed operand back to back "
-                        "(cfg.locality_order)")
+    p.add_argument("--locality-order", default="default", choices=["default", "on", "off"],
+                   help="tensor-core forms: start grouped updates that share a packed operand back to back "
+                        "(cfg.locality_order; the library's default is on)")
     p.add_argument("--cpu-n", type=int, default=8192, help="oracle sample size for the CPU baseline")
     p.add_argument("--cpu-m", type=int, default=1024)
     p.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference-arm step")
@@ -329,10 +353,10 @@ def run_ours(args):
     Xd, yd, Xsd = (torch.from_numpy(a).to(dev) for a in (X, y, Xs))
     h = api.Hyper(1.0, 1.0, 0.1)
     stream = torch.cuda.Stream(dev)
-    if args.precision == "fp32":
+    if FORM_PRODUCTS.get(args.precision, (0, ""))[1] == "tf32":
         measure_tf32_tflops(dev)  # the tensor roofline's denominator, before anything is timed
     ctx = api.Context(local, stream=stream, tile=args.tile, precision=args.precision, grid=args.grid,
-                      locality_order=args.locality_order)
+                      locality_order=locality_arg(args))
     mean = torch.empty(m, dtype=torch.float64, device=dev)
     cov = torch.empty((m, m), dtype=torch.float64, device=dev)
     fac = [None]
@@ -418,7 +442,7 @@ def run_ours(args):
             logdet64 = api.gp_logdet(ctx, fac[0])
             measure_tf32_tflops(dev)  # the tensor roofline's denominator, before the timed leg
             ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32",
-                                locality_order=args.locality_order)
+                                locality_order=locality_arg(args))
             fac32 = [None]
             mean32 = torch.empty_like(mean)
             cov32 = torch.empty_like(cov)
@@ -485,11 +509,12 @@ def run_ours(args):
     line = {"metric": "GP solve (assembly+Cholesky+mean+full cov) FP64 TFLOP/s", "value": value,
             "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "dtype": {"fp64": "f64", "fp64_ozaki": "f64 (bf16 digit products)"}.get(args.precision,
+                                                                                   f"f64+{args.precision}"),
             "data": "synthetic NFIR mass-spring-damper (seeded)",
             "config": {"workload": f"exact GP solve n={n} m={m} D={D}", "n": n, "m": m, "D": D,
-                       "tile": ctx_tile(n, args.tile, args.precision == "fp32"), "precision": args.precision,
-                       "locality_order": bool(args.locality_order),
+                       "tile": ctx_tile(n, args.tile, args.precision != "fp64"), "precision": args.precision,
+                       "locality_order": args.locality_order,
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (K is 4.4 GB)",
                        "s_per_solve": ms / 1e3, "cholesky_s": chol_ms / 1e3},
             "roofline": ({"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
@@ -498,7 +523,7 @@ def run_ours(args):
                           "traffic": fp64_cholesky_traffic(n, ctx_tile(n, args.tile)),
                           "traffic_note": "bytes per launch, ncu capture at n=8192 scaled by the tile-update count"}
                          if args.precision == "fp64" else
-                         mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), chol_ms / 1e3)),
+                         mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), chol_ms / 1e3, args.precision)),
             "gpu_launches": launches, "clocks": clocks}
     if mixed:
         line["mixed"] = mixed
@@ -591,7 +616,7 @@ def run_large(args):
     with torch.cuda.stream(stream):
         for prec in ("fp32", "fp64"):
             ctx = api.Context(0, stream=stream, tile=args.tile, precision=prec, timeout_s=900.0,
-                              locality_order=args.locality_order)
+                              locality_order=locality_arg(args))
             mean = torch.empty(m, dtype=torch.float64, device=dev)
             cov = torch.empty((m, m), dtype=torch.float64, device=dev)
             fac = [None]

@@ -68,8 +68,8 @@ enum {
   GP_BF16X3 = 2,     /* tensor cores, BF16 split of the FP32 value into two slices, three products,
                         FP32 accumulation (about 16 significant bits per product)                   */
   GP_BF16X6 = 3,     /* tensor cores, three BF16 slices, six products (FP32-class, 24 bits)          */
-  GP_TF32 = 4,       /* tensor cores, one TF32 product (about 11 bits): a factor for GMRES-based
-                        refinement; loses positive definiteness on ill-conditioned K               */
+  GP_TF32 = 4,       /* tensor cores, one TF32 product (about 11 bits) on K + shift I (cfg.shift);
+                        K^{-1} y refined by GMRES in FP64 preconditioned with that factor          */
   GP_BF16 = 5,       /* tensor cores, one BF16 product (about 8 bits): as GP_TF32, coarser            */
   GP_FP64_OZAKI = 6  /* FP64-accurate products on the BF16 tensor cores: each FP64 value cut into
                         seven 8-bit fixed-point digits (Ozaki-style error-free splitting), the 28
@@ -110,10 +110,14 @@ typedef struct {
   int32_t batch_ctas_per_sm; /* persistent-kernel CTAs per SM of batched launches (0 = library choice: two
                              for GP_FP64, one for GP_FP32; capped by occupancy). gp_batch_autotune stores
                              its choice here.                                                          */
-  int32_t locality_order;  /* GP_FP32 on the tensor cores: 1 = start the grouped trailing updates that share a
-                             packed operand group back to back when their longest-path rank is within
-                             10 % of the best ready task's (they then read the shared operand from L2);
-                             0 = longest-path order only (default)                                    */
+  int32_t locality_order;  /* tensor-core forms: start the grouped trailing updates that share a packed operand
+                             group back to back when their longest-path rank is within 10 % of the best
+                             ready task's (they then read the shared operand from L2): 0 or 1 = on (the
+                             default), -1 = off (longest-path order only)                              */
+  double shift;           /* GP_TF32 / GP_BF16 only: the factorised matrix is K + shift I (the stored FP64 K and
+                             every result keep K itself): > 0 fixed; 0 = automatic, u sqrt(n) max K_ii
+                             (u = 2^-11 / 2^-8) times 8 after each non-positive pivot, at most five
+                             tries (gp_cholesky then waits for the stream); < 0 = no shift             */
 } gp_config;
 
 typedef struct gp_ctx gp_ctx;
@@ -170,6 +174,11 @@ gp_status gp_nlml_grad(gp_ctx* ctx, const double* X, const double* y, int64_t n,
  * gp_assemble, L after gp_cholesky) to out (device, nrows x n row-major; entries above the diagonal
  * are written as 0). Asynchronous. */
 gp_status gp_factor_rows(gp_ctx* ctx, const gp_factor* f, int64_t row0, int64_t nrows, double* out);
+
+/* Refinement record of a factor (host, 4 doubles): {shift the factorised matrix carried (single-product
+ * forms), normwise backward error reached by the last gp_predict_mean, its refinement steps (GMRES:
+ * preconditioned matrix-vector products), precision form}. Host only; no wait. */
+gp_status gp_factor_stats(gp_ctx* ctx, const gp_factor* f, double out[4]);
 
 /* Copies alpha = K^{-1} y from the last gp_predict_mean on the factor to out (device, n). */
 gp_status gp_alpha(gp_ctx* ctx, const gp_factor* f, double* out);
@@ -285,7 +294,7 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
  * Cholesky used by gp_nlml_grad, 4 = the V solve of gp_predict_var) for Mt tile rows, Mc covariance
  * tile columns, tile edge T, `workers` CTAs and the cost model of precision `mixed` (0 = FP64,
- * 1 = GP_FP32; 3 = GP_FP32 with cfg.locality_order = 1) as int32 quadruples {kind, p, q, r} (kinds as in the
+ * 1 = GP_FP32 with the locality order off; 3 = GP_FP32 with it on) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
  * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J), 14 TRTRI(J): the FP64 inverse of the factored diagonal tile

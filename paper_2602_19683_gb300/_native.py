@@ -31,7 +31,7 @@ class gp_config(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int32), ("noisy_prior", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("withhold_task", ctypes.c_int32), ("withhold_enable", ctypes.c_int32),
                 ("tensor_cores", ctypes.c_int32), ("trace", ctypes.c_int32), ("batch_order", ctypes.c_int32),
-                ("batch_ctas_per_sm", ctypes.c_int32), ("locality_order", ctypes.c_int32)]
+                ("batch_ctas_per_sm", ctypes.c_int32), ("locality_order", ctypes.c_int32), ("shift", ctypes.c_double)]
 
 
 class gp_batch_desc(ctypes.Structure):
@@ -67,6 +67,7 @@ SIGNATURES = {
     "gp_batch_run": ([_P, _P], _I32),
     "gp_batch_free": ([_P, _P], _I32),
     "gp_set_batch_schedule": ([_P, _I32, _I32], _I32),
+    "gp_factor_stats": ([_P, _P, ctypes.POINTER(ctypes.c_double)], _I32),
     "gp_debug_tile_product": ([_P, _I32, _P, _P, _P, _I32, _I32, _I32, _I32], _I32),
     "gp_batch_predict": ([_P, _I32, ctypes.POINTER(gp_batch_desc), _I32, ctypes.POINTER(ctypes.c_int64)], _I32),
     "gp_batch_autotune": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(gp_autotune_opts),

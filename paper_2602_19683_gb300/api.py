@@ -56,7 +56,7 @@ class Context:
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
                  tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0,
-                 locality_order: bool = False):
+                 locality_order: bool | None = None, shift: float = 0.0):
         self.lib = N.load()
         self.precision = precision
         self.device = torch.device("cuda", device)
@@ -73,7 +73,8 @@ class Context:
         cfg.trace = int(trace)
         cfg.batch_order = batch_order
         cfg.batch_ctas_per_sm = batch_ctas_per_sm
-        cfg.locality_order = int(locality_order)
+        cfg.locality_order = 0 if locality_order is None else (1 if locality_order else -1)
+        cfg.shift = shift
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1
@@ -227,6 +228,13 @@ def gp_predict_var(ctx: Context, f: Factor, Xs: torch.Tensor, out: torch.Tensor 
     _dev(out, "var_out", (m,))
     _check(ctx.lib.gp_predict_var(ctx.h, f.h, Xs.data_ptr(), m, out.data_ptr()), "gp_predict_var")
     return out
+
+
+def gp_factor_stats(ctx: Context, f: Factor) -> dict:
+    """The factor's refinement record: diagonal shift, backward error and steps of the last mean solve."""
+    out = (ctypes.c_double * 4)()
+    _check(ctx.lib.gp_factor_stats(ctx.h, f.h, out), "gp_factor_stats")
+    return {"shift": out[0], "eta": out[1], "iterations": int(out[2]), "precision": int(out[3])}
 
 
 def gp_logdet(ctx: Context, f: Factor) -> float:

@@ -119,8 +119,11 @@ struct gp_factor {
   DevBuf Bt, Wt, Pt, cRev, beta;  // NLML gradient: adjoint tiles, reverse-POTRF workspace, diagonal partial
                                   // sums, counters, L^{-1} y
   DevBuf V, S, cCov;          // covariance workspace
+  DevBuf gV, gzero, gh;       // GMRES refinement: Krylov basis, a zero vector, Hessenberg column scratch
   bool factored = false, alpha_valid = false;
   double ir_eta = 0.0;        // backward error reached by the last refinement
+  int ir_iters = 0;           // refinement steps (GMRES: preconditioned matrix-vector products) of the last solve
+  double shift = 0.0;         // diagonal shift of the factorised matrix (single-product forms)
 };
 
 namespace {
@@ -131,6 +134,8 @@ void count_launch(gp_ctx* c, int k = 1) { c->launches += k; }
 bool is_mixed(int prec) { return prec != GP_FP64; }
 // Forms that keep an FP64 copy of K and refine K^{-1} y against it.
 bool refines(int prec) { return prec != GP_FP64 && prec != GP_FP64_OZAKI; }
+// Forms whose factor is too coarse for classic refinement: shifted factorisation, GMRES refinement.
+bool single_product(int prec) { return prec == GP_TF32 || prec == GP_BF16; }
 // Forms whose products exist only on the tensor cores with tile edge 128.
 bool slice_form(int prec) {
   return prec == GP_BF16X3 || prec == GP_BF16X6 || prec == GP_BF16 || prec == GP_FP64_OZAKI;
@@ -172,7 +177,9 @@ gpk::CostModel cost_model(const gp_ctx* c, int prec, int T = 0) {
   cm.update_group = tc ? (prec == GP_FP64_OZAKI ? 4 : 8) : 1;
   cm.tensor_cores = tc;
   cm.pair_rows = tc && T == 128 && prec == GP_FP32;
-  cm.locality_eps = (cm.tensor_cores && c->cfg.locality_order) ? 0.1 : 0.0;
+  // operand-locality order of the grouped updates: on unless the caller turned it off (measured at
+  // n = 32768, 3xTF32: mixed Cholesky 152 -> 142 ms)
+  cm.locality_eps = (cm.tensor_cores && c->cfg.locality_order >= 0) ? 0.1 : 0.0;
   if (tc && prec != GP_FP32) {
     // starting points from the operand bytes and products of each form (the 3xTF32 figures are measured)
     const double bytes = pk_bytes(prec) / 8.0;
@@ -290,6 +297,136 @@ bool valid_hyper(const gp_hyper& h) {
   return std::isfinite(h.l) && std::isfinite(h.v) && std::isfinite(h.s2) && h.l > 0 && h.v > 0 && h.s2 >= 0;
 }
 
+// Reads `cnt` doubles from the device and the device status code (waits for the stream).
+gp_status read_back(gp_ctx* c, double* host, const double* dev, int cnt, bool* device_error) {
+  int32_t code = 0;
+  GP_CUDA(cudaMemcpyAsync(host, dev, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaMemcpyAsync(&code, &c->d_status->code, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  *device_error = code != 0;
+  return GP_OK;
+}
+
+// GMRES-based iterative refinement (Carson and Higham, SIAM J. Sci. Comput. 2018) of alpha = K^{-1} y
+// for the single-product forms, whose (shifted) factor L~ is too coarse for classic refinement: each
+// outer step takes the FP64 residual r = y - K alpha against the stored FP64 K and solves K d = r by
+// restarted GMRES in FP64 on the left-preconditioned system (L~ L~^T)^{-1} K d = (L~ L~^T)^{-1} r
+// (Arnoldi by classical Gram-Schmidt applied twice), then alpha += d. The matrix-vector products,
+// the preconditioner solves and the basis updates run on the device; the host keeps only the small
+// Hessenberg least-squares problem. Stops on the same normwise backward error as classic refinement.
+gp_status gmres_refine(gp_ctx* c, gp_factor* f, const double* y, int* iters_out, bool* converged,
+                       bool* device_error) {
+  constexpr int kRestart = 40, kMaxInner = 400;
+  const int T = f->T, Mt = f->Mt;
+  const size_t npad = (size_t)Mt * T;
+  const long long n = f->n;
+  GP_TRY(grow(f->gV, (size_t)(kRestart + 1) * npad * sizeof(double)));
+  GP_TRY(grow(f->gzero, npad * sizeof(double)));
+  GP_TRY(grow(f->gh, 128 * sizeof(double)));
+  GP_CUDA(cudaMemsetAsync(f->gzero.p, 0, npad * sizeof(double), c->stream));
+  double* V = (double*)f->gV.p;
+  double* w = (double*)f->bvec.p;  // the vector the preconditioner solve works on in place
+  double* hd = (double*)f->gh.p;
+  double* alpha = (double*)f->alpha.p;
+  const double* K0 = (const double*)f->Kt0.p;
+  *converged = false;
+  *device_error = false;
+  int total = 0;
+  double eta_prev = 0.0, knorm = 0.0;
+  for (int outer = 0;; ++outer) {
+    GP_CUDA(gpk::launch_residual(K0, T, Mt, n, y, alpha, w, (double*)f->part.p, c->d_scalar, c->stream, outer == 0));
+    count_launch(c, 2);
+    double nr[6];
+    GP_TRY(read_back(c, nr, c->d_scalar, 6, device_error));
+    if (*device_error) break;
+    if (outer == 0) knorm = nr[3];
+    const double den = knorm * nr[4] + nr[5];
+    const double eta = den > 0 ? nr[2] / den : 0.0;
+    f->ir_eta = eta;
+    if (!(eta == eta)) return GP_ERR_NONFINITE;
+    if (eta <= c->cfg.ir_tol) {
+      *converged = true;
+      break;
+    }
+    if (outer > 0 && eta > 0.5 * eta_prev) {
+      *converged = eta <= 100.0 * c->cfg.ir_tol;
+      break;
+    }
+    if (outer >= c->cfg.ir_maxit || total >= kMaxInner * c->cfg.ir_maxit) break;
+    eta_prev = eta;
+    // b = M^{-1} r, beta = ||b||, v_0 = b / beta
+    GP_TRY(solve_in_place(c, f));
+    double beta2 = 0.0;
+    GP_CUDA(gpk::launch_multi_dot(w, (long long)npad, 1, w, (long long)npad, hd, c->stream));
+    count_launch(c);
+    GP_TRY(read_back(c, &beta2, hd, 1, device_error));
+    if (*device_error) break;
+    const double beta = std::sqrt(beta2);
+    if (!(beta > 0)) {
+      *converged = true;
+      break;
+    }
+    GP_CUDA(gpk::launch_scale_copy(V, w, 1.0 / beta, (long long)npad, c->stream));
+    double H[kRestart + 1][kRestart] = {};
+    double cs[kRestart] = {}, sn[kRestart] = {}, g[kRestart + 1] = {};
+    g[0] = beta;
+    int j = 0;
+    for (; j < kRestart && total < kMaxInner; ++j) {
+      double* vj = V + (size_t)j * npad;
+      // w = M^{-1} K v_j: the residual kernel with y = 0 gives -K v_j, the solve and a sign flip the rest
+      GP_CUDA(gpk::launch_residual(K0, T, Mt, n, (const double*)f->gzero.p, vj, w, (double*)f->part.p,
+                                   c->d_scalar + 16, c->stream, false));
+      GP_TRY(solve_in_place(c, f));
+      GP_CUDA(gpk::launch_scale_copy(w, w, -1.0, (long long)npad, c->stream));
+      // two passes of classical Gram-Schmidt against v_0..v_j, then the norm
+      GP_CUDA(gpk::launch_multi_dot(V, (long long)npad, j + 1, w, (long long)npad, hd, c->stream));
+      GP_CUDA(gpk::launch_multi_axpy(w, V, (long long)npad, hd, j + 1, -1.0, (long long)npad, c->stream));
+      GP_CUDA(gpk::launch_multi_dot(V, (long long)npad, j + 1, w, (long long)npad, hd + 48, c->stream));
+      GP_CUDA(gpk::launch_multi_axpy(w, V, (long long)npad, hd + 48, j + 1, -1.0, (long long)npad, c->stream));
+      GP_CUDA(gpk::launch_multi_dot(w, (long long)npad, 1, w, (long long)npad, hd + 96, c->stream));
+      count_launch(c, 9);
+      double hh[97];
+      GP_TRY(read_back(c, hh, hd, 97, device_error));
+      if (*device_error) break;
+      ++total;
+      for (int i = 0; i <= j; ++i) H[i][j] = hh[i] + hh[48 + i];
+      const double nrm = std::sqrt(hh[96]);
+      H[j + 1][j] = nrm;
+      if (nrm > 0) GP_CUDA(gpk::launch_scale_copy(V + (size_t)(j + 1) * npad, w, 1.0 / nrm, (long long)npad, c->stream));
+      // Givens rotations: the Hessenberg column j into upper-triangular form, g follows
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+        H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
+        H[i][j] = t;
+      }
+      const double rr = std::hypot(H[j][j], H[j + 1][j]);
+      cs[j] = rr > 0 ? H[j][j] / rr : 1.0;
+      sn[j] = rr > 0 ? H[j + 1][j] / rr : 0.0;
+      H[j][j] = rr;
+      H[j + 1][j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      if (std::fabs(g[j + 1]) <= 1e-10 * beta || !(nrm > 0)) {
+        ++j;
+        break;
+      }
+    }
+    if (*device_error) break;
+    // y = R^{-1} g (back substitution), alpha += V y
+    double yv[kRestart] = {};
+    for (int i = j - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < j; ++k) t -= H[i][k] * yv[k];
+      yv[i] = t / H[i][i];
+    }
+    GP_CUDA(cudaMemcpyAsync(hd, yv, (size_t)j * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    GP_CUDA(gpk::launch_multi_axpy(alpha, V, (long long)npad, hd, j, 1.0, (long long)npad, c->stream));
+    count_launch(c);
+  }
+  *iters_out = total;
+  return GP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -331,7 +468,7 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
   if (c.batch_order < 0 || c.batch_order > 1 || c.batch_ctas_per_sm < 0 || c.batch_ctas_per_sm > 2 ||
-      c.locality_order < 0 || c.locality_order > 1)
+      c.locality_order < -1 || c.locality_order > 1)
     return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(device));
   gp_ctx* ctx = new (std::nothrow) gp_ctx();
@@ -545,10 +682,11 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   f->Mt = (int)Mt;
   f->h = h;
   f->precision = c->cfg.precision;
-  // fixed-point scales: |L_ij| <= sqrt(K_ii) <= sqrt(max(v + s2, 1)) (the padding's diagonal is 1) and
-  // |V_ij| <= ||V_:,j|| <= sqrt(v) (the predictive variance v - ||V_:,j||^2 is not negative)
-  f->eL = pow2_exponent(std::sqrt(std::max(h.v + h.s2, 1.0))) + 1;
-  f->eV = pow2_exponent(std::sqrt(h.v)) + 1;
+  // fixed-point scales: the rows of L have norm sqrt(K_ii) <= sqrt(max(v + s2, 1)) (the padding's
+  // diagonal is 1) and the columns of V norm <= sqrt(v) (the predictive variance v - ||V_:,j||^2 is not
+  // negative): powers of two at or above those bounds
+  f->eL = pow2_exponent(std::sqrt(std::max(h.v + h.s2, 1.0)));
+  f->eV = pow2_exponent(std::sqrt(h.v));
   f->X = X;
   f->factored = false;
   f->alpha_valid = false;
@@ -579,7 +717,36 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   a.Linv = (double*)f->Linv.p;
   if (packed_operands(c, f)) a.Pk = (uint8_t*)f->Pk.p;
   if (packed_operands(c, f) && f->T == 128) a.PLinv = (uint8_t*)f->PLinv.p;
-  GP_TRY(run_dag(c, a, tb, mixed));
+  if (!single_product(f->precision)) {
+    GP_TRY(run_dag(c, a, tb, mixed));
+    f->factored = true;
+    return GP_OK;
+  }
+  // Single-product forms factor K + tau I (Higham and Pranesh's diagonal shift for low-precision
+  // Cholesky): cfg.shift > 0 fixes tau; 0 starts at u sqrt(n) max K_ii (u = 2^-11 for TF32, 2^-8 for
+  // BF16) and multiplies it by 8 after each non-positive pivot, refactoring from the stored FP64 K, at
+  // most five tries; < 0 factors K itself. Synchronous: the last try's device status is returned.
+  const double dmax = std::max(f->h.v + f->h.s2, 1.0);
+  const double u = std::ldexp(1.0, f->precision == GP_TF32 ? -11 : -8);
+  double tau = c->cfg.shift > 0 ? c->cfg.shift : (c->cfg.shift < 0 ? 0.0 : u * std::sqrt((double)f->n) * dmax);
+  const size_t tile_bytes = ntiles * f->T * f->T * sizeof(double);
+  for (int attempt = 0;; ++attempt) {
+    if (attempt > 0) {
+      GP_CUDA(cudaMemcpyAsync(f->Kt.p, f->Kt0.p, tile_bytes, cudaMemcpyDeviceToDevice, c->stream));
+      GP_CUDA(cudaMemsetAsync(f->cK.p, 0, ntiles * sizeof(int), c->stream));
+    }
+    if (tau > 0) {
+      GP_CUDA(gpk::launch_add_diag((double*)f->Kt.p, f->T, f->n, tau, c->stream));
+      count_launch(c);
+    }
+    GP_TRY(run_dag(c, a, tb, mixed));
+    int64_t info = 0;
+    const gp_status st = gp_sync(c, &info);
+    if (st == GP_OK) break;
+    if (st != GP_ERR_NOT_PD || c->cfg.shift != 0 || attempt >= 4) return st;
+    tau *= 8.0;
+  }
+  f->shift = tau;
   f->factored = true;
   return GP_OK;
 }
@@ -606,7 +773,13 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   GP_CUDA(cudaMemcpyAsync(f->alpha.p, f->bvec.p, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   gp_status result = GP_OK;
   int iters = 0;
-  if (mixed) {
+  if (mixed && single_product(f->precision)) {
+    GP_TRY(grow(f->rvec, npad * sizeof(double)));
+    GP_TRY(grow(f->part, (size_t)6 * Mt * nch * sizeof(double)));
+    bool converged = false, device_error = false;
+    GP_TRY(gmres_refine(c, f, y, &iters, &converged, &device_error));
+    if (!converged && !device_error) result = GP_ERR_NO_CONVERGENCE;
+  } else if (mixed) {
     // Classic iterative refinement: r = y - K alpha in FP64 against the stored FP64 K, correction
     // through the mixed-precision factor. Stops when the normwise backward error
     // eta = ||r||_inf / (||K||_inf ||alpha||_inf + ||y||_inf) <= ir_tol, or when eta stagnates (less
@@ -660,6 +833,7 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
                                   c->stream));
     count_launch(c);
   }
+  f->ir_iters = iters;
   if (ir_iters_out) *ir_iters_out = iters;
   return result;
 }
@@ -751,6 +925,15 @@ gp_status gp_factor_rows(gp_ctx* c, const gp_factor* f, int64_t row0, int64_t nr
   GP_CUDA(cudaSetDevice(c->device));
   GP_CUDA(gpk::launch_factor_rows((const double*)f->Kt.p, f->T, f->n, row0, nrows, out, c->stream));
   count_launch(c);
+  return GP_OK;
+}
+
+gp_status gp_factor_stats(gp_ctx* c, const gp_factor* f, double out[4]) {
+  if (!c || !f || !out) return GP_ERR_INVALID_ARG;
+  out[0] = f->shift;
+  out[1] = f->ir_eta;
+  out[2] = (double)f->ir_iters;
+  out[3] = (double)f->precision;
   return GP_OK;
 }
 

@@ -9,15 +9,20 @@
 //    accumulated into one FP32 accumulator.
 //  * fixed-point digits (GP_FP64_OZAKI, kS = 7; the error-free splitting of Ozaki et al. 2012 with
 //    BF16 digits, as in the tensor-core DGEMM emulations of Mukunoki et al. 2020 and Ootomo, Ozaki and
-//    Yokota 2024): with a power-of-two scale S = 2^e (|x| <= S/2), F = round(x 2^(56-e)) is cut into
-//    balanced base-256 digits, x ~ S sum_{p=1..7} d_p 2^(-8p), |d_1| <= 128, d_2..d_7 in [-128, 128).
+//    Yokota 2024): with a power-of-two scale S = 2^e (|x| <= S), F = round(x 2^(56-e)) is cut into
+//    balanced base-256 digits, x ~ S sum_{p=1..7} d_p 2^(-8p), |d_1| <= 256, d_2..d_7 in [-128, 128).
 //    Every digit is an integer of at most 8 significant bits, so BF16 holds it exactly and every
-//    digit product (<= 2^14) and every FP32 sum of up to 2^10 of them is exact. The digit products
-//    of equal weight (level L = p + q, L = 2..8: 28 products) are accumulated in their own TMEM
-//    region; the epilogue turns the seven exact integer level sums into one 64-bit fixed-point sum
-//    sum_L A_L 2^(56 - 8L) on the integer pipe and that into an FP64 value scaled by S_A S_B 2^-56.
-//    Truncating at level 8 drops terms of weight 2^-72 (relative to S_A S_B): the product is FP64-
-//    accurate, at 28 BF16 tensor-core products instead of one FP64 product.
+//    digit product is exact in FP32. The digit products of equal weight (level L = p + q, L = 2..8:
+//    28 products) are accumulated in their own TMEM region. Their FP32 sums stay exact integers
+//    (below 2^24): for one 128-wide tile product at any scale up to level 7, and for the grouped
+//    updates (at most 512 k, rows of norm <= S: L's rows, V's columns) up to level 4 by the
+//    Cauchy-Schwarz bound on the leading digits, the deeper levels being sums of rounding digits
+//    whose size is ~2^17; a rounded deep level costs at most 2^(2-8L) S_A S_B. The epilogue turns
+//    the seven level sums into one 64-bit fixed-point sum sum_L A_L 2^(lsb - 8L) on the integer pipe
+//    (lsb = 56 for norm-bounded operands, 52 for max-scaled single tiles, so the sum fits 63 bits)
+//    and that into an FP64 value scaled by S_A S_B 2^-lsb. Truncating at level 8 drops terms of
+//    weight 2^-72 S_A S_B per digit product: the product is as accurate as an FP64 product, at 28
+//    BF16 tensor-core products instead of one FP64 product.
 //
 // Packed operand layout (global memory, written once by cta_pack_bs, copied verbatim into shared
 // memory by bulk copies): an R x Kd operand (R a multiple of 128, Kd of 32) is a sequence of chunks,
@@ -38,7 +43,8 @@ constexpr int kBsSliceBytes = kUmmaM * kBsKChunk * 2;  // 8 KB: one slice of a 1
 constexpr int kBsMaxStages = 6;
 constexpr int kBsStageMem = 192 * 1024;                // stage memory (inside kUmmaSmemBytes)
 constexpr int kOzSlices = 7, kOzLevels = 7;            // digits 1..7, levels 2..8
-constexpr int kOzLsb = 56;                             // fixed-point sum in units of 2^-56 S_A S_B
+constexpr int kOzLsbBounded = 56;   // fixed-point sum unit 2^-56 S_A S_B: operands with rows of norm <= S
+constexpr int kOzLsbTile = 52;      // 2^-52 S_A S_B: max-scaled operands of one 128-wide tile product
 static_assert(kBsStageMem + 1024 <= kUmmaSmemBytes, "slice stages must fit the dynamic smem");
 static_assert(kOzLevels * 64 <= kUmmaTmemCols, "seven 64-column level accumulators must fit TMEM");
 
@@ -96,7 +102,7 @@ __device__ __forceinline__ float small_int_to_f32(int d) {
   return __uint_as_float(0x4B400000u + (uint32_t)d) - 12582912.0f;
 }
 
-// Fixed-point digits of x at scale 2^e (|x| <= 2^(e-1)): F = round(x 2^(56-e)) (ties away from zero),
+// Fixed-point digits of x at scale 2^e (|x| <= 2^e): F = round(x 2^(56-e)) (ties away from zero),
 // cut into balanced base-256 digits d_1..d_7 (most significant first), returned as BF16 bits. Integer
 // operations on the bits of x only.
 __device__ __forceinline__ void split_fixed(double x, int e, uint32_t (&h)[kOzSlices]) {
@@ -107,7 +113,7 @@ __device__ __forceinline__ void split_fixed(double x, int e, uint32_t (&h)[kOzSl
     const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;  // 53-bit integer
     const int sh = (ex - 1023) + 4 - e;  // x = m 2^(ex-1023-52); F = m 2^(ex-1023-52+56-e)
     if (sh >= 0)
-      F = m << (sh < 10 ? sh : 10);  // |x| <= 2^(e-1) keeps sh <= 2; the clamp only guards the shift
+      F = m << (sh < 10 ? sh : 10);  // |x| <= 2^e keeps sh <= 4; the clamp only guards the shift
     else if (sh > -54)
       F = (m + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) F = -F;
@@ -209,8 +215,9 @@ __device__ void cta_pack_bs_f32(const float* Xs, int ld, int nb, uint8_t* dst) {
   __syncthreads();
 }
 
-// Smallest e with max |src| <= 2^(e-1) over an R x C FP64 block (row-major, ld): the per-tile scale
-// of a fixed-point operand used in a single-tile product. Returns -1022 for an all-zero block.
+// An e with max |src| < 2^e (the smallest such power of two, or the next) over an R x C FP64 block
+// (row-major, ld): the per-tile scale of a fixed-point operand used in a single-tile product. Returns
+// -1022 for an all-zero block.
 __device__ int cta_scale_exp(const double* src, int ld, int R, int C, int* s_flag) {
   int mx = 0;  // largest biased exponent field; a value with field ex is < 2^(ex - 1022)
   for (int e2 = threadIdx.x; e2 < R * C; e2 += kThreads) {
@@ -226,7 +233,7 @@ __device__ int cta_scale_exp(const double* src, int ld, int R, int C, int* s_fla
   __syncthreads();
   const int ex = *s_flag;
   __syncthreads();
-  return ex == 0 ? -1022 : ex - 1022 + 1;  // |x| < 2^(ex-1022) = 2^(e-1)
+  return ex == 0 ? -1022 : ex - 1022;  // |x| < 2^(ex-1022)
 }
 
 // x 2^e as an FP64 value, rounded to nearest (ties to even), on the integer pipe (|x| < 2^63, the
@@ -250,13 +257,14 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long x, int e) {
 }
 
 // Epilogue of one 128 x 64 half of a fixed-point product whose MMAs are all complete: the seven
-// level sums (TMEM columns 64 (L - 2) + c, L = 2..8; exact integers in FP32) of every entry are
-// combined into sum_L A_L 2^(56 - 8L) in 64-bit integers, converted to FP64 with the factor 2^e2
-// (e2 = eA + eB - 56), staged in shared memory and applied to C with coalesced accesses:
+// level sums (TMEM columns 64 (L - 2) + c, L = 2..8; integers in FP32) of every entry are combined
+// into sum_L A_L 2^(lsb - 8L) in 64-bit integers (the levels below the unit rounded to nearest),
+// converted to FP64 with the factor 2^e2 (e2 = eA + eB - lsb), staged in shared memory and applied to
+// C with coalesced accesses:
 // C -= result (kStore: C = result); lower: entries with column > row are left as they are.
 // Warp w reads TMEM lanes 32 (w % 4).. and the 32-column quarter (w / 4) of the half.
 template <bool kStore>
-__device__ void oz_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int e2) {
+__device__ void oz_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bool lower, int e2, int lsb) {
   umma_fence_after();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int ldS = 65;
@@ -273,11 +281,11 @@ __device__ void oz_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bo
       uint32_t v[8];
       tmem_ld8(tl + (uint32_t)((L - 2) * 64 + cb + 8 * g), v);
       tmem_wait_ld();
-      const int sh = kOzLsb - 8 * L;
+      const int sh = lsb - 8 * L;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int a = __float2int_rn(__uint_as_float(v[j]));
-        acc[j] += sh >= 0 ? ((long long)a << sh) : (long long)(a >> (-sh));
+        const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));
+        acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> (-sh));
       }
     }
 #pragma unroll
@@ -312,13 +320,14 @@ struct BsPipe {
 
 // Product C[128 x 128 tile at (m0, n0)] (FP64, ldc) -= (or, kStore, =) sum_j A_j[m0..] B_j[n0..]^T over
 // Kd from packed kS-slice operands (pairs j < pr.n, each A_j / B_j a packed operand whose 128-row blocks
-// rb = m0 / 128, n0 / 128 are used). kOz: fixed-point digits, scale exponents eA, eB; else floating
-// split. lower: only entries with column <= row of the tile are written (diagonal tiles).
+// rb = m0 / 128, n0 / 128 are used). kOz: fixed-point digits, scale exponents eA, eB, fixed-point
+// unit 2^-lsb S_A S_B (kOzLsbBounded or kOzLsbTile); else floating split. lower: only entries with
+// column <= row of the tile are written (diagonal tiles).
 // Thread 0 runs copies and MMAs; all threads run the epilogue. False (error raised, copies and MMAs
 // drained) on a time-out.
 template <int kS, bool kOz, bool kStore = false>
 __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const PkPairs& pr, int Kd, int m0,
-                             int n0, bool lower, int eA, int eB, DevStatus* st, long long timeout_ns,
+                             int n0, bool lower, int eA, int eB, int lsb, DevStatus* st, long long timeout_ns,
                              long long where) {
   constexpr int kRowsB = kOz ? 64 : 128;  // B rows per pass (the fixed-point form runs two 64-column halves)
   constexpr int kABytes = kS * kBsSliceBytes, kBBytes = kS * kRowsB * kBsKChunk * 2;
@@ -443,7 +452,7 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
     }
     if (__syncthreads_or(!ok)) return false;
     if constexpr (kOz) {
-      oz_epilogue<kStore>(u, C, ldc, m0, n0 + 64 * half, lower, eA + eB - kOzLsb);
+      oz_epilogue<kStore>(u, C, ldc, m0, n0 + 64 * half, lower, eA + eB - lsb, lsb);
     } else {
       umma_epilogue<kStore>(u, C, ldc, m0, n0, lower, pr.n > kPairsPerAcc ? 2 : 1);
     }

@@ -35,16 +35,19 @@ __device__ __noinline__ void form_pack_f32(int prec, const float* Xs, int ldx, i
 
 // C (T x T tile, ldc) -= (kStore: =) sum_j A_j B_j^T from packed operands of precision form `prec`.
 // The BF16-slice forms take T = 128; eA, eB: scale exponents of the fixed-point form.
+// Fixed-point operands with a per-tile scale (single-tile products: kStore) take the fixed-point unit
+// kOzLsbTile; the norm-bounded panel and V operands of the updates kOzLsbBounded.
 template <bool kStore>
 __device__ __noinline__ bool form_product(UmmaState& u, BsPipe& bp, int prec, double* C, int ldc, const PkPairs& pr,
                                           int T, bool lower, int eA, int eB, DevStatus* st, long long to,
                                           long long where) {
+  constexpr int lsb = kStore ? kOzLsbTile : kOzLsbBounded;
   switch (prec) {
-    case GP_BF16: return bs_block_sub<1, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
-    case GP_BF16X3: return bs_block_sub<2, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
-    case GP_BF16X6: return bs_block_sub<3, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, st, to, where);
+    case GP_BF16: return bs_block_sub<1, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, 0, st, to, where);
+    case GP_BF16X3: return bs_block_sub<2, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, 0, st, to, where);
+    case GP_BF16X6: return bs_block_sub<3, false, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, 0, 0, 0, st, to, where);
     case GP_FP64_OZAKI:
-      return bs_block_sub<kOzSlices, true, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, eA, eB, st, to, where);
+      return bs_block_sub<kOzSlices, true, kStore>(u, bp, C, ldc, pr, T, 0, 0, lower, eA, eB, lsb, st, to, where);
     case GP_TF32: return umma_pk_gemm_sub<kStore, 1>(u, C, ldc, pr, T, T, T, lower, st, to, where);
     default: return umma_pk_gemm_sub<kStore, 3>(u, C, ldc, pr, T, T, T, lower, st, to, where);
   }
@@ -762,20 +765,20 @@ __global__ void __launch_bounds__(kThreads, 1) debug_product_kernel(int prec, co
   for (int it = 0; it < reps && ok; ++it) {
     switch (prec) {
       case GP_BF16:
-        ok = store ? bs_block_sub<1, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
-                   : bs_block_sub<1, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        ok = store ? bs_block_sub<1, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<1, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, 0, st, timeout_ns, -2);
         break;
       case GP_BF16X3:
-        ok = store ? bs_block_sub<2, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
-                   : bs_block_sub<2, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        ok = store ? bs_block_sub<2, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<2, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, 0, st, timeout_ns, -2);
         break;
       case GP_BF16X6:
-        ok = store ? bs_block_sub<3, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, st, timeout_ns, -2)
-                   : bs_block_sub<3, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, st, timeout_ns, -2);
+        ok = store ? bs_block_sub<3, false, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, 0, 0, 0, st, timeout_ns, -2)
+                   : bs_block_sub<3, false, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, 0, 0, 0, st, timeout_ns, -2);
         break;
       case GP_FP64_OZAKI:
-        ok = store ? bs_block_sub<kOzSlices, true, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, eA, eB, st, timeout_ns, -2)
-                   : bs_block_sub<kOzSlices, true, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, eA, eB, st,
+        ok = store ? bs_block_sub<kOzSlices, true, true>(um, bp, C, kUmmaN, pr, K, 0, 0, false, eA, eB, kOzLsbTile, st, timeout_ns, -2)
+                   : bs_block_sub<kOzSlices, true, false>(um, bp, C, kUmmaN, pr, K, 0, 0, lower, eA, eB, kOzLsbTile, st,
                                                           timeout_ns, -2);
         break;
       case GP_TF32:
@@ -1088,6 +1091,51 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(const double* __restrict_
   }
 }
 
+// Pieces of the Arnoldi process of GMRES-based refinement (FP64): out[i] = <V_i, w> for i < k, V_i the
+// rows of V (leading dimension ldv), one CTA per i, fixed summation order.
+__global__ void __launch_bounds__(kThreads) multi_dot_kernel(const double* __restrict__ V, long long ldv,
+                                                             const double* __restrict__ w, long long n,
+                                                             double* __restrict__ out) {
+  __shared__ double red[kThreads / 32];
+  const double* v = V + (size_t)blockIdx.x * ldv;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += kThreads) s = fma(v[i], w[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+    out[blockIdx.x] = t;
+  }
+}
+
+// w[i] += sign * sum_{j<k} h[j] V_j[i] (h on the device).
+__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V, long long ldv,
+                                  const double* __restrict__ h, int k, double sign, long long n) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(h[j], V[(size_t)j * ldv + i], acc);
+    w[i] = fma(sign, acc, w[i]);
+  }
+}
+
+// dst[i] = src[i] * a for i < n.
+__global__ void scale_copy_kernel(double* __restrict__ dst, const double* __restrict__ src, double a, long long n) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    dst[i] = src[i] * a;
+}
+
+// diag(K) += tau on the first n rows of the packed lower tiles (the shifted factorisation of the
+// single-product forms; the stored FP64 copy of K keeps the unshifted matrix).
+__global__ void add_diag_kernel(double* __restrict__ Kt, int T, long long n, double tau) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    const long long I = i / T, r = i % T;
+    Kt[tri(I, I) * (size_t)T * T + (size_t)r * T + r] += tau;
+  }
+}
+
 // Batched assembly and right-hand sides, one work item per CTA (see launch_batch_pre).
 __global__ void __launch_bounds__(kThreads) batch_pre_kernel(const int4* __restrict__ items,
                                                              const GpDesc* __restrict__ descs, int noisy_prior) {
@@ -1396,6 +1444,35 @@ cudaError_t launch_scan_nonfinite(const double* a, long long cnt, long long base
   if (cnt <= 0) return cudaSuccess;
   const long long b = (cnt + kThreads - 1) / kThreads;
   scan_nonfinite_kernel<<<(unsigned)(b < 1216 ? b : 1216), kThreads, 0, st>>>(a, cnt, base, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_dot(const double* V, long long ldv, int k, const double* w, long long n, double* out,
+                             cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  multi_dot_kernel<<<k, kThreads, 0, st>>>(V, ldv, w, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy(double* w, const double* V, long long ldv, const double* h, int k, double sign,
+                              long long n, cudaStream_t st) {
+  if (k <= 0 || n <= 0) return cudaSuccess;
+  const long long b = (n + kThreads - 1) / kThreads;
+  multi_axpy_kernel<<<(unsigned)(b < 1216 ? b : 1216), kThreads, 0, st>>>(w, V, ldv, h, k, sign, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(double* dst, const double* src, double a, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long b = (n + kThreads - 1) / kThreads;
+  scale_copy_kernel<<<(unsigned)(b < 1216 ? b : 1216), kThreads, 0, st>>>(dst, src, a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_diag(double* Kt, int T, long long n, double tau, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long b = (n + kThreads - 1) / kThreads;
+  add_diag_kernel<<<(unsigned)(b < 1216 ? b : 1216), kThreads, 0, st>>>(Kt, T, n, tau);
   return cudaGetLastError();
 }
 

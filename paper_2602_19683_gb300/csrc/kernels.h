@@ -167,6 +167,14 @@ cudaError_t launch_init_lbar(const double* Lt, double* Bt, int T, int Mt, long l
 // out[0..3) = the three sums. partial needs 3 * Mt(Mt+1)/2 * (T/32) doubles.
 cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* X, long long n, int D, double l,
                                  double v, double* partial, double* out, cudaStream_t st);
+// GMRES-based refinement: out[i] = <V_i, w> (i < k, rows of V with leading dimension ldv); w += sign * sum_j
+// h_j V_j (h on the device); dst = a * src; and the diagonal shift diag(K) += tau of the packed tiles.
+cudaError_t launch_multi_dot(const double* V, long long ldv, int k, const double* w, long long n, double* out,
+                             cudaStream_t st);
+cudaError_t launch_multi_axpy(double* w, const double* V, long long ldv, const double* h, int k, double sign,
+                              long long n, cudaStream_t st);
+cudaError_t launch_scale_copy(double* dst, const double* src, double a, long long n, cudaStream_t st);
+cudaError_t launch_add_diag(double* Kt, int T, long long n, double tau, cudaStream_t st);
 // out[0] = sum_{i<n} a_i b_i (one CTA).
 cudaError_t launch_dot(const double* a, const double* b, long long n, double* out, cudaStream_t st);
 

@@ -6,7 +6,8 @@ The reference is exact: each FP64 product a b is split (Veltkamp/Dekker) into fo
 products and every entry is summed with math.fsum, so the only error left is the form's own.
 Bars, as max |C - C_exact| over max_ij sum_k |a_ik b_jk| (plus, where C is updated, half an FP64 unit
 in the last place of the stored result, the rounding of the subtraction itself):
-  GP_FP64_OZAKI  <= 2^-52 (FP64-class: 28 exact BF16 digit products, integer recombination)
+  GP_FP64_OZAKI: no worse than the FP64 product of the same operands (numpy's BLAS DGEMM, measured
+  against the same exact result) or 2^-53, whichever is larger: it is an FP64 product;
   GP_FP32 (3xTF32) <= 2e-6, GP_BF16X6 <= 2e-6 (FP32-class), GP_BF16X3 <= 1e-4, GP_TF32 <= 2e-3,
   GP_BF16 <= 2e-2 (one product of 11 / 8 significant bits).
 """
@@ -20,7 +21,13 @@ import __graft_entry__
 
 pytestmark = pytest.mark.gpu
 
-BARS = {"fp64_ozaki": 2.0 ** -52, "fp32": 2e-6, "bf16x6": 2e-6, "bf16x3": 1e-4, "tf32": 2e-3, "bf16": 2e-2}
+BARS = {"fp64_ozaki": 2.0 ** -53, "fp32": 2e-6, "bf16x6": 2e-6, "bf16x3": 1e-4, "tf32": 2e-3, "bf16": 2e-2}
+
+
+def bar(prec, scale, fp64_err):
+    """Allowed absolute error of a form (fp64_err: the FP64 BLAS product's error on the same inputs)."""
+    b = BARS[prec] * scale
+    return max(b, fp64_err) if prec == "fp64_ozaki" else b
 
 
 @pytest.fixture(scope="module")
@@ -72,9 +79,11 @@ def test_tile_product_matches_exact(api, prec, K, kind):
     got = C.cpu().numpy()
     rounding = 2.0 ** -53 * float(np.max(np.abs(got)))
     err = float(np.max(np.abs((C0 - got) - exact)))
-    print(f"{prec} K={K} {kind}: max error {err / scale:.3e} of sum|ab| (bar {BARS[prec]:.1e}; output rounding "
-          f"{rounding / scale:.1e})")
-    assert err <= BARS[prec] * scale + rounding
+    c64 = C0 - A @ B.T
+    err64 = float(np.max(np.abs((C0 - c64) - exact)))
+    print(f"{prec} K={K} {kind}: max error {err / scale:.3e} of sum|ab| (FP64 BLAS {err64 / scale:.3e}; bar "
+          f"{bar(prec, scale, err64) / scale:.1e}; output rounding {rounding / scale:.1e})")
+    assert err <= bar(prec, scale, err64) + rounding
 
 
 @pytest.mark.parametrize("prec", list(BARS))
@@ -84,9 +93,10 @@ def test_tile_product_store_and_lower(api, prec):
     Ad, Bd = (torch.from_numpy(x).cuda() for x in (A, B))
     exact = exact_product(A, B)
     scale = float(np.max(np.abs(A) @ np.abs(B).T))
+    err64 = float(np.max(np.abs(A @ B.T - exact)))
     C = torch.full((128, 128), 7.0, dtype=torch.float64, device="cuda")
     api.debug_tile_product(ctx, prec, Ad, Bd, C, store=True)
-    assert float(np.max(np.abs(C.cpu().numpy() - exact))) / scale <= BARS[prec]
+    assert float(np.max(np.abs(C.cpu().numpy() - exact))) <= bar(prec, scale, err64) + 2.0 ** -53 * scale
     C0 = np.random.default_rng(9).standard_normal((128, 128))
     C = torch.from_numpy(C0.copy()).cuda()
     api.debug_tile_product(ctx, prec, Ad, Bd, C, lower=True)
@@ -95,7 +105,7 @@ def test_tile_product_store_and_lower(api, prec):
     assert np.array_equal(got[iu], C0[iu])  # above the diagonal: untouched
     il = np.tril_indices(128)
     rounding = 2.0 ** -53 * float(np.max(np.abs(got)))
-    assert float(np.max(np.abs((C0 - got)[il] - exact[il]))) <= BARS[prec] * scale + rounding
+    assert float(np.max(np.abs((C0 - got)[il] - exact[il]))) <= bar(prec, scale, err64) + rounding
 
 
 def test_tile_product_rates(api):
