@@ -190,6 +190,10 @@ def parse():
                                                "to this path; a per-task-kind summary joins the JSON line")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (GP_FP32) leg")
+    p.add_argument("--no-emulated", action="store_true", help="skip the FP64-emulating (GP_FP64_OZAKI) leg")
+    p.add_argument("--variant", default="right", choices=["right", "left", "top"],
+                   help="FP64 tile-algorithm variant of the Cholesky graph (cfg.tile_variant)")
+    p.add_argument("--e2e-steps", type=int, default=3, help="timed steps of the end-to-end pass (at most --steps)")
     p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
     p.add_argument("--locality-order", default="default", choices=["default", "on", "off"],
                    help="tensor-core forms: start grouped updates that share a packed operand back to back "
@@ -334,6 +338,73 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+def form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, ms64, mean64, cov64, logdet64,
+             barrier):
+    """One precision form on the same workload: warm-up, `steps` timed solves with per-phase events,
+    errors of the mean, covariance and log-determinant against the FP64 results of this run."""
+    if FORM_PRODUCTS[prec][1] == "tf32":
+        measure_tf32_tflops(dev)  # the tensor roofline's denominator, before the timed leg
+    cx = api.Context(local, stream=stream, tile=args.tile, precision=prec, locality_order=locality_arg(args))
+    fx = [None]
+    mean_x = torch.empty_like(mean64)
+    cov_x = torch.empty_like(cov64)
+    iters = [0]
+    ph_ev = []
+
+    def step_x(record=False):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        if record:
+            evs[0].record(stream)
+        fx[0] = api.gp_assemble(cx, Xd, h, fx[0])
+        if record:
+            evs[1].record(stream)
+        api.gp_cholesky(cx, fx[0])
+        if record:
+            evs[2].record(stream)
+        _, iters[0] = api.gp_predict_mean(cx, fx[0], yd, Xsd, out=mean_x, want_iters=True)
+        if record:
+            evs[3].record(stream)
+        api.gp_predict_full_cov(cx, fx[0], Xsd, out=cov_x)
+        if record:
+            evs[4].record(stream)
+            ph_ev.append(evs)
+
+    for _ in range(args.warmup):
+        step_x()
+    api.gp_sync(cx)
+    barrier()
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(args.steps):
+        step_x(record=True)
+    m1.record(stream)
+    barrier()
+    api.gp_sync(cx)
+    msx = m0.elapsed_time(m1) / args.steps
+    phase = [sum(e[k].elapsed_time(e[k + 1]) for e in ph_ev) / len(ph_ev) / 1e3 for k in range(4)]
+    logdet_x = api.gp_logdet(cx, fx[0])
+
+    def relerr(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+    tile = ctx_tile(n, args.tile, True)
+    desc = {"fp32": "3xTF32 trailing updates and covariance products on tcgen05, FP64 POTRF/first-column TRSM, "
+                    "FP64 iterative refinement of the mean",
+            "fp64_ozaki": "FP64-accurate products from seven 8-bit digits per value on the BF16 tensor cores "
+                          "(28 digit products, integer recombination), FP64 POTRF and diagonal-tile inverses, "
+                          "no refinement"}[prec]
+    out = {"precision": desc, "tile": tile,
+           "roofline": mixed_cholesky_roofline(n, tile, phase[1], prec),
+           "s_per_solve": msx / 1e3, "tflops": algorithmic_flops(n, m) / (msx / 1e3) / 1e12,
+           "speedup_vs_fp64": ms64 / msx, "ir_iterations": iters[0],
+           "phases_s": {"assemble": phase[0], "cholesky": phase[1], "mean": phase[2], "full_cov": phase[3]},
+           "mean_err_vs_fp64": relerr(mean_x, mean64), "cov_err_vs_fp64": relerr(cov_x, cov64),
+           "logdet_err_vs_fp64": abs(logdet_x - logdet64) / abs(logdet64)}
+    fx[0].free()
+    cx.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -356,7 +427,7 @@ def run_ours(args):
     if FORM_PRODUCTS.get(args.precision, (0, ""))[1] == "tf32":
         measure_tf32_tflops(dev)  # the tensor roofline's denominator, before anything is timed
     ctx = api.Context(local, stream=stream, tile=args.tile, precision=args.precision, grid=args.grid,
-                      locality_order=locality_arg(args))
+                      locality_order=locality_arg(args), tile_variant=args.variant)
     mean = torch.empty(m, dtype=torch.float64, device=dev)
     cov = torch.empty((m, m), dtype=torch.float64, device=dev)
     fac = [None]
@@ -426,77 +497,27 @@ def run_ours(args):
             barrier()
             s0 = torch.cuda.Event(enable_timing=True)
             s1 = torch.cuda.Event(enable_timing=True)
+            e2e_steps = max(1, min(args.steps, args.e2e_steps))
             s0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(e2e_steps):
                 step_e2e()
             s1.record(stream)
             barrier()
             api.gp_sync(ctx)
-            e2e_ms = s0.elapsed_time(s1) / args.steps
+            e2e_ms = s0.elapsed_time(s1) / e2e_steps
             e2e = {"ms": e2e_ms, "h2d": (X.nbytes + y.nbytes + Xs.nbytes), "d2h": (m + m * m) * 8}
 
-        # mixed-precision leg: same workload, GP_FP32 mode, errors against this run's FP64 results
-        mixed = None
-        if not args.no_mixed and args.precision == "fp64":
+        # tensor-core legs: the same workload in other precision forms (GP_FP32 = 3xTF32 with FP64
+        # refinement; GP_FP64_OZAKI = FP64-accurate products from BF16 digits), errors against this
+        # run's FP64 results
+        legs = {}
+        if args.precision == "fp64":
             mean64, cov64 = mean.clone(), cov.clone()
             logdet64 = api.gp_logdet(ctx, fac[0])
-            measure_tf32_tflops(dev)  # the tensor roofline's denominator, before the timed leg
-            ctx32 = api.Context(local, stream=stream, tile=args.tile, precision="fp32",
-                                locality_order=locality_arg(args))
-            fac32 = [None]
-            mean32 = torch.empty_like(mean)
-            cov32 = torch.empty_like(cov)
-            iters = [0]
-
-            ph_ev = []
-
-            def step32(record=False):
-                evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
-                if record:
-                    evs[0].record(stream)
-                fac32[0] = api.gp_assemble(ctx32, Xd, h, fac32[0])
-                if record:
-                    evs[1].record(stream)
-                api.gp_cholesky(ctx32, fac32[0])
-                if record:
-                    evs[2].record(stream)
-                _, iters[0] = api.gp_predict_mean(ctx32, fac32[0], yd, Xsd, out=mean32, want_iters=True)
-                if record:
-                    evs[3].record(stream)
-                api.gp_predict_full_cov(ctx32, fac32[0], Xsd, out=cov32)
-                if record:
-                    evs[4].record(stream)
-                    ph_ev.append(evs)
-
-            for _ in range(args.warmup):
-                step32()
-            api.gp_sync(ctx32)
-            barrier()
-            m0 = torch.cuda.Event(enable_timing=True)
-            m1 = torch.cuda.Event(enable_timing=True)
-            m0.record(stream)
-            for _ in range(args.steps):
-                step32(record=True)
-            m1.record(stream)
-            barrier()
-            api.gp_sync(ctx32)
-            ms32 = m0.elapsed_time(m1) / args.steps
-            phase32 = [sum(e[k].elapsed_time(e[k + 1]) for e in ph_ev) / len(ph_ev) / 1e3 for k in range(4)]
-            logdet32 = api.gp_logdet(ctx32, fac32[0])
-
-            def relerr(a, b):
-                return float((a - b).abs().max() / b.abs().max())
-            mixed = {"precision": "fp32 trailing updates, FP64 POTRF/first-column TRSM/refinement",
-                     "tile": ctx_tile(n, args.tile, True),
-                     "roofline": mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), phase32[1]),
-                     "s_per_solve": ms32 / 1e3, "tflops": algorithmic_flops(n, m) / (ms32 / 1e3) / 1e12,
-                     "speedup_vs_fp64": ms / ms32, "ir_iterations": iters[0],
-                     "phases_s": {"assemble": phase32[0], "cholesky": phase32[1], "mean_refined": phase32[2],
-                                  "full_cov": phase32[3]},
-                     "mean_err_vs_fp64": relerr(mean32, mean64), "cov_err_vs_fp64": relerr(cov32, cov64),
-                     "logdet_err_vs_fp64": abs(logdet32 - logdet64) / abs(logdet64)}
-            fac32[0].free()
-            ctx32.close()
+            for prec in ([] if args.no_mixed else ["fp32"]) + ([] if args.no_emulated else ["fp64_ozaki"]):
+                legs[prec] = form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, ms,
+                                      mean64, cov64, logdet64, barrier)
+        mixed = legs.get("fp32")
 
     ms, chol_ms, e2e_ms = max_over_ranks([ms, chol_ms, e2e["ms"] if e2e else 0.0], ws, dev)
     flops = algorithmic_flops(n, m)
@@ -514,7 +535,7 @@ def run_ours(args):
             "data": "synthetic NFIR mass-spring-damper (seeded)",
             "config": {"workload": f"exact GP solve n={n} m={m} D={D}", "n": n, "m": m, "D": D,
                        "tile": ctx_tile(n, args.tile, args.precision != "fp64"), "precision": args.precision,
-                       "locality_order": args.locality_order,
+                       "locality_order": args.locality_order, "tile_variant": args.variant,
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (K is 4.4 GB)",
                        "s_per_solve": ms / 1e3, "cholesky_s": chol_ms / 1e3},
             "roofline": ({"kernel": "dag_kernel (tiled Cholesky)", "bound": "alu", "achieved": achieved,
@@ -527,6 +548,8 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clocks}
     if mixed:
         line["mixed"] = mixed
+    if "fp64_ozaki" in legs:
+        line["fp64_emulated"] = legs["fp64_ozaki"]
     if args.trace and rank == 0:
         line["trace"] = traced_cholesky(api, local, Xd, h, args)
     if e2e:

@@ -118,6 +118,11 @@ typedef struct {
                              every result keep K itself): > 0 fixed; 0 = automatic, u sqrt(n) max K_ii
                              (u = 2^-11 / 2^-8) times 8 after each non-positive pivot, at most five
                              tries (gp_cholesky then waits for the stream); < 0 = no shift             */
+  int32_t tile_variant;    /* GP_FP64 Cholesky graph (Sec. 3.2 names the three tile-algorithm variants):
+                             0 = right-looking (each column's trailing updates as separate tasks, longest-
+                             path order; the default), 1 = left-looking, 2 = top-looking (all updates of a
+                             tile fused into one task before its POTRF/TRSM, dispatched column by column /
+                             row by row). The tensor-core forms always run right-looking.              */
 } gp_config;
 
 typedef struct gp_ctx gp_ctx;
@@ -294,7 +299,7 @@ gp_status gp_predict_mean_noalloc(const double* X, const double* y, int64_t n, i
  * `graph` (0 = tiled Cholesky, 1 = covariance solve, 2 = mean solve, 3 = reverse sweep of the tiled
  * Cholesky used by gp_nlml_grad, 4 = the V solve of gp_predict_var) for Mt tile rows, Mc covariance
  * tile columns, tile edge T, `workers` CTAs and the cost model of precision `mixed` (0 = FP64,
- * 1 = GP_FP32 with the locality order off; 3 = GP_FP32 with it on) as int32 quadruples {kind, p, q, r} (kinds as in the
+ * 1 = GP_FP32 with the locality order off; 3 = GP_FP32 with it on; 4 / 5 = GP_FP64 with cfg.tile_variant 1 / 2) as int32 quadruples {kind, p, q, r} (kinds as in the
  * library's task table: 0 POTRF(J), 1 TRSM(I,J), 2 UPDATE(I,K,J), 3 VTRSM(J,c), 4 VGEMM(I,J,c),
  * 5 WSYRK(a,b,J), 6 FSOLVE(J), 7 FGEMV(I,J,ch), 8 BSOLVE(J), 9 BGEMV(J,I,ch), 10 RUPD(P,K,J),
  * 11 RTRSM(P,J), 12 RDIAG(P,J), 13 RPOTRF(J), 14 TRTRI(J): the FP64 inverse of the factored diagonal tile

@@ -31,7 +31,8 @@ class gp_config(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int32), ("noisy_prior", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("withhold_task", ctypes.c_int32), ("withhold_enable", ctypes.c_int32),
                 ("tensor_cores", ctypes.c_int32), ("trace", ctypes.c_int32), ("batch_order", ctypes.c_int32),
-                ("batch_ctas_per_sm", ctypes.c_int32), ("locality_order", ctypes.c_int32), ("shift", ctypes.c_double)]
+                ("batch_ctas_per_sm", ctypes.c_int32), ("locality_order", ctypes.c_int32), ("shift", ctypes.c_double),
+                ("tile_variant", ctypes.c_int32)]
 
 
 class gp_batch_desc(ctypes.Structure):

@@ -56,7 +56,7 @@ class Context:
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
                  tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0,
-                 locality_order: bool | None = None, shift: float = 0.0):
+                 locality_order: bool | None = None, shift: float = 0.0, tile_variant: str = "right"):
         self.lib = N.load()
         self.precision = precision
         self.device = torch.device("cuda", device)
@@ -75,6 +75,7 @@ class Context:
         cfg.batch_ctas_per_sm = batch_ctas_per_sm
         cfg.locality_order = 0 if locality_order is None else (1 if locality_order else -1)
         cfg.shift = shift
+        cfg.tile_variant = {"right": 0, "left": 1, "top": 2}[tile_variant]
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1

@@ -177,6 +177,7 @@ gpk::CostModel cost_model(const gp_ctx* c, int prec, int T = 0) {
   cm.update_group = tc ? (prec == GP_FP64_OZAKI ? 4 : 8) : 1;
   cm.tensor_cores = tc;
   cm.pair_rows = tc && T == 128 && prec == GP_FP32;
+  cm.variant = tc ? 0 : c->cfg.tile_variant;  // the grouped tensor-core updates hold at most 8 columns
   // operand-locality order of the grouped updates: on unless the caller turned it off (measured at
   // n = 32768, 3xTF32: mixed Cholesky 152 -> 142 ms)
   cm.locality_eps = (cm.tensor_cores && c->cfg.locality_order >= 0) ? 0.1 : 0.0;
@@ -468,7 +469,7 @@ gp_status gp_create(gp_ctx** out, int32_t device, void* stream, const gp_config*
   if (c.ir_maxit <= 0) c.ir_maxit = 10;
   if (c.timeout_ns <= 0) c.timeout_ns = 60LL * 1000 * 1000 * 1000;
   if (c.batch_order < 0 || c.batch_order > 1 || c.batch_ctas_per_sm < 0 || c.batch_ctas_per_sm > 2 ||
-      c.locality_order < -1 || c.locality_order > 1)
+      c.locality_order < -1 || c.locality_order > 1 || c.tile_variant < 0 || c.tile_variant > 2)
     return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(device));
   gp_ctx* ctx = new (std::nothrow) gp_ctx();
@@ -577,10 +578,14 @@ int64_t gp_trace(gp_ctx* c, int64_t* out, int64_t cap) {
 
 int64_t gp_schedule_tasks(int32_t graph, int32_t Mt, int32_t Mc, int32_t T, int32_t workers, int32_t mixed,
                           int32_t* out, int64_t cap) {
-  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4 || mixed < 0 || mixed > 3 ||
+  if (Mt < 0 || Mc < 0 || T < 32 || T % 32 || workers < 1 || graph < 0 || graph > 4 || mixed < 0 || mixed > 5 ||
       mixed == 2)
     return -1;
   gpk::CostModel cm;
+  if (mixed >= 4) {  // FP64 left-looking (4) / top-looking (5) Cholesky graph
+    cm.variant = mixed - 3;
+    mixed = 0;
+  }
   cm.mixed = mixed != 0;
   cm.update_group = (mixed && T % 128 == 0) ? 8 : 1;
   cm.tensor_cores = cm.update_group > 1;

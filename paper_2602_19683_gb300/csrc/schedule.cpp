@@ -147,6 +147,43 @@ std::vector<Task4> cholesky_tasks(int Mt, int T, int workers, const CostModel& c
     c_gemm = cm.tc_gemm * s2;
     c_syrk = cm.tc_syrk * s2;
   }
+  if (cm.variant == 1 || cm.variant == 2) {
+    // left-/top-looking: tile (I, K) takes all its updates (columns J < K) in one task, then its
+    // POTRF / TRSM; dispatched in column order (left) or row order (top), longest path within
+    std::vector<int> fin(tri(Mt, 0), -1);  // the task that made tile (I, K) final
+    std::vector<double> key;
+    auto keyed = [&](int t, double k) {
+      if ((int)key.size() <= t) key.resize(t + 1, 0.0);
+      key[t] = k;
+    };
+    const bool left = cm.variant == 1;
+    for (int a = 0; a < Mt; ++a)          // left: a = column K, c = row I >= K; top: a = row I, c = column K <= I
+      for (int c = left ? a : 0; left ? c < Mt : c <= a; ++c) {
+        const int I = left ? c : a, K = left ? a : c;
+        std::vector<int> deps;
+        int upd = -1;
+        if (K > 0) {
+          for (int J = 0; J < K; ++J) {
+            deps.push_back(fin[tri(I, J)]);
+            deps.push_back(fin[tri(K, J)]);
+          }
+          upd = b.add_v(TASK_UPD, I, K, 0 | (K << 16), K * (I == K ? c_syrk : c_gemm), deps);
+          keyed(upd, -(double)a);
+        }
+        int t;
+        if (I == K) {
+          t = b.add(TASK_POTRF, K, 0, 0, c_potrf, {upd});
+          keyed(t, -(double)a);
+          keyed(b.add(TASK_TRTRI, K, 0, 0, c_trsm0, {t}), -(double)a);
+        } else {
+          t = b.add(TASK_TRSM, I, K, 0, K == 0 ? c_trsm0 : c_trsm, {fin[tri(K, K)], upd});
+          keyed(t, -(double)a);
+        }
+        fin[tri(I, K)] = t;
+      }
+    key.resize(b.tasks.size(), 0.0);
+    return b.ordered(workers, &key);
+  }
   // Updates of a tile whose critical use is still far away are grouped: columns [J0, J1) in one task
   // (one pass over the tile's C instead of J1 - J0); the last kTail columns before the tile is needed
   // stay single so the critical path is not lengthened.

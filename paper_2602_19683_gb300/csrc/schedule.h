@@ -32,6 +32,11 @@ struct CostModel {
   double tc_vtrsm = 35e-6, tc_vgemm = 5.5e-6;
   double potrf_eff = 0.5, trsm_eff = 0.8, gemm_eff = 0.97, vec_eff = 0.3;
   double task_overhead = 3e-6;
+  // Tile-algorithm variant of the Cholesky graph (Sec. 3.2 names all three): 0 = right-looking (each
+  // column's updates applied as soon as the column is factored, dispatched by longest remaining path);
+  // 1 = left-looking and 2 = top-looking (every tile's updates from all earlier columns fused into one
+  // task run just before the tile is factored, dispatched column by column / row by row).
+  int variant = 0;
 };
 
 // Operand locality for list_schedule: per task the keys of the packed left (a) and right (b) operand

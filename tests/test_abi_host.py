@@ -97,6 +97,40 @@ def test_cholesky_schedule_is_topological(lib, Mt, workers, mixed):
         assert paired > 0
 
 
+@pytest.mark.parametrize("Mt,workers,variant", [(1, 3, 4), (2, 1, 4), (9, 304, 4), (12, 152, 5), (5, 2, 5)])
+def test_left_and_top_looking_schedules(lib, Mt, workers, variant):
+    """The left-/top-looking Cholesky graphs (Sec. 3.2's other tile variants): every tile takes all its
+    updates (columns 0..K-1) in one task after those columns are final, then its POTRF/TRSM; the order
+    is topological, and the factor-final events follow the variant's column / row order."""
+    t = tasks(lib, 0, Mt, 0, 64, workers, variant)
+    assert len(t) == 2 * Mt + Mt * (Mt - 1) // 2 + Mt * (Mt + 1) // 2 - Mt
+    cnt, final_order = {}, []
+    for kind, p, q, r in t:
+        if kind == 0:
+            assert cnt.get((p, p), 0) == p
+            cnt[(p, p)] = p + 1
+            final_order.append((p, p))
+        elif kind == 14:
+            assert cnt.get((p, p), 0) == p + 1
+        elif kind == 1:
+            assert cnt.get((q, q), 0) == q + 1 and cnt.get((p, q), 0) == q
+            cnt[(p, q)] = q + 1
+            final_order.append((p, q))
+        elif kind == 2:
+            J0, J1 = r & 0xFFFF, r >> 16
+            assert J0 == 0 and J1 == q >= 1 and p >= q
+            for J in range(J1):
+                assert cnt.get((p, J), 0) == J + 1 and cnt.get((q, J), 0) == J + 1
+            assert cnt.get((p, q), 0) == 0
+            cnt[(p, q)] = J1
+        else:
+            raise AssertionError(kind)
+    assert all(cnt[(I, J)] == J + 1 for I in range(Mt) for J in range(I + 1))
+    if workers == 1:  # one worker follows the variant's order exactly
+        key = (lambda ij: (ij[1], ij[0])) if variant == 4 else (lambda ij: ij)
+        assert final_order == sorted(final_order, key=key)
+
+
 @pytest.mark.parametrize("Mt,Mc,workers,mixed", [(1, 1, 2, 0), (4, 3, 5, 0), (7, 2, 304, 0), (1, 1, 2, 1),
                                                  (9, 3, 5, 1), (13, 2, 304, 1)])
 def test_cov_schedule_is_topological(lib, Mt, Mc, workers, mixed):
@@ -191,10 +225,11 @@ def test_adjoint_schedule_is_topological(lib, Mt, workers, mixed):
 
 def test_schedule_rejects_bad_arguments(lib):
     assert lib.gp_schedule_tasks(0, 4, 0, 48, 1, 0, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 64, 1, 6, None, 0) == -1
     assert lib.gp_schedule_tasks(5, 4, 0, 64, 1, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 64, 0, 0, None, 0) == -1
     assert lib.gp_schedule_tasks(0, 4, 0, 128, 1, 2, None, 0) == -1
-    assert lib.gp_schedule_tasks(0, 4, 0, 128, 1, 4, None, 0) == -1
+    assert lib.gp_schedule_tasks(0, 4, 0, 128, 1, 7, None, 0) == -1
 
 
 def _shared_neighbours(t):

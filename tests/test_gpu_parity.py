@@ -369,3 +369,24 @@ def test_full_size_sampled_mixed(api):
     cref = oracle.assemble_prior(Xs[cols], H0) - V.T @ V
     c = cov.cpu().numpy()[np.ix_(cols, cols)]
     assert np.max(np.abs(c - cref)) <= 1e-4 * H0[1]
+
+
+@pytest.mark.parametrize("variant", ["left", "top"])
+@pytest.mark.parametrize("n,m,T", [(1000, 200, 64), (2048, 256, 128)])
+def test_left_and_top_looking_match_oracle(api, variant, n, m, T):
+    """The left- and top-looking tile variants of Sec. 3.2 (every tile's updates fused into one task,
+    dispatched column by column / row by row) give the FP64 results at the FP64 bars."""
+    X, y, Xs, _ = nfir.make_dataset(n, m, 8, 21)
+    ref = oracle.gp_predict(X, y, Xs, H0)
+    ctx = api.Context(0, tile=T, tile_variant=variant)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    L = api.gp_factor_rows(ctx, f).cpu().numpy()
+    mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+    cov = api.gp_predict_full_cov(ctx, f, Xsd)
+    api.gp_sync(ctx)
+    assert np.linalg.norm(L @ L.T - ref["K"]) / np.linalg.norm(ref["K"]) <= 1e-13
+    assert rel(mean.cpu().numpy(), ref["mean"]) <= 1e-10
+    assert rel(cov.cpu().numpy(), ref["cov"]) <= 1e-9
+    f.free()
