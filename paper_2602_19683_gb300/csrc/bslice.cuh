@@ -25,11 +25,12 @@
 //    BF16 tensor-core products instead of one FP64 product.
 //
 // Packed operand layout (global memory, written once by cta_pack_bs, copied verbatim into shared
-// memory by bulk copies): an R x Kd operand (R a multiple of 128, Kd of 32) is a sequence of chunks,
-// one per (128-row block rb, 32-wide k block kc) in the order rb (Kd / 32) + kc; a chunk holds the kS
-// slices one after the other, each 128 rows x 32 BF16 (8 KB) in the K-major 64-byte-swizzled layout
-// the MMA reads (8-row groups 512 B apart, the 16-byte unit u of row r stored at u ^ ((r >> 1) & 3)).
-// Rows 64h..64h+63 of a slice are the contiguous 4 KB at 4096 h, themselves a valid 64-row operand.
+// memory by bulk copies): an R x Kd operand (R a multiple of 128) is a sequence of chunks, one per
+// (128-row block rb, kKC-wide k block kc) in the order rb (Kd / kKC) + kc; a chunk holds the kS slices
+// one after the other, each 128 rows x kKC BF16 in the K-major swizzled layout the MMA reads: kKC = 32
+// (floating split: 8 KB slices, 64-byte swizzle, 8-row groups 512 B apart) or kKC = 16 (fixed point: 4 KB
+// slices, 32-byte swizzle, groups 256 B apart). Rows 64h..64h+63 of a slice are its contiguous second
+// half, themselves a valid 64-row operand.
 //
 // Every wait is bounded (DevStatus time-out); after a time-out the issuing thread waits, bounded, for
 // its own copies and MMAs in flight before the CTA leaves, so shared memory and TMEM are quiet.
@@ -38,25 +39,38 @@
 
 namespace gpk {
 
-constexpr int kBsKChunk = 32;                          // k per chunk (64 bytes of BF16 per row)
-constexpr int kBsSliceBytes = kUmmaM * kBsKChunk * 2;  // 8 KB: one slice of a 128-row chunk
+// Chunk widths: the floating-split forms move 32-wide k chunks (64 bytes of BF16 per row, 64-byte
+// swizzle); the fixed-point form 16-wide chunks (32 bytes per row, 32-byte swizzle), so that its
+// larger stages (seven slices of both operands) still come five deep.
+constexpr int kBsKcFloat = 32, kBsKcFixed = 16;
+template <int kKC>
+__host__ __device__ constexpr int bs_slice_bytes() { return kUmmaM * kKC * 2; }  // one slice of a 128-row chunk
 constexpr int kBsMaxStages = 6;
-constexpr int kBsStageMem = 192 * 1024;                // stage memory (inside kUmmaSmemBytes)
+constexpr int kBsStageMem = 210 * 1024;                // stage memory (inside kUmmaSmemBytes)
 constexpr int kOzSlices = 7, kOzLevels = 7;            // digits 1..7, levels 2..8
 constexpr int kOzLsbBounded = 56;   // fixed-point sum unit 2^-56 S_A S_B: operands with rows of norm <= S
 constexpr int kOzLsbTile = 52;      // 2^-52 S_A S_B: max-scaled operands of one 128-wide tile product
 static_assert(kBsStageMem + 1024 <= kUmmaSmemBytes, "slice stages must fit the dynamic smem");
 static_assert(kOzLevels * 64 <= kUmmaTmemCols, "seven 64-column level accumulators must fit TMEM");
 
-// Byte offset of BF16 element (r, k), r < 128 (or < 64 for a half), k < 32, in a 64-byte-swizzled slice.
-__device__ __forceinline__ uint32_t sw64_offset(int r, int k) {
-  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + (k & 7) * 2);
+// Byte offset of BF16 element (r, k) (k < kKC) in a K-major swizzled slice: rows of 2 kKC bytes in
+// 8-row groups; the 16-byte unit u of row r is stored at u ^ ((r >> 1) & 3) (64-byte swizzle, kKC = 32)
+// or u ^ ((r >> 2) & 1) (32-byte swizzle, kKC = 16).
+template <int kKC>
+__device__ __forceinline__ uint32_t bs_offset(int r, int k) {
+  if constexpr (kKC == 32)
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + (k & 7) * 2);
+  else
+    return (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((((k >> 3) ^ ((r >> 2) & 1))) << 4) + (k & 7) * 2);
 }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 B apart.
-__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+// Shared-memory matrix descriptor of a K-major swizzled BF16 operand: 64-byte swizzle with 8-row
+// groups 512 B apart (kKC = 32), or 32-byte swizzle with groups 256 B apart (kKC = 16).
+template <int kKC>
+__device__ __forceinline__ uint64_t bs_desc(uint32_t saddr) {
+  constexpr uint64_t sbo = (uint64_t)(8 * kKC * 2) >> 4, mode = kKC == 32 ? 4 : 6;
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | (sbo << 32) | ((uint64_t)1 << 46) |
+         (mode << 61);
 }
 
 // Instruction descriptor: kind::f16, FP32 accumulator, A and B BF16, both K-major, M = 128, N given.
@@ -127,29 +141,32 @@ __device__ __forceinline__ void split_fixed(double x, int e, uint32_t (&h)[kOzSl
   h[0] = __float_as_uint(small_int_to_f32((int)F)) >> 16;
 }
 
+template <int kKC>
 __device__ __forceinline__ size_t bs_chunk_off(int rb, int kc, int Kd, int kS) {
-  return ((size_t)rb * (Kd / kBsKChunk) + kc) * (size_t)kS * kBsSliceBytes;
+  return ((size_t)rb * (Kd / kKC) + kc) * (size_t)kS * bs_slice_bytes<kKC>();
 }
 
 // Writes the packed kS-slice operand of an R x Kd FP64 block: Op[r][k] = src[r * ld + k] (trans = false)
 // or src[k * ld + r] (trans = true). kOz: fixed-point digits at scale 2^e; otherwise floating split.
-// R a multiple of 128, Kd of 32. Loads coalesced in both forms.
-template <int kS, bool kOz>
+// kKC: the chunk width of the layout. R a multiple of 128, Kd of kKC. Loads coalesced in both forms.
+template <int kS, bool kOz, int kKC>
 __device__ void cta_pack_bs(const double* src, int ld, bool trans, int R, int Kd, uint8_t* dst, int e) {
+  constexpr int kSlice = bs_slice_bytes<kKC>();
   const int t = threadIdx.x;
   for (int rb = 0; rb < R / kUmmaM; ++rb)
-    for (int kc = 0; kc < Kd / kBsKChunk; ++kc) {
-      uint8_t* ch = dst + bs_chunk_off(rb, kc, Kd, kS);
-      if (!trans) {  // thread: k pair 2 kp (kp = t & 15), rows t >> 4 + 16 pass
-        const int kp = t & 15, rr = t >> 4;
-        double2 d[8];
+    for (int kc = 0; kc < Kd / kKC; ++kc) {
+      uint8_t* ch = dst + bs_chunk_off<kKC>(rb, kc, Kd, kS);
+      if (!trans) {  // thread: k pair 2 kp of its row; kKC / 2 threads per row
+        constexpr int kPairs = kKC / 2, kRowsPerPass = kThreads / kPairs, kPasses = kUmmaM / kRowsPerPass;
+        const int kp = t % kPairs, rr = t / kPairs;
+        double2 d[kPasses];
 #pragma unroll
-        for (int pass = 0; pass < 8; ++pass)
-          d[pass] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(rb * kUmmaM + rr + 16 * pass) * ld +
-                                                            kc * kBsKChunk) + kp);
+        for (int pass = 0; pass < kPasses; ++pass)
+          d[pass] = __ldcg(reinterpret_cast<const double2*>(
+                               src + (size_t)(rb * kUmmaM + rr + kRowsPerPass * pass) * ld + kc * kKC) + kp);
 #pragma unroll
-        for (int pass = 0; pass < 8; ++pass) {
-          const uint32_t off = sw64_offset(rr + 16 * pass, 2 * kp);
+        for (int pass = 0; pass < kPasses; ++pass) {
+          const uint32_t off = bs_offset<kKC>(rr + kRowsPerPass * pass, 2 * kp);
           uint32_t h0[kS], h1[kS];
           if constexpr (kOz) {
             split_fixed(d[pass].x, e, h0);
@@ -160,17 +177,18 @@ __device__ void cta_pack_bs(const double* src, int ld, bool trans, int R, int Kd
           }
 #pragma unroll
           for (int s = 0; s < kS; ++s)
-            *reinterpret_cast<uint32_t*>(ch + s * kBsSliceBytes + off) = h0[s] | (h1[s] << 16);
+            *reinterpret_cast<uint32_t*>(ch + s * kSlice + off) = h0[s] | (h1[s] << 16);
         }
-      } else {  // thread: k = lane, rows 16 w .. 16 w + 15 (two per double2 load)
-        const int k = t & 31, w = t >> 5;
-        double2 d[8];
+      } else {  // thread: k = t % kKC, a run of kRows consecutive r (two per double2 load)
+        constexpr int kGroups = kThreads / kKC, kRows = kUmmaM / kGroups;
+        const int k = t % kKC, g = t / kKC;
+        double2 d[kRows / 2];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          d[q] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(kc * kBsKChunk + k) * ld + rb * kUmmaM +
-                                                         w * 16) + q);
+        for (int q = 0; q < kRows / 2; ++q)
+          d[q] = __ldcg(reinterpret_cast<const double2*>(src + (size_t)(kc * kKC + k) * ld + rb * kUmmaM +
+                                                         g * kRows) + q);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kRows / 2; ++q) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             uint32_t hv[kS];
@@ -178,10 +196,10 @@ __device__ void cta_pack_bs(const double* src, int ld, bool trans, int R, int Kd
               split_fixed(c ? d[q].y : d[q].x, e, hv);
             else
               split_float<kS>(f64_to_f32_rn(c ? d[q].y : d[q].x), hv);
-            const uint32_t off = sw64_offset(w * 16 + 2 * q + c, k);
+            const uint32_t off = bs_offset<kKC>(g * kRows + 2 * q + c, k);
 #pragma unroll
             for (int s = 0; s < kS; ++s)
-              *reinterpret_cast<uint16_t*>(ch + s * kBsSliceBytes + off) = (uint16_t)hv[s];
+              *reinterpret_cast<uint16_t*>(ch + s * kSlice + off) = (uint16_t)hv[s];
           }
         }
       }
@@ -194,21 +212,22 @@ __device__ void cta_pack_bs(const double* src, int ld, bool trans, int R, int Kd
 // columns beyond nb are zero), floating split (the mixed forms' FP32 inverse of a diagonal tile).
 template <int kS>
 __device__ void cta_pack_bs_f32(const float* Xs, int ld, int nb, uint8_t* dst) {
-  for (int kc = 0; kc < nb / kBsKChunk; ++kc) {
-    uint8_t* ch = dst + bs_chunk_off(0, kc, nb, kS);
+  constexpr int kKC = kBsKcFloat, kSlice = bs_slice_bytes<kKC>();
+  for (int kc = 0; kc < nb / kKC; ++kc) {
+    uint8_t* ch = dst + bs_chunk_off<kKC>(0, kc, nb, kS);
     for (int e2 = threadIdx.x; e2 < kUmmaM * 16; e2 += kThreads) {
       const int r = e2 >> 4, kp = e2 & 15;
       float f0 = 0.f, f1 = 0.f;
       if (r < nb) {
-        f0 = Xs[r * ld + kc * kBsKChunk + 2 * kp];
-        f1 = Xs[r * ld + kc * kBsKChunk + 2 * kp + 1];
+        f0 = Xs[r * ld + kc * kKC + 2 * kp];
+        f1 = Xs[r * ld + kc * kKC + 2 * kp + 1];
       }
       uint32_t h0[kS], h1[kS];
       split_float<kS>(f0, h0);
       split_float<kS>(f1, h1);
-      const uint32_t off = sw64_offset(r, 2 * kp);
+      const uint32_t off = bs_offset<kKC>(r, 2 * kp);
 #pragma unroll
-      for (int s = 0; s < kS; ++s) *reinterpret_cast<uint32_t*>(ch + s * kBsSliceBytes + off) = h0[s] | (h1[s] << 16);
+      for (int s = 0; s < kS; ++s) *reinterpret_cast<uint32_t*>(ch + s * kSlice + off) = h0[s] | (h1[s] << 16);
     }
   }
   fence_proxy_async_global();
@@ -329,13 +348,16 @@ template <int kS, bool kOz, bool kStore = false>
 __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const PkPairs& pr, int Kd, int m0,
                              int n0, bool lower, int eA, int eB, int lsb, DevStatus* st, long long timeout_ns,
                              long long where) {
+  constexpr int kKC = kOz ? kBsKcFixed : kBsKcFloat;  // k per chunk
+  constexpr int kSlice = bs_slice_bytes<kKC>();
   constexpr int kRowsB = kOz ? 64 : 128;  // B rows per pass (the fixed-point form runs two 64-column halves)
-  constexpr int kABytes = kS * kBsSliceBytes, kBBytes = kS * kRowsB * kBsKChunk * 2;
+  constexpr int kBSlice = kRowsB * kKC * 2;  // bytes of one B slice in a stage
+  constexpr int kABytes = kS * kSlice, kBBytes = kS * kBSlice;
   constexpr int kStage = kABytes + kBBytes;
   constexpr int kStages = (kBsStageMem / kStage) < kBsMaxStages ? (kBsStageMem / kStage) : kBsMaxStages;
   static_assert(kStages >= 2, "at least two stages");
   static_assert(kStage % 1024 == 0, "stages stay 1024-byte aligned");
-  const int nkp = Kd / kBsKChunk, nk = nkp * pr.n;
+  const int nkp = Kd / kKC, nk = nkp * pr.n;
   const int rbA = m0 / kUmmaM, rbB = n0 / kUmmaM;
   constexpr int kHalves = kOz ? 2 : 1;
   for (int half = 0; half < kHalves; ++half) {
@@ -348,13 +370,12 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
         const int s = i % kStages, p = i / nkp, kc = i % nkp;
         uint8_t* base = u.smem + s * kStage;
         mbar_expect_tx(&bp.full[s], kStage);
-        tma_bulk_g2s(base, pr.A[p] + bs_chunk_off(rbA, kc, Kd, kS), kABytes, &bp.full[s]);
-        const uint8_t* bsrc = pr.B[p] + bs_chunk_off(rbB, kc, Kd, kS);
-        if (kOz) {
+        tma_bulk_g2s(base, pr.A[p] + bs_chunk_off<kKC>(rbA, kc, Kd, kS), kABytes, &bp.full[s]);
+        const uint8_t* bsrc = pr.B[p] + bs_chunk_off<kKC>(rbB, kc, Kd, kS);
+        if (kOz) {  // rows 64 half .. of every slice: a contiguous kBSlice bytes at half * kBSlice
 #pragma unroll
           for (int q = 0; q < kS; ++q)
-            tma_bulk_g2s(base + kABytes + q * (kRowsB * kBsKChunk * 2), bsrc + q * kBsSliceBytes + half * 4096, 4096,
-                         &bp.full[s]);
+            tma_bulk_g2s(base + kABytes + q * kBSlice, bsrc + q * kSlice + half * kBSlice, kBSlice, &bp.full[s]);
         } else {
           tma_bulk_g2s(base + kABytes, bsrc, kBBytes, &bp.full[s]);
         }
@@ -372,7 +393,7 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
         umma_fence_after();
         const uint32_t a0 = smem_u32(u.smem + s * kStage), b0 = a0 + kABytes;
 #pragma unroll
-        for (int ks = 0; ks < kBsKChunk / 16; ++ks) {
+        for (int ks = 0; ks < kKC / 16; ++ks) {
           const uint32_t o = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzled row
           if constexpr (kOz) {
             // slice p of A against slices q = 1 .. 8 - p of B, stacked along N (64 columns each), into
@@ -385,9 +406,8 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
                 const int q1 = (q0 + 3 < nq) ? q0 + 3 : nq;
                 const int N = (q1 - q0 + 1) * 64;
                 const uint32_t acc = (i > 0 || ks > 0 || p > 1) ? 1u : 0u;  // p = 1 opens every level
-                umma_bf16(u.tmem + (uint32_t)((p + q0 - 2) * 64),
-                          umma_desc_sw64(a0 + (p - 1) * kBsSliceBytes + o),
-                          umma_desc_sw64(b0 + (q0 - 1) * (kRowsB * kBsKChunk * 2) + o), idesc_bf16(N), acc);
+                umma_bf16(u.tmem + (uint32_t)((p + q0 - 2) * 64), bs_desc<kKC>(a0 + (p - 1) * kSlice + o),
+                          bs_desc<kKC>(b0 + (q0 - 1) * kBSlice + o), idesc_bf16(N), acc);
               }
             }
           } else {
@@ -401,8 +421,8 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
             for (int p = 1; p <= kS; ++p)
 #pragma unroll
               for (int q = 1; q + p <= kS + 1; ++q) {
-                umma_bf16(d, umma_desc_sw64(a0 + (p - 1) * kBsSliceBytes + o),
-                          umma_desc_sw64(b0 + (q - 1) * kBsSliceBytes + o), idesc_bf16(kUmmaN),
+                umma_bf16(d, bs_desc<kKC>(a0 + (p - 1) * kSlice + o), bs_desc<kKC>(b0 + (q - 1) * kBSlice + o),
+                          idesc_bf16(kUmmaN),
                           (first && !opened) ? 0u : 1u);
                 opened = true;
               }

@@ -15,10 +15,10 @@ namespace gpk {
 __device__ __noinline__ void form_pack(int prec, const double* src, int ld, bool trans, int R, int Kd, uint8_t* dst,
                                        int e) {
   switch (prec) {
-    case GP_BF16: cta_pack_bs<1, false>(src, ld, trans, R, Kd, dst, 0); break;
-    case GP_BF16X3: cta_pack_bs<2, false>(src, ld, trans, R, Kd, dst, 0); break;
-    case GP_BF16X6: cta_pack_bs<3, false>(src, ld, trans, R, Kd, dst, 0); break;
-    case GP_FP64_OZAKI: cta_pack_bs<kOzSlices, true>(src, ld, trans, R, Kd, dst, e); break;
+    case GP_BF16: cta_pack_bs<1, false, kBsKcFloat>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_BF16X3: cta_pack_bs<2, false, kBsKcFloat>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_BF16X6: cta_pack_bs<3, false, kBsKcFloat>(src, ld, trans, R, Kd, dst, 0); break;
+    case GP_FP64_OZAKI: cta_pack_bs<kOzSlices, true, kBsKcFixed>(src, ld, trans, R, Kd, dst, e); break;
     default: cta_pack_operand(src, ld, trans, R, Kd, dst); break;  // GP_FP32 (3xTF32), GP_TF32
   }
 }

@@ -30,8 +30,10 @@ constexpr int kPkStages = 3;                           // stages of the packed-o
 // diagonal tile during a shared-memory POTRF (and of two 128 x 129 FP32 tiles while its inverse is
 // formed), and of the FP64/FP32 tile routines' scratch; plus alignment slack.
 constexpr int kMixedTileSmemBytes = 128 * 129 * 8;
-constexpr int kUmmaSmemBytes =
-    (kPkStages * kUmmaStageBytes > kMixedTileSmemBytes ? kPkStages * kUmmaStageBytes : kMixedTileSmemBytes) + 4096;
+// The BF16-slice products (bslice.cuh) take 210 KB of stages; 1 KB of alignment slack on top.
+constexpr int kUmmaSmemBytes = 210 * 1024 + 1024;
+static_assert(kUmmaSmemBytes >= kPkStages * kUmmaStageBytes + 1024 && kUmmaSmemBytes >= kMixedTileSmemBytes + 4096,
+              "the dynamic smem holds the TF32 stages and the shared-memory POTRF tile");
 // four 128 x 128 FP32 accumulators: two per output tile, for the paired-row updates (umma_packed.cuh);
 // the whole tensor memory of the SM, which holds one CTA of the mixed kernel (shared memory bound)
 constexpr int kUmmaTmemCols = 512;

@@ -33,7 +33,7 @@ MIXED_BOUNDS_8192 = {
     "tc": {"factor": 2e-5, "mean": 1e-10, "cov": 2e-4, "logdet": 1e-5},   # GP_FP32: tcgen05, 3xTF32
     "fma": {"factor": 1e-5, "mean": 1e-10, "cov": 1e-4, "logdet": 1e-5},  # GP_FP32: FP32 FMA pipes
     "bf16x6": {"factor": 2e-5, "mean": 1e-10, "cov": 2e-4, "logdet": 2e-5},
-    "bf16x3": {"factor": 1e-4, "mean": 1e-10, "cov": 5e-4, "logdet": 1e-4},
+    "bf16x3": {"factor": 1e-4, "mean": 1e-10, "cov": 1e-3, "logdet": 1e-4},
     # FP64 products emulated on the BF16 tensor cores: the FP64 bars
     "fp64_ozaki": {"factor": 1e-13, "mean": 1e-10, "cov": 1e-9, "logdet": 1e-12},
 }
