@@ -722,6 +722,38 @@ def run_large(args):
     return 0
 
 
+def vendor_gp_loop(torch, gps, ref_means, args):
+    """Per-GP loop over vendor library calls: K from torch elementwise ops, L by cuSOLVER potrf
+    (torch.linalg.cholesky), alpha by potrs (torch.cholesky_solve), V by cuBLAS trsm
+    (torch.linalg.solve_triangular), the mean and W by cuBLAS gemm. FP64. Returns its GPs/s and its
+    largest mean difference from the library's FP64 batch."""
+    def solve(X, y, Xs, h):
+        def k(A, B):
+            return h.v * torch.exp(-torch.cdist(A, B).square() / (2.0 * h.l * h.l))
+        K = k(X, X) + h.s2 * torch.eye(X.shape[0], dtype=X.dtype, device=X.device)
+        L = torch.linalg.cholesky(K)
+        Kxs = k(X, Xs)
+        alpha = torch.cholesky_solve(y[:, None], L)
+        mean = (Kxs.T @ alpha)[:, 0]
+        V = torch.linalg.solve_triangular(L, Kxs, upper=False)
+        cov = k(Xs, Xs) - V.T @ V
+        return mean, cov
+    outs = [solve(*g) for g in gps]  # warm-up: library handles, kernels
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 2))
+    e0.record()
+    for _ in range(reps):
+        outs = [solve(*g) for g in gps]
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps / 1e3
+    err = max(float((o[0] - r).abs().max() / r.abs().max()) for o, r in zip(outs, ref_means))
+    return {"s_per_batch": t, "gps_per_s": len(gps) / t, "mean_diff_vs_library_fp64": err,
+            "calls": "torch.linalg.cholesky (cuSOLVER potrf), cholesky_solve (potrs), solve_triangular (cuBLAS "
+                     "trsm), matmul (cuBLAS gemm); K from torch.cdist/exp"}
+
+
 def run_batch(args):
     """512 independent GPs, n ~ U[128, 4096], m = 256, D in {4, 8, 16}: one CUDA-graph launch (batched
     assembly + one persistent DAG launch + outputs). Per precision: the autotuner (gp_batch_autotune)
@@ -789,6 +821,9 @@ def run_batch(args):
         res[prec]["loop_s"] = tl
         res[prec]["loop_gps_per_s"] = B / tl
         res[prec]["speedup_vs_loop"] = tl / t
+    # vendor per-GP loop: the same pipeline (Eqs. 1-3) in FP64 through cuSOLVER potrf/potrs and cuBLAS
+    # trsm/gemm as torch exposes them, one GP at a time (a baseline only; never the product path)
+    res["fp64"]["vendor_loop"] = vendor_gp_loop(torch, gps, ref_means, args)
     line = {"metric": "batched GP prediction (512 uneven GPs, mean + full cov)", "value": res["fp64"]["gps_per_s"],
             "unit": "GPs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["fp64"]["s_per_batch"] * 1e3, "higher_is_better": True, "scaling": "weak",

@@ -381,8 +381,37 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
         }
         bp.fpend[s] = 1;
       };
-      for (int i = 0; i < nk && i < kStages; ++i) load(i);
+      // Chunk loads are requested in order as soon as their stage is free (the MMAs of the chunk it held
+      // kStages earlier have completed), probed without blocking after each chunk's MMAs are issued, so
+      // several chunks' MMAs stay queued on the tensor pipe while copies fly; a blocking (bounded) wait
+      // only when the chunk about to be consumed has not been requested yet.
+      int next_load = 0, issued = 0;
+      auto refill = [&](bool block) -> bool {
+        while (next_load < nk) {
+          const int j = next_load, sj = j % kStages;
+          if (j >= kStages) {
+            if (j - kStages >= issued) break;  // the stage still holds an unconsumed chunk
+            if (bp.epend[sj]) {
+              if (block) {
+                if (!mbar_wait(&bp.empty[sj], bp.eph[sj], st, timeout_ns, where)) return false;
+              } else if (!mbar_try_wait(&bp.empty[sj], bp.eph[sj])) {
+                break;
+              }
+              bp.eph[sj] ^= 1u;
+              bp.epend[sj] = 0;
+            }
+          }
+          load(j);
+          ++next_load;
+          block = false;
+        }
+        return true;
+      };
       for (int i = 0; i < nk && ok; ++i) {
+        if (next_load <= i && !refill(true)) {
+          ok = false;
+          break;
+        }
         const int s = i % kStages;
         if (!mbar_wait(&bp.full[s], bp.fph[s], st, timeout_ns, where)) {
           ok = false;
@@ -430,18 +459,8 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
         }
         umma_commit(&bp.empty[s]);
         bp.epend[s] = 1;
-        if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
-          const int sp = (i - 1) % kStages, j = i - 1 + kStages;
-          if (j < nk) {
-            if (!mbar_wait(&bp.empty[sp], bp.eph[sp], st, timeout_ns, where)) {
-              ok = false;
-              break;
-            }
-            bp.eph[sp] ^= 1u;
-            bp.epend[sp] = 0;
-            load(j);
-          }
-        }
+        issued = i + 1;
+        refill(false);
       }
       // every MMA complete before TMEM is read and the stages are reused
       for (int i = 0; i < kStages; ++i) {

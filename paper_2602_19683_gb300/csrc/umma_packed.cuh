@@ -136,8 +136,35 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
       tma_bulk_g2s(base + kPkChunkBytes, pr.B[p] + pk_chunk_off(rbB, kc, Kd), kPkChunkBytes, &u.pfull[s]);
       u.fpend[s] = 1;
     };
-    for (int i = 0; i < nk && i < kPkStages; ++i) load(i);
+    // loads requested as soon as their stage is free, probed without blocking after each chunk's MMAs
+    // (several chunks' MMAs stay queued); a bounded blocking wait only for the chunk about to be consumed
+    int next_load = 0, issued = 0;
+    auto refill = [&](bool block) -> bool {
+      while (next_load < nk) {
+        const int j = next_load, sj = j % kPkStages;
+        if (j >= kPkStages) {
+          if (j - kPkStages >= issued) break;  // the stage still holds an unconsumed chunk
+          if (u.epend[sj]) {
+            if (block) {
+              if (!mbar_wait(&u.pempty[sj], u.eph[sj], st, timeout_ns, where)) return false;
+            } else if (!mbar_try_wait(&u.pempty[sj], u.eph[sj])) {
+              break;
+            }
+            u.eph[sj] ^= 1u;
+            u.epend[sj] = 0;
+          }
+        }
+        load(j);
+        ++next_load;
+        block = false;
+      }
+      return true;
+    };
     for (int i = 0; i < nk && ok; ++i) {
+      if (next_load <= i && !refill(true)) {
+        ok = false;
+        break;
+      }
       const int s = i % kPkStages;
       if (!mbar_wait(&u.pfull[s], u.fph[s], st, timeout_ns, where)) {
         ok = false;
@@ -164,18 +191,8 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
       }
       umma_commit(&u.pempty[s]);
       u.epend[s] = 1;
-      if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
-        const int sp = (i - 1) % kPkStages, j = i - 1 + kPkStages;
-        if (j < nk) {
-          if (!mbar_wait(&u.pempty[sp], u.eph[sp], st, timeout_ns, where)) {
-            ok = false;
-            break;
-          }
-          u.eph[sp] ^= 1u;
-          u.epend[sp] = 0;
-          load(j);
-        }
-      }
+      issued = i + 1;
+      refill(false);
     }
     // every MMA of the block must be complete before TMEM is read (and before the stages are reused)
     for (int i = 0; i < kPkStages; ++i) {
@@ -249,8 +266,33 @@ __device__ bool umma_pk_block2_sub(UmmaState& u, double* C0, double* C1, int ldc
       tma_bulk_g2s(base + 2 * kPkChunkBytes, pr.B[p] + pk_chunk_off(0, kc, Kd), kPkChunkBytes, &u.pfull[s]);
       u.fpend[s] = 1;
     };
-    for (int i = 0; i < nk && i < kStages2; ++i) load(i);
+    int next_load = 0, issued = 0;  // the same lazy refill as umma_pk_block_sub
+    auto refill = [&](bool block) -> bool {
+      while (next_load < nk) {
+        const int j = next_load, sj = j % kStages2;
+        if (j >= kStages2) {
+          if (j - kStages2 >= issued) break;
+          if (u.epend[sj]) {
+            if (block) {
+              if (!mbar_wait(&u.pempty[sj], u.eph[sj], st, timeout_ns, where)) return false;
+            } else if (!mbar_try_wait(&u.pempty[sj], u.eph[sj])) {
+              break;
+            }
+            u.eph[sj] ^= 1u;
+            u.epend[sj] = 0;
+          }
+        }
+        load(j);
+        ++next_load;
+        block = false;
+      }
+      return true;
+    };
     for (int i = 0; i < nk && ok; ++i) {
+      if (next_load <= i && !refill(true)) {
+        ok = false;
+        break;
+      }
       const int s = i % kStages2;
       if (!mbar_wait(&u.pfull[s], u.fph[s], st, timeout_ns, where)) {
         ok = false;
@@ -278,18 +320,8 @@ __device__ bool umma_pk_block2_sub(UmmaState& u, double* C0, double* C1, int ldc
       }
       umma_commit(&u.pempty[s]);
       u.epend[s] = 1;
-      if (i >= 1) {  // refill the stage of chunk i-1 once its MMAs are done (chunk i's are queued)
-        const int sp = (i - 1) % kStages2, j = i - 1 + kStages2;
-        if (j < nk) {
-          if (!mbar_wait(&u.pempty[sp], u.eph[sp], st, timeout_ns, where)) {
-            ok = false;
-            break;
-          }
-          u.eph[sp] ^= 1u;
-          u.epend[sp] = 0;
-          load(j);
-        }
-      }
+      issued = i + 1;
+      refill(false);
     }
     // every MMA must be complete before TMEM is read (and before the stages are reused)
     for (int i = 0; i < kStages2; ++i) {
