@@ -578,7 +578,9 @@ def run_ours(args):
                               "ffma64_tflops": v.get("ffma64", {}).get("tflops"),
                               "dmma_tflops": v.get("dmma_m8n8k4", {}).get("tflops"),
                               "ffma32_tflops": v.get("ffma32", {}).get("tflops"),
-                              "cublas_dgemm_tflops": v.get("cublas_dgemm", {}).get("tflops")}
+                              "cublas_dgemm_tflops": v.get("cublas_dgemm", {}).get("tflops"),
+                              "cublas_int8_gemm_tops": v.get("cublas_igemm_int8", {}).get("tops"),
+                              "cublas_bf16_gemm_tflops": v.get("cublas_bf16gemm", {}).get("tflops")}
         except Exception as e:  # the baseline leg must not hide the measured line
             line["vendor"] = {"error": str(e)[:200]}
     if ws > 1:
@@ -621,10 +623,11 @@ def ctx_tile(n, tile, mixed=False):
 def run_large(args):
     """The largest single GP: n = 65536 training points (K is 34 GB in FP64, 17 GB in FP32), m = 8192
     test points, D = 16 lags, in the mixed mode (FP32-class trailing updates on the tensor cores, FP64
-    POTRF / first-column TRSM / refinement of K^-1 y). Times the mixed solve (assembly + Cholesky +
-    refined mean + full covariance); then solves once in plain FP64 on the same GPU as the accuracy
-    reference (log-determinant, predictive-variance, mean and covariance errors of the mixed form), and
-    times cuSOLVER Dpotrf (64-bit API, one call) on an n x n FP64 matrix as a baseline."""
+    POTRF / first-column TRSM / refinement of K^-1 y) and in the FP64-emulating form (FP64-accurate
+    products on the BF16 tensor cores). Times both solves (assembly + Cholesky + mean + full
+    covariance); then solves once in plain FP64 on the same GPU as the accuracy reference
+    (log-determinant, predictive-variance, mean and covariance errors of both forms), and times
+    cuSOLVER Dpotrf (64-bit API, one call) on an n x n FP64 matrix as a baseline."""
     import torch
     import nfir
     from paper_2602_19683_gb300 import api
@@ -637,9 +640,9 @@ def run_large(args):
     res = {}
     outs = {}
     with torch.cuda.stream(stream):
-        for prec in ("fp32", "fp64"):
-            ctx = api.Context(0, stream=stream, tile=args.tile, precision=prec, timeout_s=900.0,
-                              locality_order=locality_arg(args))
+        for prec in ("fp32", "fp64_ozaki", "fp64"):
+            ctx = api.Context(0, stream=stream, tile=args.tile if prec == "fp64" else 0, precision=prec,
+                              timeout_s=900.0, locality_order=locality_arg(args))
             mean = torch.empty(m, dtype=torch.float64, device=dev)
             cov = torch.empty((m, m), dtype=torch.float64, device=dev)
             fac = [None]
@@ -664,8 +667,8 @@ def run_large(args):
                 api.gp_predict_full_cov(ctx, fac[0], Xsd, out=cov)
                 mark("t4")
 
-            reps = args.steps if prec == "fp32" else 1
-            for _ in range(args.warmup if prec == "fp32" else 0):
+            reps = args.steps if prec != "fp64" else 1
+            for _ in range(args.warmup if prec != "fp64" else 0):
                 solve()
             api.gp_sync(ctx)
             phases = []
@@ -686,16 +689,18 @@ def run_large(args):
             ctx.close()
             torch.cuda.synchronize(dev)
             torch.cuda.empty_cache()
-    m32, c32, ld32 = outs["fp32"]
     m64, c64, ld64 = outs["fp64"]
 
     def relerr(a, b):
         return float((a - b).abs().max() / b.abs().max())
-    res["errors_mixed_vs_fp64"] = {"logdet_rel": abs(ld32 - ld64) / abs(ld64), "logdet_fp64": ld64,
-                                   "var_rel": relerr(torch.diagonal(c32), torch.diagonal(c64)),
-                                   "mean_rel": relerr(m32, m64), "cov_rel": relerr(c32, c64)}
+    for prec, key in (("fp32", "errors_mixed_vs_fp64"), ("fp64_ozaki", "errors_emulated_vs_fp64")):
+        mx, cx, ldx = outs[prec]
+        res[key] = {"logdet_rel": abs(ldx - ld64) / abs(ld64), "logdet_fp64": ld64,
+                    "var_rel": relerr(torch.diagonal(cx), torch.diagonal(c64)),
+                    "mean_rel": relerr(mx, m64), "cov_rel": relerr(cx, c64)}
     res["speedup_mixed_vs_fp64"] = res["fp64"]["s_per_solve"] / res["fp32"]["s_per_solve"]
-    del outs, m32, c32, m64, c64, Xd, yd, Xsd
+    res["speedup_emulated_vs_fp64"] = res["fp64"]["s_per_solve"] / res["fp64_ozaki"]["s_per_solve"]
+    del outs, m64, c64, Xd, yd, Xsd
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     if not args.no_vendor:
@@ -708,7 +713,9 @@ def run_large(args):
                              "cholesky_speedup_mixed_vs_cusolver": dp.get("ms", float("nan")) / 1e3 /
                              res["fp32"]["cholesky_s"],
                              "cholesky_speedup_fp64_vs_cusolver": dp.get("ms", float("nan")) / 1e3 /
-                             res["fp64"]["cholesky_s"]}
+                             res["fp64"]["cholesky_s"],
+                             "cholesky_speedup_emulated_vs_cusolver": dp.get("ms", float("nan")) / 1e3 /
+                             res["fp64_ozaki"]["cholesky_s"]}
         except Exception as e:  # the baseline leg must not hide the measured line
             res["vendor"] = {"error": str(e)[:200]}
     line = {"metric": "GP solve (assembly+Cholesky+mean+full cov) TFLOP/s, mixed precision, n=65536",

@@ -145,6 +145,32 @@ int main(int argc, char** argv) {
     printf("{\"probe\": \"cublas_dgemm\", \"n\": %d, \"tflops\": %.4f}\n", N, 2.0 * N * N * (double)N / ms / 1e9);
     cudaFree(B);
     cudaFree(C);
+    // the tensor-core kinds an FP64 emulation could build on: INT8 (int32 accumulation) and BF16 (FP32
+    // accumulation) GEMMs of the same size, operands zero-filled (the rate, not the values, is measured)
+    void *A8, *C32;
+    CK(cudaMalloc(&A8, (size_t)N * N * 2));
+    CK(cudaMalloc(&C32, (size_t)N * N * 4));
+    CK(cudaMemset(A8, 0, (size_t)N * N * 2));
+    const int32_t ione = 1, izero = 0;
+    const float fone = 1.f, fzero = 0.f;
+    cublasStatus_t s8 = CUBLAS_STATUS_SUCCESS;
+    float ms8 = best_ms([&] {
+      s8 = cublasGemmEx(bh, CUBLAS_OP_T, CUBLAS_OP_N, N, N, N, &ione, A8, CUDA_R_8I, N, A8, CUDA_R_8I, N, &izero, C32,
+                        CUDA_R_32I, N, CUBLAS_COMPUTE_32I, CUBLAS_GEMM_DEFAULT);
+    }, 2);
+    if (s8 == CUBLAS_STATUS_SUCCESS)
+      printf("{\"probe\": \"cublas_igemm_int8\", \"n\": %d, \"tops\": %.1f}\n", N, 2.0 * N * N * (double)N / ms8 / 1e9);
+    else
+      printf("{\"probe\": \"cublas_igemm_int8\", \"n\": %d, \"status\": %d}\n", N, (int)s8);
+    cublasStatus_t sb = CUBLAS_STATUS_SUCCESS;
+    float msb = best_ms([&] {
+      sb = cublasGemmEx(bh, CUBLAS_OP_T, CUBLAS_OP_N, N, N, N, &fone, A8, CUDA_R_16BF, N, A8, CUDA_R_16BF, N, &fzero,
+                        C32, CUDA_R_32F, N, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    }, 2);
+    if (sb == CUBLAS_STATUS_SUCCESS)
+      printf("{\"probe\": \"cublas_bf16gemm\", \"n\": %d, \"tflops\": %.1f}\n", N, 2.0 * N * N * (double)N / msb / 1e9);
+    cudaFree(A8);
+    cudaFree(C32);
   }
   fflush(stdout);
   if (potrf) {
