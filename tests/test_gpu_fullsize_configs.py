@@ -100,6 +100,12 @@ def check_nlml_gradient(api, to_dev, n, D):
     theta = np.array([1.0, 1.0, 0.1])
     nl, g = api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*theta))
     g = np.array(g)
+    # the NLML value against the oracle at this size (its tiled factor of Sec. 3.2 and the solves of
+    # Eq. 2; the oracle's K^{-1}-based gradient is O(n^3) with strided access, too slow here)
+    L = oracle.cholesky_tiled(oracle.assemble_K(X, Hyper(*theta)), 256)
+    alpha, _ = oracle.predict_mean(L, y, np.zeros((0, n)))
+    nl_ref = oracle.nlml(L, y, alpha)
+    assert abs(nl - nl_ref) <= 1e-12 * abs(nl_ref), (nl, nl_ref)
     for k in range(3):
         h = 1e-5 * theta[k]
         tp, tm = theta.copy(), theta.copy()
