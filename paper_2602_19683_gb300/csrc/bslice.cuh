@@ -394,7 +394,7 @@ __device__ bool bs_block_sub(UmmaState& u, BsPipe& bp, double* C, int ldc, const
             if (bp.epend[sj]) {
               if (block) {
                 if (!mbar_wait(&bp.empty[sj], bp.eph[sj], st, timeout_ns, where)) return false;
-              } else if (!mbar_try_wait(&bp.empty[sj], bp.eph[sj])) {
+              } else if (!mbar_test_wait(&bp.empty[sj], bp.eph[sj])) {
                 break;
               }
               bp.eph[sj] ^= 1u;

@@ -147,7 +147,7 @@ __device__ bool umma_pk_block_sub(UmmaState& u, double* C, int ldc, const PkPair
           if (u.epend[sj]) {
             if (block) {
               if (!mbar_wait(&u.pempty[sj], u.eph[sj], st, timeout_ns, where)) return false;
-            } else if (!mbar_try_wait(&u.pempty[sj], u.eph[sj])) {
+            } else if (!mbar_test_wait(&u.pempty[sj], u.eph[sj])) {
               break;
             }
             u.eph[sj] ^= 1u;
@@ -275,7 +275,7 @@ __device__ bool umma_pk_block2_sub(UmmaState& u, double* C0, double* C1, int ldc
           if (u.epend[sj]) {
             if (block) {
               if (!mbar_wait(&u.pempty[sj], u.eph[sj], st, timeout_ns, where)) return false;
-            } else if (!mbar_try_wait(&u.pempty[sj], u.eph[sj])) {
+            } else if (!mbar_test_wait(&u.pempty[sj], u.eph[sj])) {
               break;
             }
             u.eph[sj] ^= 1u;
