@@ -735,9 +735,11 @@ def vendor_gp_loop(torch, gps, ref_means, args):
     (torch.linalg.solve_triangular), the mean and W by cuBLAS gemm. FP64. Returns its GPs/s and its
     largest mean difference from the library's FP64 batch."""
     def solve(X, y, Xs, h):
+        l, v, s2 = h
+
         def k(A, B):
-            return h.v * torch.exp(-torch.cdist(A, B).square() / (2.0 * h.l * h.l))
-        K = k(X, X) + h.s2 * torch.eye(X.shape[0], dtype=X.dtype, device=X.device)
+            return v * torch.exp(-torch.cdist(A, B).square() / (2.0 * l * l))
+        K = k(X, X) + s2 * torch.eye(X.shape[0], dtype=X.dtype, device=X.device)
         L = torch.linalg.cholesky(K)
         Kxs = k(X, Xs)
         alpha = torch.cholesky_solve(y[:, None], L)

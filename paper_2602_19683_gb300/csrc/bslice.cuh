@@ -53,6 +53,8 @@ constexpr int kOzLsbBounded = 56;   // fixed-point sum unit 2^-56 S_A S_B: opera
 constexpr int kOzLsbTile = 52;      // 2^-52 S_A S_B: max-scaled operands of one 128-wide tile product
 static_assert(kBsStageMem + 1024 <= kUmmaSmemBytes, "slice stages must fit the dynamic smem");
 static_assert(kOzLevels * 64 <= kUmmaTmemCols, "seven 64-column level accumulators must fit TMEM");
+static_assert(128 * 129 * 8 + 10 * 1024 * 8 + 1024 <= kUmmaSmemBytes,
+              "the factored 128 tile and the blocks of its FP64 inverse must fit the dynamic smem");
 
 // Byte offset of BF16 element (r, k) (k < kKC) in a K-major swizzled slice: rows of 2 kKC bytes in
 // 8-row groups; the 16-byte unit u of row r is stored at u ^ ((r >> 1) & 3) (64-byte swizzle, kKC = 32)
@@ -328,6 +330,80 @@ __device__ void oz_epilogue(UmmaState& u, double* C, int ldc, int m0, int n0, bo
     *c2 = c;
   }
   __syncthreads();  // smem and TMEM are reused next
+}
+
+// X = L^{-1} in FP64 for a factored nb x nb diagonal tile still held in shared memory by the POTRF
+// (sL: nb x (nb + 1) doubles at the start of `smem`, lower triangle; nb a multiple of 32, at most 128),
+// written to Xg (nb x nb row-major, upper triangle zero). Blocked by 32: warp d inverts diagonal block d
+// (lane j solves column j, the pivots' reciprocals taken once and shared by shuffles), then block rows
+// bi = 1.. follow X_{bi,bj} = -X_{bi,bi} sum_{bj <= k < bi} L_{bi,k} X_{k,bj}. The lower blocks of X live
+// in shared memory behind the factor (10 blocks of 32 x 32 doubles for nb = 128).
+__device__ __noinline__ void cta_inverse_f64_smem(uint8_t* smem, int nb, double* Xg) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31, ldl = nb + 1, nblk = nb / 32;
+  const double* sL = reinterpret_cast<const double*>(smem);
+  double* sX = reinterpret_cast<double*>(smem + (size_t)nb * ldl * 8);
+  auto xblk = [&](int bi, int bj) { return sX + (size_t)(bi * (bi + 1) / 2 + bj) * 1024; };
+  if (w < nblk) {  // diagonal blocks
+    const int d0 = 32 * w;
+    const double rd = 1.0 / sL[(d0 + lane) * ldl + d0 + lane];
+    double x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      double acc = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc = fma(-sL[(d0 + i) * ldl + d0 + k], x[k], acc);
+      x[i] = acc * __shfl_sync(0xffffffffu, rd, i);
+    }
+    double* X = xblk(w, w);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) X[i * 32 + lane] = x[i];
+  }
+  __syncthreads();
+  for (int bi = 1; bi < nblk; ++bi) {
+    // W_bj = sum_{bj <= k < bi} L_{bi,k} X_{k,bj}, parked in the (unused) slots of X_{bi,bj}
+    for (int e = t; e < bi * 1024; e += kThreads) {
+      const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+      const double* lrow = sL + (32 * bi + r) * ldl;
+      double acc = 0.0;
+      for (int kb = bj; kb < bi; ++kb) {
+        const double* Xk = xblk(kb, bj);
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) acc = fma(lrow[32 * kb + kk], Xk[kk * 32 + c], acc);
+      }
+      xblk(bi, bj)[r * 32 + c] = acc;
+    }
+    __syncthreads();
+    // X_{bi,bj} = -X_{bi,bi} W_bj (through registers: W is read in place)
+    double res[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * kThreads;
+      res[q] = 0.0;
+      if (e < bi * 1024) {
+        const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        const double* xrow = xblk(bi, bi) + r * 32;
+        const double* Wb = xblk(bi, bj);
+        double acc = 0.0;
+        for (int k = 0; k <= r; ++k) acc = fma(xrow[k], Wb[k * 32 + c], acc);
+        res[q] = -acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * kThreads;
+      if (e < bi * 1024) {
+        const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        xblk(bi, bj)[r * 32 + c] = res[q];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < nb * nb; e += kThreads) {  // coalesced write-out, zero above the diagonal
+    const int i = e / nb, j = e % nb, bi = i >> 5, bj = j >> 5;
+    Xg[e] = bj <= bi ? xblk(bi, bj)[(i & 31) * 32 + (j & 31)] : 0.0;
+  }
+  __syncthreads();
 }
 
 // Pipeline state of the slice products (barriers in smem; thread 0 drives it).

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, kMixed ? 1 : 2) dag_kernel(DagArgs a
             // digits at its own scale for the column's TRSMs and V solves
             __syncthreads();
             double* Li = a.Linv + (size_t)p * TT;
-            cta_trtri(a.Kt + tri(p, p) * TT, T, Li, T, s);
+            cta_inverse_f64_smem(um.smem, T, Li);  // from the factor left in shared memory
             const int e = cta_scale_exp(Li, T, T, T, &s_flag);
             if (threadIdx.x == 0) a.PLinvExp[p] = e;
             form_pack(a.prec, Li, T, false, T, T, dst, e);
