@@ -373,10 +373,13 @@ __device__ __noinline__ void cta_inverse_f64_smem(uint8_t* smem, int nb, double*
       xblk(bi, bj)[r * 32 + c] = acc;
     }
     __syncthreads();
-    // X_{bi,bj} = -X_{bi,bi} W_bj (through registers: W is read in place)
-    double res[4];
+    // X_{bi,bj} = -X_{bi,bi} W_bj (through registers: W is read in place); bi * 1024 <= 3 * 1024 entries,
+    // twelve per thread
+    constexpr int kPer = 3 * 1024 / kThreads;
+    static_assert(kPer * kThreads == 3 * 1024, "the entries of block row 3 split evenly over the CTA");
+    double res[kPer];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kPer; ++q) {
       const int e = t + q * kThreads;
       res[q] = 0.0;
       if (e < bi * 1024) {
@@ -390,7 +393,7 @@ __device__ __noinline__ void cta_inverse_f64_smem(uint8_t* smem, int nb, double*
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kPer; ++q) {
       const int e = t + q * kThreads;
       if (e < bi * 1024) {
         const int bj = e >> 10, r = (e >> 5) & 31, c = e & 31;
