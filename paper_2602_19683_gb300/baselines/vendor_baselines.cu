@@ -65,6 +65,34 @@ __global__ void dmma_loop(double* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// FP64 FFMA in the warps of one half of each CTA and FP64 mma.sync in the other, at the same time:
+// whether the two issue to separate FP64 units (their rates would add) or share one.
+__global__ void mixed_fp64_loop(double* out, int iters_ffma, int iters_dmma, double a, double b) {
+  const int w = threadIdx.x >> 5;
+  double s = 0;
+  if (w & 1) {
+    double x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = threadIdx.x + j;
+    for (int i = 0; i < iters_ffma; ++i)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = fma(x[j], a, b);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s += x[j];
+  } else {
+    double c[8][2];
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = 0;
+    for (int i = 0; i < iters_dmma; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(c[j][0]), "+d"(c[j][1])
+                     : "d"(a), "d"(b));
+    for (int j = 0; j < 8; ++j) s += c[j][0] + c[j][1];
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // A = exp(-((i-j)/64)^2) + 0.1 I: symmetric positive definite.
 __global__ void fill_spd(double* A, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * n; e += (long long)gridDim.x * blockDim.x) {
@@ -128,6 +156,13 @@ int main(int argc, char** argv) {
     const int grid = sms * 4, iters = 400;
     float ms = best_ms([&] { dmma_loop<<<grid, 256>>>(out, iters); }, 3);
     printf("{\"probe\": \"dmma_m8n8k4\", \"tflops\": %.4f}\n", 2.0 * 256 * 8 * iters * (double)grid * 8 / ms / 1e9);
+  }
+  if (probes) {  // FFMA and DMMA issued together (half the warps each); flops of both counted
+    const int grid = sms * 4, it_f = 2000, it_d = 200;
+    float ms = best_ms([&] { mixed_fp64_loop<<<grid, 256>>>(out, it_f, it_d, 0.999, 1e-3); }, 3);
+    const double ffma = 2.0 * 16 * it_f * (double)grid * 128, dmma = 2.0 * 256 * 8 * it_d * (double)grid * 4;
+    printf("{\"probe\": \"ffma64_and_dmma\", \"tflops\": %.4f, \"ffma_share\": %.3f}\n", (ffma + dmma) / ms / 1e9,
+           ffma / (ffma + dmma));
   }
   fflush(stdout);
   double* A;

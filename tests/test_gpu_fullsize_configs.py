@@ -159,6 +159,42 @@ def test_nlml_gradient_full_size(api):
 
 
 @pytest.mark.gpu
+def test_emulated_fp64_matches_native_fp64_at_the_benchmark_size(api):
+    """The benchmark workload (n = 32768, m = 4096, D = 8) solved twice with independent arithmetic: the
+    FP64 FFMA path (checked against the oracle element-wise at n = 8192 and by sampled rows here) and
+    the FP64 emulated from BF16 digit products on the tensor cores. They must agree at the FP64 bars:
+    mean 1e-10, covariance 1e-9, log-determinant 1e-12 (relative), and the emulated factor must
+    reconstruct sampled rows of K to FP64 accuracy."""
+    n, m, D = 32768, 4096, 8
+    X, y, Xs, _ = nfir.make_dataset(n, m, D, 0)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    out = {}
+    for prec in ("fp64", "fp64_ozaki"):
+        ctx = api.Context(0, precision=prec, timeout_s=120)
+        f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+        api.gp_cholesky(ctx, f)
+        mean = api.gp_predict_mean(ctx, f, yd, Xsd)
+        cov = api.gp_predict_full_cov(ctx, f, Xsd)
+        logdet = api.gp_logdet(ctx, f)
+        Lrows = np.stack([api.gp_factor_rows(ctx, f, r, 1).cpu().numpy()[0] for r in (0, 1, 8191, 16384, 24577, n - 1)])
+        api.gp_sync(ctx)
+        out[prec] = (mean.cpu().numpy(), cov.cpu().numpy(), logdet, Lrows)
+        f.free()
+        ctx.close()
+        torch.cuda.empty_cache()
+    m64, c64, ld64, _ = out["fp64"]
+    mo, co, ldo, Lo = out["fp64_ozaki"]
+    em, ec, el = rel(mo, m64), rel(co, c64), abs(ldo - ld64) / abs(ld64)
+    print(f"emulated vs native FP64 at n={n}: mean {em:.2e} cov {ec:.2e} logdet {el:.2e}")
+    assert em <= 1e-10 and ec <= 1e-9 and el <= 1e-12
+    # sampled rows of the emulated factor: (L L^T)_{r, r'} on the sampled rows against K from the oracle
+    rows = np.array([0, 1, 8191, 16384, 24577, n - 1])
+    ii, jj = np.meshgrid(np.arange(len(rows)), np.arange(len(rows)), indexing="ij")
+    Kij = oracle.kernel_entries(X, X, rows[ii.ravel()], rows[jj.ravel()], rows[ii.ravel()] == rows[jj.ravel()], H0)
+    assert rel((Lo @ Lo.T).ravel(), Kij) <= 1e-13
+
+
+@pytest.mark.gpu
 def test_batch_512_uneven_gps(api):
     check_batch(api, to_dev, 512, 256, 4096)
 
