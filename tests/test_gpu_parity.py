@@ -79,7 +79,7 @@ def test_fp64_pipeline_matches_oracle(api, n, m, D, T, h, seed):
     f.free()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64_ozaki", "bf16x6"])
 def test_variance_only_matches_covariance_diagonal(api, precision):
     """gp_predict_var = diag of Eq. (3) (oracle), without forming V^T V."""
     X, y, Xs, _ = nfir.make_dataset(900, 150, 8, 13)
@@ -90,7 +90,7 @@ def test_variance_only_matches_covariance_diagonal(api, precision):
     api.gp_cholesky(ctx, f)
     var = api.gp_predict_var(ctx, f, Xsd).cpu().numpy()
     api.gp_sync(ctx)
-    assert rel(var, np.diag(ref["cov"])) <= (1e-9 if precision == "fp64" else 1e-4)
+    assert rel(var, np.diag(ref["cov"])) <= (1e-9 if precision in ("fp64", "fp64_ozaki") else 1e-4)
 
 
 def test_noisy_prior_adds_s2(api):
