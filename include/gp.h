@@ -93,11 +93,14 @@ typedef struct {
   int32_t ir_maxit;       /* refinement iteration limit (0 = 10)                                      */
   int32_t noisy_prior;    /* 1: K_{Xs,Xs} includes s2 on its diagonal (noisy-target covariance)       */
   int64_t timeout_ns;     /* bound on any single device-side wait (0 = 60 s)                          */
-  int32_t grid;           /* persistent-kernel CTAs (0 = as many as fit, up to two per SM)            */
-  int32_t withhold_task;  /* TEST HOOK, read only when withhold_enable != 0: the persistent-kernel
-                             task with this index (in dispatch order) is skipped and never publishes
-                             its completion, so the bounded waits of the tasks that depend on it expire
-                             and the call ends with GP_ERR_TIMEOUT. Leave both fields 0.              */
+  int32_t grid;           /* persistent-kernel CTAs (0 = as many as fit, up to two per SM; the mean's
+                             triangular-solve kernel takes one per SM at most)                        */
+  int32_t withhold_task;  /* TEST HOOK, read only when withhold_enable != 0. withhold_enable = 1: the
+                             persistent-kernel task with this index (in dispatch order) is skipped and
+                             never publishes its completion; = 2: the mean solve's forward block with
+                             this index is computed but never published. Either way the bounded waits
+                             that depend on it expire and the call ends with GP_ERR_TIMEOUT. Leave both
+                             fields 0.                                                                */
   int32_t withhold_enable;
   int32_t tensor_cores;   /* GP_FP32 trailing updates: 0 = tensor cores (tcgen05, 3xTF32 split products)
                              when the tile edge is a multiple of 128, -1 = FP32 FMA pipes only       */
@@ -187,6 +190,14 @@ gp_status gp_factor_stats(gp_ctx* ctx, const gp_factor* f, double out[4]);
 
 /* Copies alpha = K^{-1} y from the last gp_predict_mean on the factor to out (device, n). */
 gp_status gp_alpha(gp_ctx* ctx, const gp_factor* f, double* out);
+
+/* x = (L L^T)^{-1} b with the stored factor L (of K, or of K + shift I for the single-product forms), by
+ * the two blocked substitutions of Eq. 2 and no refinement: b, x device arrays of n doubles (they may be
+ * the same array). GP_FP64 and GP_FP64_OZAKI solve in FP64; the refined forms (FP32-accurate factors)
+ * solve with the factor's FP32 copy in FP32 arithmetic at tile edges 128 and 256 (their correction
+ * solves), in FP64 at other tile edges. Asynchronous; a device wait that expires is reported by gp_sync
+ * as GP_ERR_TIMEOUT. GP_ERR_INVALID_ARG before gp_cholesky. */
+gp_status gp_solve(gp_ctx* ctx, gp_factor* f, const double* b, double* x);
 
 gp_status gp_factor_free(gp_ctx* ctx, gp_factor* f);
 

@@ -55,7 +55,7 @@ class Context:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, tile: int = 0,
                  precision: str = "fp64", ir_tol: float = 0.0, ir_maxit: int = 0, noisy_prior: bool = False,
                  timeout_s: float = 0.0, grid: int = 0, withhold_task: int | None = None,
-                 tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0,
+                 withhold_solve_block: int | None = None, tensor_cores: bool = True, trace: bool = False, batch_order: int = 0, batch_ctas_per_sm: int = 0,
                  locality_order: bool | None = None, shift: float = 0.0, tile_variant: str = "right"):
         self.lib = N.load()
         self.precision = precision
@@ -79,6 +79,9 @@ class Context:
         if withhold_task is not None:  # test hook: never publish this task's completion
             cfg.withhold_task = withhold_task
             cfg.withhold_enable = 1
+        elif withhold_solve_block is not None:  # test hook: never publish this forward block of the mean solve
+            cfg.withhold_task = withhold_solve_block
+            cfg.withhold_enable = 2
         h = ctypes.c_void_p()
         _check(self.lib.gp_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(cfg)),
                "gp_create")
@@ -218,6 +221,17 @@ def gp_factor_rows(ctx: Context, f: Factor, row0: int = 0, nrows: int | None = N
 def gp_alpha(ctx: Context, f: Factor) -> torch.Tensor:
     out = torch.empty(f.n, dtype=torch.float64, device=ctx.device)
     _check(ctx.lib.gp_alpha(ctx.h, f.h, out.data_ptr()), "gp_alpha")
+    return out
+
+
+def gp_solve(ctx: Context, f: Factor, b: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """x = (L L^T)^{-1} b with the stored factor, no refinement (FP32 arithmetic for the refined forms at
+    tile edges 128 and 256, FP64 otherwise). Asynchronous: errors are reported by gp_sync."""
+    _dev(b, "b", (f.n,))
+    if out is None:
+        out = torch.empty(f.n, dtype=torch.float64, device=b.device)
+    _dev(out, "out", (f.n,))
+    _check(ctx.lib.gp_solve(ctx.h, f.h, b.data_ptr(), out.data_ptr()), "gp_solve")
     return out
 
 

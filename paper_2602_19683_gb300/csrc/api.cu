@@ -88,6 +88,7 @@ struct gp_ctx {
   std::map<TaskKey, TaskBuf> tasks;
   gp_factor* grad_factor = nullptr;  // reused by gp_nlml_grad across calls of the same size
   DevBuf trace;                      // per-task timing records of the last launch (cfg.trace)
+  DevBuf trace_items;                // task records written by the mean-solve kernel (cfg.trace)
   DevBuf debug_work;                 // packed operands of gp_debug_tile_product
   const void* trace_tasks = nullptr; // its task list (device)
   int trace_ntasks = 0;
@@ -120,6 +121,9 @@ struct gp_factor {
                                   // sums, counters, L^{-1} y
   DevBuf V, S, cCov;          // covariance workspace
   DevBuf gV, gzero, gh;       // GMRES refinement: Krylov basis, a zero vector, Hessenberg column scratch
+  DevBuf Lt32, Linv32;        // refined forms, T = 128 / 256: FP32 copies of the factor tiles and inverses
+                              // (the correction solves' operands)
+  bool has32 = false;         // Lt32 / Linv32 hold the current factor
   bool factored = false, alpha_valid = false;
   double ir_eta = 0.0;        // backward error reached by the last refinement
   int ir_iters = 0;           // refinement steps (GMRES: preconditioned matrix-vector products) of the last solve
@@ -240,7 +244,7 @@ gpk::DagArgs base_args(gp_ctx* c, gp_factor* f) {
   a.cK = (int*)f->cK.p;
   a.st = c->d_status;
   a.timeout_ns = c->cfg.timeout_ns;
-  a.withhold_task = c->cfg.withhold_enable ? c->cfg.withhold_task : -1;
+  a.withhold_task = c->cfg.withhold_enable == 1 ? c->cfg.withhold_task : -1;
   a.use_umma = (is_mixed(f->precision) && c->cfg.tensor_cores >= 0) ? 1 : 0;
   a.prec = f->precision;
   a.pkb = pk_bytes(f->precision);
@@ -274,14 +278,40 @@ gp_status run_dag(gp_ctx* c, gpk::DagArgs a, const TaskBuf* tb, bool mixed) {
   return GP_OK;
 }
 
-// Mean-solve DAG (L beta = b, L^T x = beta) on f->bvec in place; FP64 arithmetic in both modes.
+// Mean solve (L beta = b, L^T x = beta) on f->bvec in place. The refined precision forms, whose factor is
+// FP32-accurate, solve with its FP32 copy in FP32 arithmetic (trsv.cu) whenever that copy exists; every
+// other solve runs in FP64 on the persistent DAG kernel (chunked vector tasks), whose FP64 pipe bound is
+// shared by any FP64 formulation of it.
 gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
   const int T = f->T, Mt = f->Mt, nch = T / 32;
   const size_t ncnt = (size_t)Mt * nch * 2 + (size_t)Mt * 2;
+  GP_TRY(grow(f->xvec, (size_t)Mt * T * sizeof(double)));
+  const int ctas = c->cfg.grid > 0 && c->cfg.grid < c->sms ? c->cfg.grid : c->sms;  // one per SM at most
+  int stages = 0;
+  if (f->has32 && gpk::trsv32_smem_bytes(T, Mt, ctas, &stages) > 0) {
+    GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, 2 * sizeof(int), c->stream));
+    const int withhold = c->cfg.withhold_enable == 2 ? c->cfg.withhold_task : -1;
+    long long* trace = nullptr;
+    int4* items = nullptr;
+    if (c->cfg.trace) {
+      const size_t nitems = (size_t)Mt * (Mt + 1);
+      GP_TRY(grow(c->trace, nitems * 4 * sizeof(long long)));
+      GP_TRY(grow(c->trace_items, nitems * sizeof(int4)));
+      GP_CUDA(cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), c->stream));
+      trace = (long long*)c->trace.p;
+      items = (int4*)c->trace_items.p;
+      c->trace_tasks = c->trace_items.p;
+      c->trace_ntasks = (int)nitems;
+    }
+    GP_CUDA(gpk::launch_trsv32((const float*)f->Lt32.p, (const float*)f->Linv32.p, (double*)f->bvec.p,
+                               (double*)f->xvec.p, (int*)f->cMean.p, T, Mt, ctas, c->d_status, c->cfg.timeout_ns,
+                               withhold, trace, items, c->stream));
+    count_launch(c);
+    return GP_OK;
+  }
   GP_CUDA(cudaMemsetAsync(f->cMean.p, 0, ncnt * sizeof(int), c->stream));
   const TaskBuf* tb;
   GP_TRY(get_tasks(c, 2, Mt, 0, T, GP_FP64, &tb));
-  GP_TRY(grow(f->xvec, (size_t)Mt * T * sizeof(double)));
   gpk::DagArgs a = base_args(c, f);
   a.bvec = (double*)f->bvec.p;
   a.xvec = (double*)f->xvec.p;
@@ -516,6 +546,7 @@ gp_status gp_destroy(gp_ctx* c) {
   if (c->grad_factor) gp_factor_free(c, c->grad_factor);
   for (auto& kv : c->tasks) release(kv.second.buf);
   release(c->trace);
+  release(c->trace_items);
   release(c->debug_work);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalar) cudaFree(c->d_scalar);
@@ -642,6 +673,12 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->Pk);
   release(f->PV);
   release(f->PLinv);
+  release(f->PLinvExp);
+  release(f->gV);
+  release(f->gzero);
+  release(f->gh);
+  release(f->Lt32);
+  release(f->Linv32);
   release(f->V);
   release(f->S);
   release(f->cCov);
@@ -704,6 +741,24 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   return GP_OK;
 }
 
+namespace {
+// The refined forms' correction solves read an FP32 copy of the factor (tile edges 128 and 256): made once
+// per factorisation, on the stream after the factorisation.
+gp_status make_f32_copy(gp_ctx* c, gp_factor* f) {
+  f->has32 = false;
+  if (!refines(f->precision) || (f->T != 128 && f->T != 256)) return GP_OK;
+  const size_t TT = (size_t)f->T * f->T, ntiles = (size_t)f->Mt * (f->Mt + 1) / 2;
+  GP_TRY(grow(f->Lt32, ntiles * TT * sizeof(float)));
+  GP_TRY(grow(f->Linv32, (size_t)f->Mt * TT * sizeof(float)));
+  GP_CUDA(gpk::launch_to_f32((const double*)f->Kt.p, (float*)f->Lt32.p, (long long)(ntiles * TT), c->sms, c->stream));
+  GP_CUDA(gpk::launch_to_f32((const double*)f->Linv.p, (float*)f->Linv32.p, (long long)(f->Mt * TT), c->sms,
+                             c->stream));
+  count_launch(c, 2);
+  f->has32 = true;
+  return GP_OK;
+}
+}  // namespace
+
 gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   if (!c || !f || !f->Kt.p) return GP_ERR_INVALID_ARG;
   if (f->factored) return GP_ERR_INVALID_ARG;  // already holds L
@@ -724,6 +779,7 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   if (packed_operands(c, f) && f->T == 128) a.PLinv = (uint8_t*)f->PLinv.p;
   if (!single_product(f->precision)) {
     GP_TRY(run_dag(c, a, tb, mixed));
+    GP_TRY(make_f32_copy(c, f));
     f->factored = true;
     return GP_OK;
   }
@@ -752,6 +808,7 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
     tau *= 8.0;
   }
   f->shift = tau;
+  GP_TRY(make_f32_copy(c, f));
   f->factored = true;
   return GP_OK;
 }
@@ -946,6 +1003,20 @@ gp_status gp_alpha(gp_ctx* c, const gp_factor* f, double* out) {
   if (!c || !f || !out || !f->alpha_valid) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   GP_CUDA(cudaMemcpyAsync(out, f->alpha.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return GP_OK;
+}
+
+gp_status gp_solve(gp_ctx* c, gp_factor* f, const double* b, double* x) {
+  if (!c || !f || !b || !x || !f->factored) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  const int T = f->T, Mt = f->Mt, nch = T / 32;
+  const size_t npad = (size_t)Mt * T;
+  GP_TRY(grow(f->bvec, npad * sizeof(double)));
+  GP_TRY(grow(f->cMean, ((size_t)Mt * nch * 2 + (size_t)Mt * 2) * sizeof(int)));
+  GP_CUDA(cudaMemsetAsync(f->bvec.p, 0, npad * sizeof(double), c->stream));
+  GP_CUDA(cudaMemcpyAsync(f->bvec.p, b, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  GP_TRY(solve_in_place(c, f));
+  GP_CUDA(cudaMemcpyAsync(x, f->bvec.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   return GP_OK;
 }
 

@@ -133,6 +133,21 @@ cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long lo
 cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long row0, long long nrows, double* out,
                                cudaStream_t st);
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st);
+// Blocked triangular solves with the factor in FP32 (trsv.cu), the correction solves of the refined
+// precision forms: b <- L^{-T} L^{-1} b on the packed lower FP32 tiles Lt (edge T = 128 or 256, Mt tile rows)
+// with the FP32 diagonal-tile inverses Linv; b (FP64) holds the right-hand side on entry and the solution
+// on exit, xb (FP64) receives the forward result; front (2 ints) must be zero on entry. One persistent
+// CTA per SM (grid, capped at Mt). withhold >= 0: test hook, that forward block is never published (its
+// dependants' bounded waits expire with GP_ERR_TIMEOUT). trace (optional, Mt(Mt+1) items): per item
+// {CTA, start, ready, done} times and {kind, I, J, 0}, the layout of the persistent kernel's trace; the
+// slot counter is st->next_task (zero on entry). trsv32_smem_bytes returns the dynamic shared memory of a
+// launch (and its stages), or -1 when the solve does not fit this kernel (T, or too many tile rows per CTA).
+int trsv32_smem_bytes(int T, int Mt, int grid, int* stages);
+cudaError_t launch_trsv32(const float* Lt, const float* Linv, double* b, double* xb, int* front, int T, int Mt,
+                          int grid, DevStatus* st, long long timeout_ns, int withhold, long long* trace,
+                          int4* trace_items, cudaStream_t stream);
+// dst[i] = (float)src[i] for i < n (the FP32 copy of the factor and of its diagonal-tile inverses).
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, int sms, cudaStream_t stream);
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,
                        bool batch = false);
 int dag_max_ctas_per_sm_batch(bool mixed, int use_umma);

@@ -1,5 +1,5 @@
 // Tensor-core (tcgen05) primitives of the mixed-precision mode and its FP32-in-TMEM epilogue:
-// TMEM allocation, mbarriers with bounded waits, shared-memory matrix and instruction descriptors,
+// TMEM allocation, shared-memory matrix and instruction descriptors (mbarriers and bulk copies: bulk.cuh),
 // the kind::tf32 MMA and its commit, and tcgen05.ld of the accumulator.
 //
 // The mixed trailing updates form C (FP64) -= A B^T from three TF32 split products (3xTF32:
@@ -18,6 +18,7 @@
 // Every mbarrier wait is bounded by the task's time limit; a wait that gives up reports
 // GP_ERR_TIMEOUT and the caller returns after freeing its TMEM.
 #pragma once
+#include "bulk.cuh"
 #include "tiles_f32.cuh"
 
 namespace gpk {
@@ -38,8 +39,6 @@ static_assert(kUmmaSmemBytes >= kPkStages * kUmmaStageBytes + 1024 && kUmmaSmemB
 // the whole tensor memory of the SM, which holds one CTA of the mixed kernel (shared memory bound)
 constexpr int kUmmaTmemCols = 512;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, int ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                "r"(ncols));
@@ -50,48 +49,8 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Non-blocking probe (test_wait: unlike try_wait it never suspends the thread) of a phase's completion.
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity to complete. False on time-out / abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, long long timeout_ns,
-                                          long long where) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((long long)(globaltimer() - t0) > timeout_ns) {
-      raise_error(st, GP_ERR_TIMEOUT, where);
-      return false;
-    }
-  }
-}
 __device__ __forceinline__ void umma_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void umma_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {

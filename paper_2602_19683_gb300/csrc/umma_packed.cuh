@@ -35,24 +35,6 @@ __device__ __forceinline__ size_t pk_chunk_off(int rb, int kc, int Kd) {
   return ((size_t)rb * (Kd / kUmmaKChunk) + kc) * kPkChunkBytes;
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// One bulk copy global -> shared (this CTA), completion signalled on bar as transaction bytes. Both
-// addresses 16-byte aligned, bytes a multiple of 16 (chunks are 32 KB at 32 KB offsets).
-__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // Writes the packed operand of an R x Kd FP64 block: Op[r][k] = src[r * ld + k] (trans = false) or
 // src[k * ld + r] (trans = true). R a multiple of 128, Kd of 32. Loads are coalesced in both forms;
 // stores of the transposed form are one 128-byte packed row per warp instruction.
