@@ -580,7 +580,9 @@ def run_ours(args):
                               "ffma32_tflops": v.get("ffma32", {}).get("tflops"),
                               "cublas_dgemm_tflops": v.get("cublas_dgemm", {}).get("tflops"),
                               "cublas_int8_gemm_tops": v.get("cublas_igemm_int8", {}).get("tops"),
-                              "cublas_bf16_gemm_tflops": v.get("cublas_bf16gemm", {}).get("tflops")}
+                              "cublas_bf16_gemm_tflops": v.get("cublas_bf16gemm", {}).get("tflops"),
+                              "stream_gpu_gbs": {k: v.get("stream_gpu", {}).get(k + "_gbs")
+                                                 for k in ("fp64_consumer", "fp32_consumer", "bulk64k_fp32_consumer")}}
         except Exception as e:  # the baseline leg must not hide the measured line
             line["vendor"] = {"error": str(e)[:200]}
     if ws > 1:
@@ -608,8 +610,38 @@ def traced_cholesky(api, local, Xd, h, args):
         sel = rows[(rows[:, 0] & 31) == k]
         out[api.TASK_NAMES[k]] = {"count": int(len(sel)), "run_us": float(((sel[:, 7] - sel[:, 6]) / 1e3).mean()),
                                   "wait_us": float(((sel[:, 6] - sel[:, 5]) / 1e3).mean())}
+    if args.precision not in ("fp64", "fp64_ozaki"):
+        out["fp32_solve"] = traced_solve(api, ctx, f, np)
     f.free()
     ctx.close()
+    return out
+
+
+def traced_solve(api, ctx, f, np):
+    """One FP32 correction solve (the refined forms' L^-T L^-1 r) with the per-item trace: per item kind
+    count and mean wait/run, the two sweeps' spans and the dependency chain's step times (between
+    consecutive diagonal blocks of the forward sweep)."""
+    import torch
+    b = torch.ones(f.n, dtype=torch.float64, device=ctx.device)
+    api.gp_solve(ctx, f, b)
+    api.gp_sync(ctx)
+    rows = api.gp_trace(ctx)
+    out = {}
+    for k in np.unique(rows[:, 0]):
+        sel = rows[rows[:, 0] == k]
+        out[api.TASK_NAMES[k]] = {"count": int(len(sel)), "run_us": float(((sel[:, 7] - sel[:, 6]) / 1e3).mean()),
+                                  "wait_us": float(((sel[:, 6] - sel[:, 5]) / 1e3).mean())}
+    fs = rows[rows[:, 0] == 6]
+    fs = fs[np.argsort(fs[:, 1])]
+    bs = rows[rows[:, 0] == 8]
+    if len(fs) == 0 or len(bs) == 0:  # tile edge outside the FP32 solve kernel: the FP64 DAG solve ran
+        return out
+    steps = np.diff(fs[:, 7]) / 1e3
+    out["forward_ms"] = float((fs[-1, 7] - rows[:, 5].min()) / 1e6)
+    out["backward_ms"] = float((bs[:, 7].max() - fs[-1, 7]) / 1e6)
+    if len(steps):
+        out["chain_step_us"] = {"p50": float(np.median(steps)), "p90": float(np.percentile(steps, 90)),
+                                "mean": float(steps.mean())}
     return out
 
 

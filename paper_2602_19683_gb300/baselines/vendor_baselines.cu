@@ -1,7 +1,10 @@
 // Vendor baselines and pipe-throughput probes on the same GPU (never on libgp's product path):
 //   cuSOLVER Dpotrf / Spotrf on an n x n SPD matrix (the single-call factorisation the paper's
 //   tiled approach is compared with in Sec. 4.1), cuBLAS DGEMM, and register-only FP64 FFMA,
-//   FP64 mma.sync (DMMA) and FP32 FFMA loops that bound what FMA-issue-bound kernels can reach.
+//   FP64 mma.sync (DMMA) and FP32 FFMA loops that bound what FMA-issue-bound kernels can reach, and
+//   streaming probes (a read-only 4 GB buffer consumed by FP64 or by FP32 adds, through plain loads or
+//   through a ring of bulk copies) that show whether a matrix-vector-type pass is bound by HBM or by
+//   the FP64 pipe.
 // Prints one JSON object per measurement.
 // Usage: vendor_baselines [n] [--no-potrf] [--no-spotrf] [--no-probes] [--once]
 //   --once: time the first Dpotrf call (no warm-up call; for sizes where one call takes a minute).
@@ -106,6 +109,94 @@ __global__ void to_float(const double* A, float* B, long long cnt) {
     B[e] = (float)A[e];
 }
 
+// Streaming probes. Each CTA reads its own contiguous slice (bytes_per_cta) once.
+// FP64 consumer: one FP64 add per 8 bytes (the issue cost of a dense FP64 matrix-vector product).
+__global__ void __launch_bounds__(512) stream_fp64(const double2* src, long long n2_per_cta, double* sink) {
+  const double2* base = src + (long long)blockIdx.x * n2_per_cta;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < n2_per_cta; i += 512 * 8) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (i + u * 512 < n2_per_cta) ? __ldg(base + i + u * 512) : make_double2(0, 0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u].x + v[u].y;
+  }
+  if (acc == 1234.5) sink[0] = acc;
+}
+// FP32 consumer: one FP32 add per 4 bytes.
+__global__ void __launch_bounds__(512) stream_fp32(const float4* src, long long n4_per_cta, double* sink) {
+  const float4* base = src + (long long)blockIdx.x * n4_per_cta;
+  float acc = 0.f;
+  for (long long i = threadIdx.x; i < n4_per_cta; i += 512 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (i + u * 512 < n4_per_cta) ? __ldg(base + i + u * 512) : make_float4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+  }
+  if (acc == 1234.5f) sink[0] = acc;
+}
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool mbar_done(unsigned long long* b, unsigned par) {
+  unsigned ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(smem_addr(b)), "r"(par) : "memory");
+  return ok;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bulk-copy ring: 64 KB chunks, 3 stages, thread 0 issues; FP32 consumer. Every wait is bounded (50 ms,
+// then *err is set and the CTA drains its copies and leaves).
+__global__ void __launch_bounds__(512, 1) stream_bulk_fp32(const unsigned char* src, long long bytes_per_cta,
+                                                           double* sink, int* err) {
+  constexpr int CB = 65536, S = 3;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ unsigned long long full[S];
+  __shared__ int fail;
+  const unsigned char* base = src + (long long)blockIdx.x * bytes_per_cta;
+  const long long nchunks = bytes_per_cta / CB;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail = 0;
+  }
+  __syncthreads();
+  long long issued = 0;
+  auto issue = [&]() {
+    if (issued >= nchunks) return;
+    const int s = issued % S;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])), "r"(CB) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(sm + (long long)s * CB)), "l"(base + issued * CB), "r"(CB), "r"(smem_addr(&full[s]))
+                 : "memory");
+    ++issued;
+  };
+  if (threadIdx.x == 0)
+    for (int q = 0; q < S; ++q) issue();
+  float acc = 0.f;
+  long long i = 0;
+  for (; i < nchunks; ++i) {
+    const int s = i % S;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_done(&full[s], (unsigned)(i / S) & 1u))
+      if (gtimer() - t0 > 50000000ull) { fail = 1; atomicExch(err, 1); break; }
+    const float4* d = reinterpret_cast<const float4*>(sm + (long long)s * CB);
+    for (int e = threadIdx.x; e < CB / 16; e += 512) { const float4 v = d[e]; acc += (v.x + v.y) + (v.z + v.w); }
+    __syncthreads();
+    if (fail) break;
+    if (threadIdx.x == 0) issue();
+  }
+  if (fail && threadIdx.x == 0)
+    for (long long q = i; q < issued; ++q) {
+      const unsigned long long t0 = gtimer();
+      while (!mbar_done(&full[q % S], (unsigned)(q / S) & 1u) && gtimer() - t0 < 50000000ull) {}
+    }
+  if (acc == 1234.5f) sink[0] = acc;
+}
+
 template <class F>
 float best_ms(F f, int reps) {
   cudaEvent_t e0, e1;
@@ -163,6 +254,30 @@ int main(int argc, char** argv) {
     const double ffma = 2.0 * 16 * it_f * (double)grid * 128, dmma = 2.0 * 256 * 8 * it_d * (double)grid * 4;
     printf("{\"probe\": \"ffma64_and_dmma\", \"tflops\": %.4f, \"ffma_share\": %.3f}\n", (ffma + dmma) / ms / 1e9,
            ffma / (ffma + dmma));
+  }
+  if (probes) {  // streaming: whole GPU (one 512-thread CTA per SM, 4 GB) and one CTA (256 MB)
+    const long long total = 4LL << 30;
+    unsigned char* buf;
+    int* err;
+    CK(cudaMalloc(&buf, total));
+    CK(cudaMemset(buf, 0, total));
+    CK(cudaMalloc(&err, sizeof(int)));
+    CK(cudaMemset(err, 0, sizeof(int)));
+    CK(cudaFuncSetAttribute(stream_bulk_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 65536));
+    for (int grid : {sms, 1}) {
+      const long long per = (grid == 1 ? (256LL << 20) : total / grid) / 65536 * 65536;
+      const double gb = (double)per * grid / 1e9;
+      const float m64 = best_ms([&] { stream_fp64<<<grid, 512>>>((const double2*)buf, per / 16, out); }, 3);
+      const float m32 = best_ms([&] { stream_fp32<<<grid, 512>>>((const float4*)buf, per / 16, out); }, 3);
+      const float mb = best_ms([&] { stream_bulk_fp32<<<grid, 512, 3 * 65536>>>(buf, per, out, err); }, 3);
+      int herr = 0;
+      CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+      printf("{\"probe\": \"stream_%s\", \"ctas\": %d, \"fp64_consumer_gbs\": %.1f, \"fp32_consumer_gbs\": %.1f, "
+             "\"bulk64k_fp32_consumer_gbs\": %.1f, \"timeouts\": %d}\n",
+             grid == 1 ? "one_cta" : "gpu", grid, gb / m64 * 1e3, gb / m32 * 1e3, gb / mb * 1e3, herr);
+    }
+    cudaFree(buf);
+    cudaFree(err);
   }
   fflush(stdout);
   double* A;

@@ -89,6 +89,36 @@ __device__ __forceinline__ void cta_publish_add(int* counter) {
   }
 }
 
+// FP64 <-> FP32 conversions on the integer pipe. On GB300 the cvt instructions between double and
+// float issue on the FP64 pipe (about 2 per clock per SM, like an FP64 FMA), so staging FP64 operands
+// as FP32 with cvt would cost as much FP64 issue as the FP32 FMAs they feed. These do the same
+// IEEE conversion with 32-bit integer operations on the two halves of the double:
+//   narrowing: round to nearest, ties to even; results below the FP32 normal range flush to a
+//              signed zero, values beyond it become a signed infinity, NaN stays NaN;
+//   widening:  exact (FP32 subnormals flush to a signed zero).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const unsigned rem = lo & 0x1FFFFFFFu;                   // the 29 bits rounded away
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u));
+  const int e32 = e - 896;  // rebias 1023 -> 127
+  if (e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned inc = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((sign | ((unsigned)e32 << 23) | m) + inc);  // a mantissa carry bumps the exponent
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const unsigned hi = (e == 0xFFu) ? (sign | 0x7FF00000u | (m >> 3)) : (sign | ((e + 896u) << 20) | (m >> 3));
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+
 // L2-only load (bypasses L1, so data written by other SMs after an acquire is never stale).
 template <class T>
 __device__ __forceinline__ T ldcg(const T* p) {

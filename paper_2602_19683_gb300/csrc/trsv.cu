@@ -440,15 +440,17 @@ cudaError_t launch_trsv32(const float* Lt, const float* Linv, double* b, double*
   return cudaGetLastError();
 }
 
-// FP32 copies of the factor for the correction solves: dst[i] = (float)src[i], n values.
+// FP32 copies of the factor for the correction solves: dst[i] = src[i] rounded to nearest FP32, n values
+// (src 16-byte aligned). The conversion runs on the integer pipe (f64_to_f32_rn), so the pass is bound by
+// HBM, not by FP64 issue.
 __global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x * 2;
   for (long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
     if (i + 1 < n) {
-      const double2 v = *reinterpret_cast<const double2*>(src + i);
-      *reinterpret_cast<float2*>(dst + i) = make_float2((float)v.x, (float)v.y);
+      const double2 v = __ldcs(reinterpret_cast<const double2*>(src + i));
+      *reinterpret_cast<float2*>(dst + i) = make_float2(f64_to_f32_rn(v.x), f64_to_f32_rn(v.y));
     } else {
-      dst[i] = (float)src[i];
+      dst[i] = f64_to_f32_rn(src[i]);
     }
   }
 }
