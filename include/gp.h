@@ -353,6 +353,11 @@ void gp_debug_fail_alloc(int64_t k);
 gp_status gp_debug_tile_product(gp_ctx* ctx, int32_t precision, const double* A, const double* B, double* C,
                                 int32_t K, int32_t store, int32_t lower, int32_t reps);
 
+/* TEST HOOK: out[i] = the covariance assembly's exponential of x[i] (device arrays of n doubles; the
+ * assembly only evaluates x <= 0): a table-driven evaluation after Tang (ACM TOMS 1989), x < -745.2
+ * giving +0 and NaN staying NaN. Asynchronous. */
+gp_status gp_debug_exp_neg(gp_ctx* ctx, const double* x, int64_t n, double* out);
+
 #ifdef __cplusplus
 }
 #endif

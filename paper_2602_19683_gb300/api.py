@@ -224,6 +224,14 @@ def gp_alpha(ctx: Context, f: Factor) -> torch.Tensor:
     return out
 
 
+def debug_exp_neg(ctx: Context, x: torch.Tensor) -> torch.Tensor:
+    """Test hook: the covariance assembly's exponential of each entry of x (float64 CUDA tensor)."""
+    _dev(x, "x")
+    out = torch.empty_like(x)
+    _check(ctx.lib.gp_debug_exp_neg(ctx.h, x.data_ptr(), x.numel(), out.data_ptr()), "gp_debug_exp_neg")
+    return out
+
+
 def gp_solve(ctx: Context, f: Factor, b: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """x = (L L^T)^{-1} b with the stored factor, no refinement (FP32 arithmetic for the refined forms at
     tile edges 128 and 256, FP64 otherwise). Asynchronous: errors are reported by gp_sync."""

@@ -121,6 +121,8 @@ struct gp_factor {
                                   // sums, counters, L^{-1} y
   DevBuf V, S, cCov;          // covariance workspace
   DevBuf gV, gzero, gh;       // GMRES refinement: Krylov basis, a zero vector, Hessenberg column scratch
+  DevBuf Xq, fx;              // fixed-point coordinates of X and their scale (the assembly of K)
+  DevBuf Xq2, Xsq, fx2;       // X and the test points under one common scale (cross-covariance calls)
   DevBuf Lt32, Linv32;        // refined forms, T = 128 / 256: FP32 copies of the factor tiles and inverses
                               // (the correction solves' operands)
   bool has32 = false;         // Lt32 / Linv32 hold the current factor
@@ -679,12 +681,42 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->gh);
   release(f->Lt32);
   release(f->Linv32);
+  release(f->Xq);
+  release(f->fx);
+  release(f->Xq2);
+  release(f->Xsq);
+  release(f->fx2);
   release(f->V);
   release(f->S);
   release(f->cCov);
   delete f;
   return GP_OK;
 }
+
+namespace {
+// Fixed-point coordinates for the covariance assembly (se_kernel.cuh) for the unrolled dimensions; the
+// scale is decided on the device (no host wait). B may be null (one point set).
+bool fx_dims(int D) { return D == 4 || D == 8 || D == 16; }
+
+gp_status fx_quantize(gp_ctx* c, const double* A, long long na, const double* B, long long nb, int D, double l,
+                      DevBuf& qa, DevBuf* qb, DevBuf& fx) {
+  GP_TRY(grow(fx, sizeof(gpk::FxScale)));
+  GP_TRY(grow(qa, (size_t)std::max(na, 1LL) * D * sizeof(long long)));
+  if (qb) GP_TRY(grow(*qb, (size_t)std::max(nb, 1LL) * D * sizeof(long long)));
+  GP_CUDA(gpk::launch_fx_prepare(A, na, B, B ? nb : 0, D, l, (gpk::FxScale*)fx.p, c->stream));
+  GP_CUDA(gpk::launch_fx_quantize(A, na * D, (const gpk::FxScale*)fx.p, (long long*)qa.p, c->sms, c->stream));
+  if (qb) GP_CUDA(gpk::launch_fx_quantize(B, nb * D, (const gpk::FxScale*)fx.p, (long long*)qb->p, c->sms, c->stream));
+  count_launch(c, qb ? 3 : 2);
+  return GP_OK;
+}
+
+// X and the test points Xs under one common scale (f->Xq2, f->Xsq, f->fx2): the cross-covariance calls.
+gp_status fx_cross(gp_ctx* c, gp_factor* f, const double* Xs, long long m) {
+  if (!fx_dims(f->D)) return GP_OK;
+  return fx_quantize(c, f->X, f->n, Xs, m, f->D, f->h.l, f->Xq2, &f->Xsq, f->fx2);
+}
+
+}  // namespace
 
 gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper h, gp_factor** K_out) {
   if (!c || !K_out || !X || n < 1 || D < 1 || D > 4096 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
@@ -733,7 +765,11 @@ gp_status gp_assemble(gp_ctx* c, const double* X, int64_t n, int32_t D, gp_hyper
   f->factored = false;
   f->alpha_valid = false;
   GP_CUDA(gpk::launch_scan_nonfinite(X, n * D, 0, c->d_status, c->stream));
-  GP_CUDA(gpk::launch_assemble_tiles(X, n, D, h.l, h.v, h.s2, (double*)f->Kt.p, T, (int)Mt, c->stream));
+  const bool fxd = fx_dims(D);
+  if (fxd) GP_TRY(fx_quantize(c, X, n, nullptr, 0, D, h.l, f->Xq, nullptr, f->fx));
+  GP_CUDA(gpk::launch_assemble_tiles(X, n, D, h.l, h.v, h.s2, (double*)f->Kt.p, T, (int)Mt, c->stream,
+                                     fxd ? (const long long*)f->Xq.p : nullptr,
+                                     fxd ? (const gpk::FxScale*)f->fx.p : nullptr));
   count_launch(c, 2);
   if (mixed)
     GP_CUDA(cudaMemcpyAsync(f->Kt0.p, f->Kt.p, ntiles * T * T * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -891,8 +927,12 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
   }
   f->alpha_valid = true;
   if (m > 0) {
+    GP_TRY(fx_cross(c, f, Xs, m));
+    const bool fxd = fx_dims(f->D);
     GP_CUDA(gpk::launch_mean_gemv(Xs, m, f->X, f->n, f->D, f->h.l, f->h.v, (const double*)f->alpha.p, mean_out,
-                                  c->stream));
+                                  c->stream, fxd ? (const long long*)f->Xsq.p : nullptr,
+                                  fxd ? (const long long*)f->Xq2.p : nullptr,
+                                  fxd ? (const gpk::FxScale*)f->fx2.p : nullptr));
     count_launch(c);
   }
   f->ir_iters = iters;
@@ -915,10 +955,16 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
   GP_CUDA(gpk::launch_scan_nonfinite(Xs, m * f->D, 0, c->d_status, c->stream));
   count_launch(c);
   // Right-hand side K_{X,Xs} (n x m, zero padded) and the prior K_{Xs,Xs} (Eq. 3).
+  GP_TRY(fx_cross(c, f, Xs, m));
+  const bool fxd = fx_dims(f->D);
+  const long long* qx = fxd ? (const long long*)f->Xq2.p : nullptr;
+  const long long* qs = fxd ? (const long long*)f->Xsq.p : nullptr;
+  const gpk::FxScale* fx = fxd ? (const gpk::FxScale*)f->fx2.p : nullptr;
   GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
-                                     (long long)npad, (long long)ldv, c->stream));
+                                     (long long)npad, (long long)ldv, c->stream, qx, qs, fx));
   GP_CUDA(gpk::launch_assemble_dense(Xs, m, Xs, m, f->D, f->h.l, f->h.v, c->cfg.noisy_prior ? f->h.s2 : 0.0,
-                                     (double*)f->S.p, (long long)ldv, (long long)ldv, (long long)ldv, c->stream));
+                                     (double*)f->S.p, (long long)ldv, (long long)ldv, (long long)ldv, c->stream, qs, qs,
+                                     fx));
   count_launch(c, 2);
   GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
   const bool mixed = is_mixed(f->precision);
@@ -957,8 +1003,13 @@ gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, d
   GP_TRY(grow(f->cCov, ncnt * sizeof(int)));
   GP_CUDA(gpk::launch_scan_nonfinite(Xs, m * f->D, 0, c->d_status, c->stream));
   count_launch(c);
+  GP_TRY(fx_cross(c, f, Xs, m));
+  const bool fxd = fx_dims(f->D);
   GP_CUDA(gpk::launch_assemble_dense(f->X, f->n, Xs, m, f->D, f->h.l, f->h.v, 0.0, (double*)f->V.p, (long long)ldv,
-                                     (long long)npad, (long long)ldv, c->stream));
+                                     (long long)npad, (long long)ldv, c->stream,
+                                     fxd ? (const long long*)f->Xq2.p : nullptr,
+                                     fxd ? (const long long*)f->Xsq.p : nullptr,
+                                     fxd ? (const gpk::FxScale*)f->fx2.p : nullptr));
   count_launch(c);
   GP_CUDA(cudaMemsetAsync(f->cCov.p, 0, ncnt * sizeof(int), c->stream));
   const bool mixed = is_mixed(f->precision);
@@ -1017,6 +1068,14 @@ gp_status gp_solve(gp_ctx* c, gp_factor* f, const double* b, double* x) {
   GP_CUDA(cudaMemcpyAsync(f->bvec.p, b, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   GP_TRY(solve_in_place(c, f));
   GP_CUDA(cudaMemcpyAsync(x, f->bvec.p, (size_t)f->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return GP_OK;
+}
+
+gp_status gp_debug_exp_neg(gp_ctx* c, const double* x, int64_t n, double* out) {
+  if (!c || n < 0 || (n > 0 && (!x || !out))) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(gpk::launch_exp_neg(x, n, out, c->sms, c->stream));
+  count_launch(c);
   return GP_OK;
 }
 

@@ -20,6 +20,13 @@ struct DevStatus {
   unsigned long long pad[5];
 };
 
+// Fixed-point coordinates of the covariance assembly (se_kernel.cuh): the quantisation shared by the
+// point sets of one launch family (device resident, written by fx_prepare_kernel).
+struct FxScale {
+  int32_t F;       // q = round(x 2^F)
+  int32_t usable;  // 1: every quantised coordinate |q| < 2^58 and max |x| <= 64 l (the error bound holds)
+};
+
 #ifdef __CUDACC__
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;

@@ -5,6 +5,7 @@
 
 #include "bslice.cuh"
 #include "kernels.h"
+#include "se_kernel.cuh"
 
 namespace gpk {
 
@@ -73,12 +74,80 @@ __device__ __forceinline__ double sqdist_t(const double* __restrict__ a, const d
   return r2;
 }
 
-// Lower tiles of K: tile blockIdx.x (packed index), rows [blockIdx.y*32, +32) of it. Entries
-// outside the n x n matrix form the identity padding.
+// r^2 = |a - b|^2 from fixed-point coordinates (exact, rounded once); D > 0.
+template <int D>
+__device__ __forceinline__ double fx_sqdist(const long long* qa, const long long (&qb)[D], int twoF) {
+  U128 acc{0ull, 0ull};
+#pragma unroll
+  for (int d = 0; d < D; ++d) fx_add_sq(acc, __ldg(qa + d), qb[d]);
+  return fx_to_double(acc, twoF);
+}
+
+// Quantisation of one launch family: S = max |coordinate| over A (na x D) and B (nb x D); F = 57 -
+// floor(log2 S), so that |q| < 2^58; usable when S <= 64 l, 2F <= 1022, D <= 256 and every coordinate is
+// finite (a zero S quantises everything to 0 with F = 0). One CTA.
+__global__ void __launch_bounds__(1024) fx_prepare_kernel(const double* __restrict__ A, long long na,
+                                                          const double* __restrict__ B, long long nb, int D, double l,
+                                                          FxScale* out) {
+  __shared__ double red[32];
+  __shared__ int bad[32];
+  double mx = 0.0;
+  int nonfinite = 0;
+  for (long long e = threadIdx.x; e < (na + nb) * D; e += blockDim.x) {
+    const double x = e < na * D ? A[e] : B[e - na * D];
+    if (!(fabs(x) <= 1.7976931348623157e308)) nonfinite = 1;
+    else mx = fmax(mx, fabs(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
+  }
+  if (threadIdx.x % 32 == 0) {
+    red[threadIdx.x / 32] = mx;
+    bad[threadIdx.x / 32] = nonfinite;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    int nf = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      S = fmax(S, red[w]);
+      nf |= bad[w];
+    }
+    FxScale r{0, 0};
+    if (!nf && D <= 256) {
+      if (S == 0.0) {
+        r.usable = 1;
+      } else {
+        r.F = 57 - ilogb(S);
+        r.usable = (S <= 64.0 * l && r.F <= 511 && r.F >= -448) ? 1 : 0;
+      }
+    }
+    *out = r;
+  }
+}
+
+// Q[e] = round(X[e] 2^F) (nothing when the scale is not usable).
+__global__ void fx_quantize_kernel(const double* __restrict__ X, long long cnt, const FxScale* __restrict__ fx,
+                                   long long* __restrict__ Q) {
+  const FxScale f = *fx;
+  if (!f.usable) return;
+  const double scale = ldexp(1.0, f.F);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    Q[e] = __double2ll_rn(X[e] * scale);
+}
+
+// Lower tiles of K: tile blockIdx.x (packed index), rows [blockIdx.y*32, +32) of it. Entries outside
+// the n x n matrix form the identity padding. With usable fixed-point coordinates Q (D > 0) the
+// distances are the exact integer ones; a thread keeps its column's coordinates in registers while its
+// column stays the same.
 template <int D>
 __global__ void __launch_bounds__(kThreads) assemble_tiles_kernel(const double* __restrict__ X, long long n, int Dr,
                                                                   double neg_half_inv_l2, double v, double s2,
-                                                                  double* __restrict__ Kt, int T) {
+                                                                  double* __restrict__ Kt, int T,
+                                                                  const long long* __restrict__ Q,
+                                                                  const FxScale* __restrict__ fx) {
   const long long t = blockIdx.x;
   long long I = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while (I * (I + 1) / 2 > t) --I;
@@ -86,13 +155,27 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles_kernel(const double* 
   const long long J = t - I * (I + 1) / 2;
   double* tile = Kt + (size_t)t * T * T;
   const int r0 = blockIdx.y * 32;
+  const bool use_fx = D > 0 && Q != nullptr && fx->usable;
+  const int twoF = use_fx ? 2 * fx->F : 0;
+  long long qj[D > 0 ? D : 1];
+  long long jcached = -1;
   for (int e = threadIdx.x; e < 32 * T; e += kThreads) {
     const int r = r0 + e / T, c = e % T;
     const long long i = I * T + r, j = J * T + c;
     double val;
     if (i < n && j < n) {
-      const double r2 = sqdist_t<D>(X + i * Dr, X + j * Dr, Dr);
-      val = v * exp(r2 * neg_half_inv_l2) + (i == j ? s2 : 0.0);
+      double r2;
+      if (D > 0 && use_fx) {
+        if (j != jcached) {
+#pragma unroll
+          for (int d = 0; d < (D > 0 ? D : 1); ++d) qj[d] = __ldg(Q + j * D + d);
+          jcached = j;
+        }
+        r2 = fx_sqdist<(D > 0 ? D : 1)>(Q + i * D, qj, twoF);
+      } else {
+        r2 = sqdist_t<D>(X + i * Dr, X + j * Dr, Dr);
+      }
+      val = v * exp_neg(r2 * neg_half_inv_l2) + (i == j ? s2 : 0.0);
     } else {
       val = (i == j) ? 1.0 : 0.0;
     }
@@ -101,45 +184,86 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles_kernel(const double* 
 }
 
 // Dense block out[i*ld + j], i < rows_pad, j < cols_pad: k(A_i, B_j) for i < na, j < nb (no noise:
-// different point sets), plus diag_add on i == j when same_set, and 0 in the padding.
+// different point sets), plus diag_add on i == j when same_set, and 0 in the padding. QA, QB: the
+// fixed-point coordinates of A and B under one common scale fx (or null).
 template <int D>
 __global__ void __launch_bounds__(kThreads) assemble_dense_kernel(const double* __restrict__ A, long long na,
                                                                   const double* __restrict__ B, long long nb, int Dr,
                                                                   double neg_half_inv_l2, double v, double diag_add,
                                                                   double* __restrict__ out, long long ld,
-                                                                  long long rows_pad, long long cols_pad) {
+                                                                  long long rows_pad, long long cols_pad,
+                                                                  const long long* __restrict__ QA,
+                                                                  const long long* __restrict__ QB,
+                                                                  const FxScale* __restrict__ fx) {
   const long long i = (long long)blockIdx.y * 8 + threadIdx.x / 32;
   if (i >= rows_pad) return;
+  const bool use_fx = D > 0 && QA != nullptr && fx->usable && i < na;
+  const int twoF = use_fx ? 2 * fx->F : 0;
+  long long qi[D > 0 ? D : 1];
+  if (use_fx) {
+#pragma unroll
+    for (int d = 0; d < (D > 0 ? D : 1); ++d) qi[d] = __ldg(QA + i * D + d);
+  }
   for (long long j = (long long)blockIdx.x * 128 + (threadIdx.x % 32); j < cols_pad && j < (long long)(blockIdx.x + 1) * 128;
        j += 32) {
     double val = 0.0;
     if (i < na && j < nb) {
-      const double r2 = sqdist_t<D>(A + i * Dr, B + j * Dr, Dr);
-      val = v * exp(r2 * neg_half_inv_l2) + (i == j ? diag_add : 0.0);
+      const double r2 = (D > 0 && use_fx) ? fx_sqdist<(D > 0 ? D : 1)>(QB + j * D, qi, twoF)
+                                          : sqdist_t<D>(A + i * Dr, B + j * Dr, Dr);
+      val = v * exp_neg(r2 * neg_half_inv_l2) + (i == j ? diag_add : 0.0);
     }
     out[(size_t)i * ld + j] = val;
   }
 }
 
 // mean[i] = sum_{j<n} k(Xs_i, X_j) alpha_j, the kernel row recomputed on the fly (Eq. 2's last
-// step fused with the assembly of K_{Xs,X}). 8 test points per CTA.
+// step fused with the assembly of K_{Xs,X}). 8 test points per CTA. QXs, QX: fixed-point coordinates
+// under one common scale fx (or null).
 template <int D>
 __global__ void __launch_bounds__(kThreads) mean_gemv_kernel(const double* __restrict__ Xs, long long m,
                                                              const double* __restrict__ X, long long n, int Dr,
                                                              double neg_half_inv_l2, double v,
-                                                             const double* __restrict__ alpha, double* __restrict__ mean) {
+                                                             const double* __restrict__ alpha, double* __restrict__ mean,
+                                                             const long long* __restrict__ QXs,
+                                                             const long long* __restrict__ QX,
+                                                             const FxScale* __restrict__ fx) {
   __shared__ double red[8][kThreads / 32];
+  __shared__ long long qs[8][D > 0 ? D : 1];
   const long long i0 = (long long)blockIdx.x * 8;
+  const bool use_fx = D > 0 && QX != nullptr && fx->usable;
+  const int twoF = use_fx ? 2 * fx->F : 0;
+  if (use_fx) {
+    for (int e = threadIdx.x; e < 8 * (D > 0 ? D : 1); e += kThreads) {
+      const int q = e / (D > 0 ? D : 1), d = e % (D > 0 ? D : 1);
+      qs[q][d] = i0 + q < m ? QXs[(i0 + q) * (D > 0 ? D : 1) + d] : 0;
+    }
+    __syncthreads();
+  }
   double acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
   for (long long j = threadIdx.x; j < n; j += kThreads) {
     const double aj = __ldg(alpha + j);
+    if (D > 0 && use_fx) {
+      long long qj[D > 0 ? D : 1];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (i0 + q < m) {
-        const double r2 = sqdist_t<D>(Xs + (i0 + q) * Dr, X + j * Dr, Dr);
-        acc[q] = fma(v * exp(r2 * neg_half_inv_l2), aj, acc[q]);
+      for (int d = 0; d < (D > 0 ? D : 1); ++d) qj[d] = __ldg(QX + j * (D > 0 ? D : 1) + d);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (i0 + q < m) {
+          U128 sacc{0ull, 0ull};
+#pragma unroll
+          for (int d = 0; d < (D > 0 ? D : 1); ++d) fx_add_sq(sacc, qs[q][d], qj[d]);
+          acc[q] = fma(v * exp_neg(fx_to_double(sacc, twoF) * neg_half_inv_l2), aj, acc[q]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (i0 + q < m) {
+          const double r2 = sqdist_t<D>(Xs + (i0 + q) * Dr, X + j * Dr, Dr);
+          acc[q] = fma(v * exp_neg(r2 * neg_half_inv_l2), aj, acc[q]);
+        }
       }
     }
   }
@@ -1242,46 +1366,74 @@ __global__ void __launch_bounds__(kThreads) var_from_v_kernel(const double* __re
 
 // ---------------------------------------------------------------- host launchers
 
+__global__ void exp_neg_kernel(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = exp_neg(x[i]);
+}
+
+cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + kThreads - 1) / kThreads;
+  exp_neg_kernel<<<(unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8), kThreads, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fx_prepare(const double* A, long long na, const double* B, long long nb, int D, double l, FxScale* out,
+                              cudaStream_t st) {
+  fx_prepare_kernel<<<1, 1024, 0, st>>>(A, na, B, nb, D, l, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fx_quantize(const double* X, long long cnt, const FxScale* fx, long long* Q, int sms, cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  const long long want = (cnt + kThreads - 1) / kThreads;
+  const unsigned grid = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+  fx_quantize_kernel<<<grid, kThreads, 0, st>>>(X, cnt, fx, Q);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble_tiles(const double* X, long long n, int D, double l, double v, double s2, double* Kt, int T,
-                                  int Mt, cudaStream_t st) {
+                                  int Mt, cudaStream_t st, const long long* Q, const FxScale* fx) {
   const long long ntiles = (long long)Mt * (Mt + 1) / 2;
   if (ntiles == 0) return cudaSuccess;
   dim3 grid((unsigned)ntiles, (unsigned)(T / 32));
   const double c = -0.5 / (l * l);
   switch (D) {
-    case 4: assemble_tiles_kernel<4><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T); break;
-    case 8: assemble_tiles_kernel<8><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T); break;
-    case 16: assemble_tiles_kernel<16><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T); break;
-    default: assemble_tiles_kernel<0><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T); break;
+    case 4: assemble_tiles_kernel<4><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T, Q, fx); break;
+    case 8: assemble_tiles_kernel<8><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T, Q, fx); break;
+    case 16: assemble_tiles_kernel<16><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T, Q, fx); break;
+    default: assemble_tiles_kernel<0><<<grid, kThreads, 0, st>>>(X, n, D, c, v, s2, Kt, T, nullptr, nullptr); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_dense(const double* A, long long na, const double* B, long long nb, int D, double l,
                                   double v, double diag_add, double* out, long long ld, long long rows_pad,
-                                  long long cols_pad, cudaStream_t st) {
+                                  long long cols_pad, cudaStream_t st, const long long* QA, const long long* QB,
+                                  const FxScale* fx) {
   if (rows_pad == 0 || cols_pad == 0) return cudaSuccess;
   dim3 grid((unsigned)((cols_pad + 127) / 128), (unsigned)((rows_pad + 7) / 8));
   const double c = -0.5 / (l * l);
   switch (D) {
-    case 4: assemble_dense_kernel<4><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad); break;
-    case 8: assemble_dense_kernel<8><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad); break;
-    case 16: assemble_dense_kernel<16><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad); break;
-    default: assemble_dense_kernel<0><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad); break;
+    case 4: assemble_dense_kernel<4><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad, QA, QB, fx); break;
+    case 8: assemble_dense_kernel<8><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad, QA, QB, fx); break;
+    case 16: assemble_dense_kernel<16><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad, QA, QB, fx); break;
+    default: assemble_dense_kernel<0><<<grid, kThreads, 0, st>>>(A, na, B, nb, D, c, v, diag_add, out, ld, rows_pad, cols_pad, nullptr, nullptr, nullptr); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_mean_gemv(const double* Xs, long long m, const double* X, long long n, int D, double l, double v,
-                             const double* alpha, double* mean, cudaStream_t st) {
+                             const double* alpha, double* mean, cudaStream_t st, const long long* QXs,
+                             const long long* QX, const FxScale* fx) {
   if (m == 0) return cudaSuccess;
   const unsigned grid = (unsigned)((m + 7) / 8);
   const double c = -0.5 / (l * l);
   switch (D) {
-    case 4: mean_gemv_kernel<4><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
-    case 8: mean_gemv_kernel<8><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
-    case 16: mean_gemv_kernel<16><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
-    default: mean_gemv_kernel<0><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean); break;
+    case 4: mean_gemv_kernel<4><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean, QXs, QX, fx); break;
+    case 8: mean_gemv_kernel<8><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean, QXs, QX, fx); break;
+    case 16: mean_gemv_kernel<16><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean, QXs, QX, fx); break;
+    default: mean_gemv_kernel<0><<<grid, kThreads, 0, st>>>(Xs, m, X, n, D, c, v, alpha, mean, nullptr, nullptr, nullptr); break;
   }
   return cudaGetLastError();
 }

@@ -120,13 +120,22 @@ struct DagArgs {
   long long* trace;   // optional: per task {CTA, t_taken, t_ready, t_done} (%globaltimer ns), 4 x int64
 };
 
+// Covariance assembly (Eq. 1). Q / QA, QB / QXs, QX: the points' fixed-point coordinates under the common
+// scale fx (launch_fx_prepare over every point set of the call, then launch_fx_quantize per set; null:
+// the FP64 distance). With a usable scale the squared distances are exact integer sums (se_kernel.cuh).
+cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, cudaStream_t st);
+cudaError_t launch_fx_prepare(const double* A, long long na, const double* B, long long nb, int D, double l, FxScale* out,
+                              cudaStream_t st);
+cudaError_t launch_fx_quantize(const double* X, long long cnt, const FxScale* fx, long long* Q, int sms, cudaStream_t st);
 cudaError_t launch_assemble_tiles(const double* X, long long n, int D, double l, double v, double s2, double* Kt, int T,
-                                  int Mt, cudaStream_t st);
+                                  int Mt, cudaStream_t st, const long long* Q = nullptr, const FxScale* fx = nullptr);
 cudaError_t launch_assemble_dense(const double* A, long long na, const double* B, long long nb, int D, double l,
                                   double v, double diag_add, double* out, long long ld, long long rows_pad,
-                                  long long cols_pad, cudaStream_t st);
+                                  long long cols_pad, cudaStream_t st, const long long* QA = nullptr,
+                                  const long long* QB = nullptr, const FxScale* fx = nullptr);
 cudaError_t launch_mean_gemv(const double* Xs, long long m, const double* X, long long n, int D, double l, double v,
-                             const double* alpha, double* mean, cudaStream_t st);
+                             const double* alpha, double* mean, cudaStream_t st, const long long* QXs = nullptr,
+                             const long long* QX = nullptr, const FxScale* fx = nullptr);
 cudaError_t launch_var_from_v(const double* V, long long ldv, long long nrows, double v, double diag_add, double* var,
                               long long m, cudaStream_t st);
 cudaError_t launch_cov_copy(const double* S, long long lds, double* cov, long long m, cudaStream_t st);
