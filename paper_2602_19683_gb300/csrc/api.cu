@@ -99,6 +99,7 @@ struct gp_batch {
   bool mixed = false;
   size_t counter_bytes = 0;
   DevBuf work, counters, descs, tasks, items;
+  DevBuf qwork, fxs;  // per GP: fixed-point coordinates of X and Xs, and their scale
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -1142,7 +1143,8 @@ gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, i
   }
   // contraction with dK/dtheta recomputed from X (dK never stored)
   GP_CUDA(gpk::launch_grad_contract((const double*)f->Bt.p, T, Mt, X, n, D, h.l, h.v, (double*)f->part.p,
-                                    c->d_scalar + 10, c->stream));
+                                    c->d_scalar + 10, c->stream, fx_dims(D) ? (const long long*)f->Xq.p : nullptr,
+                                    fx_dims(D) ? (const gpk::FxScale*)f->fx.p : nullptr));
   count_launch(c, 2);
   double hv[5];
   GP_CUDA(cudaMemcpyAsync(hv, c->d_scalar + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1189,9 +1191,12 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
   std::vector<gpk::GpDesc> hd(B);
   std::vector<gpk::BatchGp> shapes(B);
   size_t dbl = 0, ints = 0;
-  std::vector<size_t> offK(B), offV(B), offS(B), offb(B), offc(B);
+  std::vector<size_t> offK(B), offV(B), offS(B), offb(B), offc(B), offq(B);
+  size_t qn = 0;
   for (int g = 0; g < B; ++g) {
     const gp_batch_desc& d = descs[g];
+    offq[g] = qn;
+    qn += (size_t)(d.n + d.m) * d.D;
     const int T = d.tile ? d.tile : batch_tile(d.n);
     const long long Mt = (d.n + T - 1) / T, Mc = d.m > 0 ? (d.m + T - 1) / T : 0;
     const bool cov = want_cov && d.cov_out && d.m > 0;
@@ -1214,6 +1219,8 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
   gp_status st = grow(b->work, dbl * sizeof(double));
   if (st == GP_OK) st = grow(b->counters, ints * sizeof(int));
   if (st == GP_OK) st = grow(b->descs, (size_t)B * sizeof(gpk::GpDesc));
+  if (st == GP_OK) st = grow(b->qwork, qn * sizeof(long long));
+  if (st == GP_OK) st = grow(b->fxs, (size_t)B * sizeof(gpk::FxScale));
   if (st != GP_OK) {
     gp_batch_free(c, b);
     return st;
@@ -1230,6 +1237,9 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
     e.V = W + offV[g];
     e.S = W + offS[g];
     e.bvec = W + offb[g];
+    e.QX = (long long*)b->qwork.p + offq[g];
+    e.QXs = e.QX + (size_t)e.n * e.D;
+    e.fx = (gpk::FxScale*)b->fxs.p + g;
     int* cc = C + offc[g];
     e.cK = cc; cc += ntiles;
     if (Mc > 0) {
@@ -1284,6 +1294,7 @@ gp_status gp_batch_create(gp_ctx* c, int32_t B, const gp_batch_desc* descs, gp_b
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->counters.p, 0, b->counter_bytes, cs);
     cudaMemsetAsync(&c->d_status->next_task, 0, sizeof(unsigned long long), cs);
+    gpk::launch_batch_fx((const gpk::GpDesc*)b->descs.p, B, cs);
     gpk::launch_batch_pre((const int4*)b->items.p, b->npre, (const gpk::GpDesc*)b->descs.p, c->cfg.noisy_prior != 0, cs);
     gpk::DagArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1323,7 +1334,7 @@ gp_status gp_batch_run(gp_ctx* c, gp_batch* b) {
   if (!c || !b || !b->exec) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   GP_CUDA(cudaGraphLaunch(b->exec, c->stream));
-  count_launch(c, 3);
+  count_launch(c, 4);  // quantisation, assembly, persistent kernel, outputs
   return GP_OK;
 }
 
@@ -1337,6 +1348,8 @@ gp_status gp_batch_free(gp_ctx* c, gp_batch* b) {
   release(b->descs);
   release(b->tasks);
   release(b->items);
+  release(b->qwork);
+  release(b->fxs);
   delete b;
   return GP_OK;
 }

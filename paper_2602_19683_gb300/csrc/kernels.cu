@@ -83,6 +83,28 @@ __device__ __forceinline__ double fx_sqdist(const long long* qa, const long long
   return fx_to_double(acc, twoF);
 }
 
+// The same with the dimension known at run time (both coordinate rows read from memory).
+__device__ __forceinline__ double fx_sqdist_rt(const long long* qa, const long long* qb, int D, int twoF) {
+  U128 acc{0ull, 0ull};
+  for (int d = 0; d < D; ++d) fx_add_sq(acc, __ldg(qa + d), __ldg(qb + d));
+  return fx_to_double(acc, twoF);
+}
+
+// The scale rule shared by the single-GP and batched preparations: F = 57 - floor(log2 S) for the largest
+// |coordinate| S; usable when every coordinate is finite, S <= 64 l, D <= 256 and F is in range.
+__device__ __forceinline__ FxScale fx_decide(double S, int nonfinite, int D, double l) {
+  FxScale r{0, 0};
+  if (!nonfinite && D <= 256) {
+    if (S == 0.0) {
+      r.usable = 1;
+    } else {
+      r.F = 57 - ilogb(S);
+      r.usable = (S <= 64.0 * l && r.F <= 511 && r.F >= -448) ? 1 : 0;
+    }
+  }
+  return r;
+}
+
 // Quantisation of one launch family: S = max |coordinate| over A (na x D) and B (nb x D); F = 57 -
 // floor(log2 S), so that |q| < 2^58; usable when S <= 64 l, 2F <= 1022, D <= 256 and every coordinate is
 // finite (a zero S quantises everything to 0 with F = 0). One CTA.
@@ -115,16 +137,7 @@ __global__ void __launch_bounds__(1024) fx_prepare_kernel(const double* __restri
       S = fmax(S, red[w]);
       nf |= bad[w];
     }
-    FxScale r{0, 0};
-    if (!nf && D <= 256) {
-      if (S == 0.0) {
-        r.usable = 1;
-      } else {
-        r.F = 57 - ilogb(S);
-        r.usable = (S <= 64.0 * l && r.F <= 511 && r.F >= -448) ? 1 : 0;
-      }
-    }
-    *out = r;
+    *out = fx_decide(S, nf, D, l);
   }
 }
 
@@ -1138,7 +1151,9 @@ __global__ void __launch_bounds__(kThreads) init_lbar_kernel(const double* __res
 template <int D>
 __global__ void __launch_bounds__(kThreads) grad_contract_kernel(const double* __restrict__ Bt, int T,
                                                                  const double* __restrict__ X, long long n, int Dr,
-                                                                 double l, double v, double* __restrict__ partial) {
+                                                                 double l, double v, double* __restrict__ partial,
+                                                                 const long long* __restrict__ Q,
+                                                                 const FxScale* __restrict__ fx) {
   __shared__ double red[3][kThreads / 32];
   const long long t = blockIdx.x;
   long long I = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -1154,8 +1169,9 @@ __global__ void __launch_bounds__(kThreads) grad_contract_kernel(const double* _
     if (i >= n || j >= n || j > i) continue;
     double wgt = Bt[base + (size_t)r * T + c];
     if (i == j) wgt *= 0.5;  // diagonal tiles hold Abar + Abar^T
-    const double r2 = sqdist_t<D>(X + i * Dr, X + j * Dr, Dr);
-    const double ex = exp(r2 * neg_half_inv_l2);
+    const double r2 = (D > 0 && Q != nullptr && fx->usable) ? fx_sqdist_rt(Q + i * Dr, Q + j * Dr, Dr, 2 * fx->F)
+                                                            : sqdist_t<D>(X + i * Dr, X + j * Dr, Dr);
+    const double ex = exp_neg(r2 * neg_half_inv_l2);
     gl = fma(wgt, v * ex * r2 * inv_l3, gl);
     gv = fma(wgt, ex, gv);
     if (i == j) gs += wgt;
@@ -1260,6 +1276,51 @@ __global__ void add_diag_kernel(double* __restrict__ Kt, int T, long long n, dou
   }
 }
 
+// Per GP (one CTA each): the common scale over X and Xs (fx_decide), then both sets quantised.
+__global__ void __launch_bounds__(1024) batch_fx_kernel(const GpDesc* __restrict__ descs) {
+  __shared__ double red[32];
+  __shared__ int bad[32];
+  __shared__ FxScale sc;
+  const GpDesc& d = descs[blockIdx.x];
+  const long long nx = d.n * d.D, ns = d.m * d.D;
+  double mx = 0.0;
+  int nonfinite = 0;
+  for (long long e = threadIdx.x; e < nx + ns; e += blockDim.x) {
+    const double x = e < nx ? d.X[e] : d.Xs[e - nx];
+    if (!(fabs(x) <= 1.7976931348623157e308)) nonfinite = 1;
+    else mx = fmax(mx, fabs(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
+  }
+  if (threadIdx.x % 32 == 0) {
+    red[threadIdx.x / 32] = mx;
+    bad[threadIdx.x / 32] = nonfinite;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    int nf = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      S = fmax(S, red[w]);
+      nf |= bad[w];
+    }
+    sc = fx_decide(S, nf, d.D, d.l);
+    *d.fx = sc;
+  }
+  __syncthreads();
+  if (!sc.usable) return;
+  const double scale = ldexp(1.0, sc.F);
+  for (long long e = threadIdx.x; e < nx + ns; e += blockDim.x) {
+    if (e < nx)
+      d.QX[e] = __double2ll_rn(d.X[e] * scale);
+    else
+      d.QXs[e - nx] = __double2ll_rn(d.Xs[e - nx] * scale);
+  }
+}
+
 // Batched assembly and right-hand sides, one work item per CTA (see launch_batch_pre).
 __global__ void __launch_bounds__(kThreads) batch_pre_kernel(const int4* __restrict__ items,
                                                              const GpDesc* __restrict__ descs, int noisy_prior) {
@@ -1274,12 +1335,16 @@ __global__ void __launch_bounds__(kThreads) batch_pre_kernel(const int4* __restr
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     const long long J = t - I * (I + 1) / 2;
     double* tile = d.Kt + (size_t)t * T * T;
+    const bool use_fx = d.fx && d.fx->usable;
+    const int twoF = use_fx ? 2 * d.fx->F : 0;
     for (int e = threadIdx.x; e < 32 * T; e += kThreads) {
       const int r = it.w * 32 + e / T, cc = e % T;
       const long long i = I * T + r, j = J * T + cc;
       double val;
       if (i < d.n && j < d.n)
-        val = d.v * exp(sqdist_t<0>(d.X + i * d.D, d.X + j * d.D, d.D) * c) + (i == j ? d.s2 : 0.0);
+        val = d.v * exp_neg((use_fx ? fx_sqdist_rt(d.QX + i * d.D, d.QX + j * d.D, d.D, twoF)
+                                    : sqdist_t<0>(d.X + i * d.D, d.X + j * d.D, d.D)) * c) +
+              (i == j ? d.s2 : 0.0);
       else
         val = (i == j) ? 1.0 : 0.0;
       tile[(size_t)r * T + cc] = val;
@@ -1291,12 +1356,17 @@ __global__ void __launch_bounds__(kThreads) batch_pre_kernel(const int4* __restr
     const double* A = isV ? d.X : d.Xs;
     const long long na = isV ? d.n : d.m;
     const double diag = (!isV && noisy_prior) ? d.s2 : 0.0;
+    const long long* QA = isV ? d.QX : d.QXs;
+    const bool use_fx = d.fx && d.fx->usable;
+    const int twoF = use_fx ? 2 * d.fx->F : 0;
     for (int q = 0; q < 8; ++q) {
       const long long i = (long long)it.z + q;
       for (long long j = threadIdx.x; j < ld; j += kThreads) {
         double val = 0.0;
         if (i < na && j < d.m)
-          val = d.v * exp(sqdist_t<0>(A + i * d.D, d.Xs + j * d.D, d.D) * c) + ((!isV && i == j) ? diag : 0.0);
+          val = d.v * exp_neg((use_fx ? fx_sqdist_rt(QA + i * d.D, d.QXs + j * d.D, d.D, twoF)
+                                      : sqdist_t<0>(A + i * d.D, d.Xs + j * d.D, d.D)) * c) +
+                ((!isV && i == j) ? diag : 0.0);
         out[(size_t)i * ld + j] = val;
       }
     }
@@ -1318,12 +1388,17 @@ __global__ void __launch_bounds__(kThreads) batch_post_kernel(const int4* __rest
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    const bool use_fx = d.fx && d.fx->usable;
+    const int twoF = use_fx ? 2 * d.fx->F : 0;
     for (long long j = threadIdx.x; j < d.n; j += kThreads) {
       const double aj = d.bvec[j];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (i0 + q < d.m)
-          acc[q] = fma(d.v * exp(sqdist_t<0>(d.Xs + (i0 + q) * d.D, d.X + j * d.D, d.D) * c), aj, acc[q]);
+        if (i0 + q < d.m) {
+          const double r2 = use_fx ? fx_sqdist_rt(d.QXs + (i0 + q) * d.D, d.QX + j * d.D, d.D, twoF)
+                                   : sqdist_t<0>(d.Xs + (i0 + q) * d.D, d.X + j * d.D, d.D);
+          acc[q] = fma(d.v * exp_neg(r2 * c), aj, acc[q]);
+        }
     }
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
@@ -1548,6 +1623,12 @@ cudaError_t launch_residual(const double* Kt, int T, int Mt, long long n, const 
   return cudaGetLastError();
 }
 
+cudaError_t launch_batch_fx(const GpDesc* descs, int B, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  batch_fx_kernel<<<B, 1024, 0, st>>>(descs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs, bool noisy_prior, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
   batch_pre_kernel<<<nitems, kThreads, 0, st>>>(items, descs, noisy_prior ? 1 : 0);
@@ -1573,14 +1654,15 @@ cudaError_t launch_init_lbar(const double* Lt, double* Bt, int T, int Mt, long l
 }
 
 cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* X, long long n, int D, double l,
-                                 double v, double* partial, double* out, cudaStream_t st) {
+                                 double v, double* partial, double* out, cudaStream_t st, const long long* Q,
+                                 const FxScale* fx) {
   const long long ntiles = (long long)Mt * (Mt + 1) / 2;
   dim3 grid((unsigned)ntiles, (unsigned)(T / 32));
   switch (D) {
-    case 4: grad_contract_kernel<4><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
-    case 8: grad_contract_kernel<8><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
-    case 16: grad_contract_kernel<16><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
-    default: grad_contract_kernel<0><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial); break;
+    case 4: grad_contract_kernel<4><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial, Q, fx); break;
+    case 8: grad_contract_kernel<8><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial, Q, fx); break;
+    case 16: grad_contract_kernel<16><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial, Q, fx); break;
+    default: grad_contract_kernel<0><<<grid, kThreads, 0, st>>>(Bt, T, X, n, D, l, v, partial, nullptr, nullptr); break;
   }
   sum3_kernel<<<1, kThreads, 0, st>>>(partial, ntiles * (T / 32), out);
   return cudaGetLastError();

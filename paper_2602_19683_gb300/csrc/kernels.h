@@ -63,6 +63,9 @@ struct GpDesc {
   long long n, m, ldv, lds;
   double l, v, s2;
   int D, T, Mt, Mc, nch, pad;
+  long long* QX;      // fixed-point coordinates of X and Xs under the GP's scale fx (se_kernel.cuh)
+  long long* QXs;
+  FxScale* fx;
 };
 
 // Partial sums of the reverse sweep's diagonal adjoint: RDIAG(P, J) accumulates into partial
@@ -171,6 +174,8 @@ cudaError_t dag_enable_umma();
 //   pre:  0 = K tile a rows [b*32, +32); 1 = K_{X,Xs} rows [a, a+8); 2 = K_{Xs,Xs} rows [a, a+8);
 //         3 = rhs vector (y, zero padded)
 //   post: 0 = mean rows [a, a+8) (fused K_{Xs,X} alpha); 1 = covariance rows [a, a+8) copied/mirrored
+// One CTA per GP: the GP's common fixed-point scale over X and Xs, then both sets quantised.
+cudaError_t launch_batch_fx(const GpDesc* descs, int B, cudaStream_t st);
 cudaError_t launch_batch_pre(const int4* items, int nitems, const GpDesc* descs, bool noisy_prior, cudaStream_t st);
 cudaError_t launch_batch_post(const int4* items, int nitems, const GpDesc* descs, cudaStream_t st);
 int dag_max_ctas_per_sm(bool mixed, int use_umma);
@@ -190,7 +195,8 @@ cudaError_t launch_init_lbar(const double* Lt, double* Bt, int T, int Mt, long l
 // Partials of sum over stored lower entries of Abar_ij dK_ij/d(l, v, s2), dK recomputed from X; then
 // out[0..3) = the three sums. partial needs 3 * Mt(Mt+1)/2 * (T/32) doubles.
 cudaError_t launch_grad_contract(const double* Bt, int T, int Mt, const double* X, long long n, int D, double l,
-                                 double v, double* partial, double* out, cudaStream_t st);
+                                 double v, double* partial, double* out, cudaStream_t st,
+                                 const long long* Q = nullptr, const FxScale* fx = nullptr);
 // GMRES-based refinement: out[i] = <V_i, w> (i < k, rows of V with leading dimension ldv); w += sign * sum_j
 // h_j V_j (h on the device); dst = a * src; and the diagonal shift diag(K) += tau of the packed tiles.
 cudaError_t launch_multi_dot(const double* V, long long ldv, int k, const double* w, long long n, double* out,
