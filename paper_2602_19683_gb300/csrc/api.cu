@@ -125,6 +125,7 @@ struct gp_factor {
   DevBuf Xq, fx;              // fixed-point coordinates of X and their scale (the assembly of K)
   DevBuf Xq2, Xsq, fx2;       // X and the test points under one common scale (cross-covariance calls)
   DevBuf Lt32, Linv32;        // refined forms, T = 128 / 256: FP32 copies of the factor tiles and inverses
+  DevBuf Mch, Pch;            // and the FP32 solve's chain matrices (launch_chain_mats)
                               // (the correction solves' operands)
   bool has32 = false;         // Lt32 / Linv32 hold the current factor
   bool factored = false, alpha_valid = false;
@@ -306,7 +307,8 @@ gp_status solve_in_place(gp_ctx* c, gp_factor* f) {
       c->trace_tasks = c->trace_items.p;
       c->trace_ntasks = (int)nitems;
     }
-    GP_CUDA(gpk::launch_trsv32((const float*)f->Lt32.p, (const float*)f->Linv32.p, (double*)f->bvec.p,
+    GP_CUDA(gpk::launch_trsv32((const float*)f->Lt32.p, (const float*)f->Linv32.p, (const float*)f->Mch.p,
+                               (const float*)f->Pch.p, (double*)f->bvec.p,
                                (double*)f->xvec.p, (int*)f->cMean.p, T, Mt, ctas, c->d_status, c->cfg.timeout_ns,
                                withhold, trace, items, c->stream));
     count_launch(c);
@@ -682,6 +684,8 @@ gp_status gp_factor_free(gp_ctx* c, gp_factor* f) {
   release(f->gh);
   release(f->Lt32);
   release(f->Linv32);
+  release(f->Mch);
+  release(f->Pch);
   release(f->Xq);
   release(f->fx);
   release(f->Xq2);
@@ -790,7 +794,11 @@ gp_status make_f32_copy(gp_ctx* c, gp_factor* f) {
   GP_CUDA(gpk::launch_to_f32((const double*)f->Kt.p, (float*)f->Lt32.p, (long long)(ntiles * TT), c->sms, c->stream));
   GP_CUDA(gpk::launch_to_f32((const double*)f->Linv.p, (float*)f->Linv32.p, (long long)(f->Mt * TT), c->sms,
                              c->stream));
-  count_launch(c, 2);
+  GP_TRY(grow(f->Mch, (size_t)f->Mt * TT * sizeof(float)));
+  GP_TRY(grow(f->Pch, (size_t)f->Mt * TT * sizeof(float)));
+  GP_CUDA(gpk::launch_chain_mats((const float*)f->Lt32.p, (const float*)f->Linv32.p, (float*)f->Mch.p,
+                                 (float*)f->Pch.p, f->T, f->Mt, c->stream));
+  count_launch(c, f->Mt > 1 ? 3 : 2);
   f->has32 = true;
   return GP_OK;
 }

@@ -147,7 +147,7 @@ cudaError_t launch_factor_rows(const double* Kt, int T, long long n, long long r
 cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cudaStream_t st);
 // Blocked triangular solves with the factor in FP32 (trsv.cu), the correction solves of the refined
 // precision forms: b <- L^{-T} L^{-1} b on the packed lower FP32 tiles Lt (edge T = 128 or 256, Mt tile rows)
-// with the FP32 diagonal-tile inverses Linv; b (FP64) holds the right-hand side on entry and the solution
+// with the FP32 diagonal-tile inverses Linv and the chain's matrices M, P (launch_chain_mats); b (FP64) holds the right-hand side on entry and the solution
 // on exit, xb (FP64) receives the forward result; front (2 ints) must be zero on entry. One persistent
 // CTA per SM (grid, capped at Mt). withhold >= 0: test hook, that forward block is never published (its
 // dependants' bounded waits expire with GP_ERR_TIMEOUT). trace (optional, Mt(Mt+1) items): per item
@@ -155,9 +155,12 @@ cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cud
 // slot counter is st->next_task (zero on entry). trsv32_smem_bytes returns the dynamic shared memory of a
 // launch (and its stages), or -1 when the solve does not fit this kernel (T, or too many tile rows per CTA).
 int trsv32_smem_bytes(int T, int Mt, int grid, int* stages);
-cudaError_t launch_trsv32(const float* Lt, const float* Linv, double* b, double* xb, int* front, int T, int Mt,
-                          int grid, DevStatus* st, long long timeout_ns, int withhold, long long* trace,
-                          int4* trace_items, cudaStream_t stream);
+cudaError_t launch_trsv32(const float* Lt, const float* Linv, const float* M, const float* P, double* b, double* xb,
+                          int* front, int T, int Mt, int grid, DevStatus* st, long long timeout_ns, int withhold,
+                          long long* trace, int4* trace_items, cudaStream_t stream);
+// The chain's matrices of the FP32 solve, once per factor (Mt T^2 floats each): M_I = L_II^-1 L_{I,I-1}
+// (I >= 1) and P_J = L_{J+1,J} L_JJ^-1 (J <= Mt - 2), from the FP32 tiles and inverses. T = 128 or 256.
+cudaError_t launch_chain_mats(const float* Lt, const float* Linv, float* M, float* P, int T, int Mt, cudaStream_t stream);
 // dst[i] = (float)src[i] for i < n (the FP32 copy of the factor and of its diagonal-tile inverses).
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, int sms, cudaStream_t stream);
 cudaError_t launch_dag(const DagArgs& a, int grid, bool mixed, cudaStream_t st, bool reverse = false,

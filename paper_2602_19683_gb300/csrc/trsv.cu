@@ -3,14 +3,16 @@
 // FP32-accurate. The diagonal-block solves are products with the stored inverses of the diagonal tiles.
 // Right-hand side and solution are FP64 in memory; the tiles, the products and the sums are FP32.
 //
-// The solve is bound by HBM (4 bytes per value of L per sweep against one FMA) and by its dependency
-// chain. One persistent CTA per SM owns the tile rows I = c, c + G, c + 2G, ... (G CTAs). For the
-// forward sweep it walks the tile columns J = 0, 1, ... in order and, for each owned row I > J,
-// accumulates L_IJ beta_J into that row's sum (kept in shared memory) as soon as beta_J is published;
-// right after its last tile (I, I-1) it forms beta_I = Linv_I (b_I - sum) and publishes it. The
-// backward sweep mirrors this: the owner of block J accumulates L_IJ^T alpha_I for I = Mt-1, ..., J+1
-// and forms alpha_J = Linv_J^T (beta_J - sum). Blocks are published strictly in order (each one waits
-// for its predecessor), so one counter per sweep carries every dependency.
+// The solve is bound by its dependency chain (and by HBM: 4 bytes per value of L per sweep against one
+// FMA). One persistent CTA per SM owns the tile rows I = c, c + G, c + 2G, ... (G CTAs). For the forward
+// sweep it walks the tile columns J = 0, 1, ... in order and, for each owned row I, subtracts L_IJ beta_J
+// from that row's running right-hand side (kept in shared memory) as soon as beta_J is published. After
+// tile (I, I-2) it forms y_I = L_II^-1 (that right-hand side); the chain's step of row I is then the
+// single product beta_I = y_I - M_I beta_{I-1}, M_I = L_II^-1 L_{I,I-1} precomputed once per factor
+// (chain_mats_kernel), so the wait for beta_{I-1} is followed by one tile product only. The backward
+// sweep mirrors this: alpha_J = y_J - P_J^T alpha_{J+1}, P_J = L_{J+1,J} L_JJ^-1, y_J = L_JJ^-T (beta_J -
+// sum_{I > J+1} L_IJ^T alpha_I). Blocks are published strictly in order (each one waits for its
+// predecessor), so one counter per sweep carries every dependency.
 //
 // A CTA's tiles and inverses stream through shared memory as 64 KB row chunks moved by cp.async.bulk,
 // several stages ahead of the arithmetic and independent of the dependency waits (the factor does not
@@ -29,93 +31,144 @@ constexpr int kTsChunkBytes = 64 * 1024;
 constexpr int kTsMaxStages = 4;
 constexpr int kTsSmemLimit = 226 * 1024;  // dynamic shared memory cap (227 KB less the static part)
 
-enum : int { kFTile = 0, kFDiag = 1, kBTile = 2, kBDiag = 3 };
+// Item kinds. Forward (kind < 4): a tile product L_IJ beta_J (kFTile); the chain's step beta_I = y_I -
+// M_I beta_{I-1} with M_I = L_II^-1 L_{I,I-1} (kFFinal); y_I = L_II^-1 (the right-hand side less every
+// tile product but the last) (kFPrep); beta_0 = L_00^-1 b_0 (kFDiag). Backward mirrors them with
+// transposed products: L_IJ^T alpha_I, alpha_J = y_J - P_J^T alpha_{J+1} with P_J = L_{J+1,J} L_JJ^-1,
+// y_J = L_JJ^-T (...), alpha_{Mt-1} = L^-T beta_{Mt-1}.
+enum : int { kFTile = 0, kFFinal = 1, kFPrep = 2, kFDiag = 3, kBTile = 4, kBFinal = 5, kBPrep = 6, kBDiag = 7 };
 
 struct TsItem {
-  int kind, I, J;
+  int kind, I, J;  // the final steps carry (I, I - 1); the diagonal items (blk, blk)
 };
 
-// The sequence of work items of CTA c (rows c, c + G, ... owned), identical for its producer thread
-// and its consumers. Forward: the diagonal block 0 (owner of row 0), then per column J the owned rows
-// I > J in ascending order, the diagonal block I inserted right after tile (I, I-1). Backward: the
-// diagonal block Mt-1, then per row I = Mt-1, ..., 1 the owned blocks J < I in descending order, the
-// diagonal block J right after tile (J+1, J).
+// The sequence of work items of CTA c (rows c, c + G, ... owned), identical for its producer thread and
+// its consumers. Forward: beta_0 (owner of row 0), y_1 (owner of row 1); then per column J the chain's
+// step of row J + 1 (its owner) first, then the owned rows I >= J + 2 in ascending order, y_I right after
+// tile (I, I - 2), its last tile before the chain reaches it. Backward: alpha_{Mt-1}, y_{Mt-2}; then per row
+// I = Mt-1, ..., 1 the chain's step of block I - 1 first, then the owned blocks J <= I - 2 in descending
+// order, y_J right after tile (J + 2, J). The chain's steps wait only for the previous block; every
+// other product of a block is done a step ahead.
 struct TsIter {
-  int phase = 0;  // 0 forward, 1 backward, 2 done
-  int col = -1;   // forward: tile column J (-1: start); backward: tile row I (Mt: start)
+  int phase = 0;  // 0 forward start, 1 forward columns, 2 backward start, 3 backward rows, 4 done
+  int col = 0;    // forward: tile column J; backward: tile row I
   int k = 0;      // next owned-row index within the column / row
-  int pend = -1;  // diagonal block to emit next (-1: none)
+  int stage = 0;  // position within a start list, or 0/1 before/after a column's chain step
+  int pend = -1;  // y block to emit next (-1: none)
 };
 
-__device__ __forceinline__ int ts_kstart(int J, int c, int G) { return J < c ? 0 : (J - c) / G + 1; }
-__device__ __forceinline__ int ts_kmax(int I, int c, int G) { return I - 1 < c ? -1 : (I - 1 - c) / G; }
+__device__ __forceinline__ bool ts_own(int r, int c, int G, int Mt) { return r >= c && r < Mt && (r - c) % G == 0; }
+// first owned row index k with c + k G >= J + 2; last owned block index with c + k G <= I - 2 (-1: none)
+__device__ __forceinline__ int ts_kfirst(int J, int c, int G) { return J + 2 <= c ? 0 : (J + 2 - c + G - 1) / G; }
+__device__ __forceinline__ int ts_klast(int I, int c, int G) { return I - 2 < c ? -1 : (I - 2 - c) / G; }
 
 __device__ bool ts_next(TsIter& s, int c, int G, int Mt, TsItem& it) {
+  const int last = c + ((Mt - 1 - c) / G) * G;  // the CTA's last row
   for (;;) {
     if (s.pend >= 0) {
-      it = TsItem{s.phase == 0 ? kFDiag : kBDiag, s.pend, s.pend};
+      it = TsItem{s.phase < 2 ? kFPrep : kBPrep, s.pend, s.pend};
       s.pend = -1;
       return true;
     }
-    if (s.phase == 0) {
-      if (s.col < 0) {
-        s.col = 0;
-        s.k = ts_kstart(0, c, G);
-        if (c == 0) {
-          it = TsItem{kFDiag, 0, 0};
-          return true;
+    switch (s.phase) {
+      case 0:
+        if (s.stage == 0) {
+          s.stage = 1;
+          if (c == 0) {
+            it = TsItem{kFDiag, 0, 0};
+            return true;
+          }
         }
-        continue;
-      }
-      // no owned row below the diagonal past the CTA's last row: straight to the backward sweep
-      if (s.col > Mt - 2 || s.col >= c + ((Mt - 1 - c) / G) * G) {
+        if (s.stage == 1) {
+          s.stage = 2;
+          if (Mt > 1 && ts_own(1, c, G, Mt)) {
+            it = TsItem{kFPrep, 1, 1};
+            return true;
+          }
+        }
         s.phase = 1;
-        s.col = Mt;
+        s.col = 0;
+        s.stage = 0;
         continue;
-      }
-      const int I = c + s.k * G;
-      if (I < Mt) {
-        ++s.k;
-        if (I == s.col + 1) s.pend = I;
-        it = TsItem{kFTile, I, s.col};
-        return true;
-      }
-      ++s.col;
-      s.k = ts_kstart(s.col, c, G);
-      continue;
-    }
-    if (s.phase == 1) {
-      if (s.col == Mt) {
-        s.col = Mt - 1;
-        s.k = ts_kmax(Mt - 1, c, G);
-        if ((Mt - 1) % G == c) {
-          it = TsItem{kBDiag, Mt - 1, Mt - 1};
+      case 1: {
+        if (s.col > Mt - 2 || s.col >= last) {  // no owned row below this column's diagonal
+          s.phase = 2;
+          s.stage = 0;
+          continue;
+        }
+        if (s.stage == 0) {
+          s.stage = 1;
+          s.k = ts_kfirst(s.col, c, G);
+          if (ts_own(s.col + 1, c, G, Mt)) {
+            it = TsItem{kFFinal, s.col + 1, s.col};
+            return true;
+          }
+        }
+        const int I = c + s.k * G;
+        if (I < Mt) {
+          ++s.k;
+          if (I == s.col + 2) s.pend = I;
+          it = TsItem{kFTile, I, s.col};
           return true;
         }
+        ++s.col;
+        s.stage = 0;
         continue;
       }
-      if (s.col < 1) {
-        s.phase = 2;
+      case 2:
+        if (s.stage == 0) {
+          s.stage = 1;
+          if (ts_own(Mt - 1, c, G, Mt)) {
+            it = TsItem{kBDiag, Mt - 1, Mt - 1};
+            return true;
+          }
+        }
+        if (s.stage == 1) {
+          s.stage = 2;
+          if (Mt > 1 && ts_own(Mt - 2, c, G, Mt)) {
+            it = TsItem{kBPrep, Mt - 2, Mt - 2};
+            return true;
+          }
+        }
+        s.phase = 3;
+        s.col = Mt - 1;
+        s.stage = 0;
+        continue;
+      case 3: {
+        if (s.col <= c) {  // rows at or above the CTA's first block hold none of its items
+          s.phase = 4;
+          return false;
+        }
+        if (s.stage == 0) {
+          s.stage = 1;
+          s.k = ts_klast(s.col, c, G);
+          if (ts_own(s.col - 1, c, G, Mt)) {
+            it = TsItem{kBFinal, s.col, s.col - 1};
+            return true;
+          }
+        }
+        if (s.k >= 0) {
+          const int J = c + s.k * G;
+          --s.k;
+          if (J == s.col - 2) s.pend = J;
+          it = TsItem{kBTile, s.col, J};
+          return true;
+        }
+        --s.col;
+        s.stage = 0;
+        continue;
+      }
+      default:
         return false;
-      }
-      if (s.k >= 0) {
-        const int J = c + s.k * G;
-        --s.k;
-        if (J == s.col - 1) s.pend = J;
-        it = TsItem{kBTile, s.col, J};
-        return true;
-      }
-      --s.col;
-      s.k = ts_kmax(s.col, c, G);
-      continue;
     }
-    return false;
   }
 }
 
 struct TsArgs {
   const float* Lt;     // packed lower tiles of L (FP32), tile (I, J) at (I(I+1)/2 + J) T^2, row-major
   const float* Linv;   // Mt inverses of the diagonal tiles (FP32), T x T row-major (upper triangle not read)
+  const float* M;      // M_I = L_II^-1 L_{I,I-1} at I T^2 (I >= 1), T x T row-major
+  const float* P;      // P_J = L_{J+1,J} L_JJ^-1 at J T^2 (J <= Mt - 2), T x T row-major
   double* b;           // Mt*T: right-hand side on entry, alpha on exit
   double* xb;          // Mt*T: beta (forward result)
   int* front;          // [0]: forward blocks published, [1]: backward blocks published (zero on entry)
@@ -132,8 +185,13 @@ __device__ __forceinline__ size_t ts_tri(long long I, long long J) { return (siz
 
 __device__ __forceinline__ const float* ts_chunk_src(const TsArgs& a, const TsItem& it, int ch) {
   const size_t TT = (size_t)a.T * a.T, off = (size_t)ch * a.CR * a.T;
-  if (it.kind == kFDiag || it.kind == kBDiag) return a.Linv + (size_t)it.I * TT + off;
-  return a.Lt + ts_tri(it.I, it.J) * TT + off;
+  switch (it.kind) {
+    case kFFinal: return a.M + (size_t)it.I * TT + off;
+    case kBFinal: return a.P + (size_t)it.J * TT + off;
+    case kFTile:
+    case kBTile: return a.Lt + ts_tri(it.I, it.J) * TT + off;
+    default: return a.Linv + (size_t)it.I * TT + off;  // the diagonal items: (blk, blk)
+  }
 }
 
 // Thread 0: bounded wait until *p >= target. Returns the value seen (>= target), or -1 after a time-out
@@ -245,8 +303,11 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
   long long t_start = 0, t_ready = 0;
   while (ts_next(it_s, c, G, Mt, it)) {
     if (a.trace && t == 0) t_start = (long long)globaltimer();
-    const bool fwd = it.kind <= kFDiag;
-    const bool diag = it.kind == kFDiag || it.kind == kBDiag;
+    const bool fwd = it.kind < kBTile;
+    // diagonal items: the product with L_blk^-1 (or its transpose) of the running right-hand side
+    const bool diag = it.kind == kFDiag || it.kind == kFPrep || it.kind == kBDiag || it.kind == kBPrep;
+    const bool final = it.kind == kFFinal || it.kind == kBFinal;  // the chain's steps
+    const bool publish = final || it.kind == kFDiag || it.kind == kBDiag;
     const int blk = fwd ? it.I : it.J;  // the owned block this item contributes to
     float* accb = acc + (size_t)((blk - c) / G) * T;
     if (!diag) {
@@ -256,8 +317,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
           const int need = fwd ? it.J + 1 : Mt - it.I;
           int& known = fwd ? known_f : known_b;
           if (known < need) {
-            const bool urgent = fwd ? it.I == it.J + 1 : it.J == it.I - 1;  // the tile before a diagonal block
-            const int v = ts_wait(a.front + (fwd ? 0 : 1), need, urgent, a.st, a.timeout_ns, fwd ? it.J : it.I);
+            const int v = ts_wait(a.front + (fwd ? 0 : 1), need, final, a.st, a.timeout_ns, fwd ? it.J : it.I);
             if (v < 0)
               s_fail = 1;
             else
@@ -318,11 +378,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
         const float tot = warp_sum_rows<kR>(v, lane);
         if ((lane & (32 / kR - 1)) == 0) {
           const int r = r0 + w + 16 * warp_sum_row_of<kR>(lane);
-          if (diag) {
-            a.xb[(size_t)blk * T + r] = (double)tot;
-            accb[r] = tot;  // the backward sweep's right-hand side of this block starts at beta
-          } else {
+          if (it.kind == kFTile) {
             accb[r] -= tot;
+          } else if (it.kind == kFPrep) {
+            accb[r] = tot;  // y_I, the chain step's starting value
+          } else {  // beta (kFDiag: the product itself; kFFinal: y_I - M_I beta_{I-1})
+            const float beta = it.kind == kFDiag ? tot : accb[r] - tot;
+            a.xb[(size_t)blk * T + r] = (double)beta;
+            accb[r] = beta;  // the backward sweep's right-hand side of this block starts at beta
           }
         }
       } else {
@@ -360,14 +423,19 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
         float sum = 0.f;
 #pragma unroll
         for (int q = 0; q < NG; ++q) sum += red[(size_t)q * T + t];
-        if (diag)
-          a.b[(size_t)blk * T + t] = (double)sum;
-        else
+        if (it.kind == kBTile) {
           accb[t] -= sum;
+        } else if (it.kind == kBPrep) {
+          accb[t] = sum;  // y_J
+        } else {  // alpha (kBDiag: the product itself; kBFinal: y_J - P_J^T alpha_{J+1})
+          const float alpha = it.kind == kBDiag ? sum : accb[t] - sum;
+          accb[t] = alpha;
+          a.b[(size_t)blk * T + t] = (double)alpha;
+        }
       }
       __syncthreads();
     }
-    if (diag) {
+    if (publish) {
       const bool withheld = fwd && blk == a.withhold;
       __syncthreads();
       if (t == 0 && !withheld) {
@@ -377,7 +445,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
     }
     if (a.trace && t == 0) {
       const unsigned long long slot = atomicAdd(a.trace_next, 1ull);
-      const int kinds[4] = {TASK_FGEMV, TASK_FSOLVE, TASK_BGEMV, TASK_BSOLVE};
+      // chain steps and the first block as FSOLVE/BSOLVE, the y products as FSOLVE_C/BSOLVE_C
+      const int kinds[8] = {TASK_FGEMV, TASK_FSOLVE, TASK_FSOLVE_C, TASK_FSOLVE,
+                            TASK_BGEMV, TASK_BSOLVE, TASK_BSOLVE_C, TASK_BSOLVE};
       a.trace_items[slot] = make_int4(kinds[it.kind], it.I, it.J, 0);
       long long* rec = a.trace + 4 * slot;
       rec[0] = c;
@@ -389,6 +459,60 @@ __global__ void __launch_bounds__(kTsThreads, 1) trsv32_kernel(TsArgs a) {
   // after a failure: wait (bounded) for this CTA's copies still in flight before leaving
   if (fail && t == 0)
     for (int q = i; q < issued; ++q) mbar_wait(&full[q % S], (uint32_t)(q / S) & 1u, a.st, a.timeout_ns, -1);
+}
+
+// The chain's matrices, once per factor (FP32 products with FP32 sums): blockIdx.y = 0 writes
+// M_I = L_II^-1 L_{I,I-1} for I = blockIdx.x >= 1, blockIdx.y = 1 writes P_J = L_{J+1,J} L_JJ^-1 for
+// J = blockIdx.x <= Mt - 2. The inverses' upper triangles are masked (not read as data). T = 128 or 256:
+// four (or sixteen) 128 x 128 output quadrants, each thread an 8 x 8 block of one quadrant, k in chunks
+// of 16 staged in shared memory.
+template <int T>
+__global__ void __launch_bounds__(256) chain_mats_kernel(const float* __restrict__ Lt, const float* __restrict__ Linv,
+                                                         float* __restrict__ M, float* __restrict__ P, int Mt) {
+  __shared__ float As[128][17];
+  __shared__ float Bs[16][128];
+  const int b = blockIdx.x, t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const bool isM = blockIdx.y == 0;
+  if (isM ? b < 1 : b > Mt - 2) return;
+  const size_t TT = (size_t)T * T;
+  // A (row-major T x T) and B (row-major T x T); amask: A lower triangular, bmask: B lower triangular
+  const float* A = isM ? Linv + (size_t)b * TT : Lt + ts_tri(b + 1, b) * TT;
+  const float* B = isM ? Lt + ts_tri(b, b - 1) * TT : Linv + (size_t)b * TT;
+  float* C = (isM ? M : P) + (size_t)b * TT;
+  for (int q0 = 0; q0 < T; q0 += 128)
+    for (int q1 = 0; q1 < T; q1 += 128) {
+      float acc[8][8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+      for (int k0 = 0; k0 < T; k0 += 16) {
+        for (int e = t; e < 128 * 16; e += 256) {
+          const int r = e / 16, k = e % 16, gr = q0 + r, gk = k0 + k;
+          As[r][k] = (!isM || gk <= gr) ? A[(size_t)gr * T + gk] : 0.f;
+          const int kb = e / 128, cb = e % 128, gkb = k0 + kb, gc = q1 + cb;
+          Bs[kb][cb] = (isM || gc <= gkb) ? B[(size_t)gkb * T + gc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          float av[8], bv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) av[u] = As[ty * 8 + u][k];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) bv[v] = Bs[k][tx * 8 + v];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) C[(size_t)(q0 + ty * 8 + u) * T + q1 + tx * 8 + v] = acc[u][v];
+    }
 }
 
 }  // namespace
@@ -405,15 +529,29 @@ int trsv32_smem_bytes(int T, int Mt, int grid, int* stages) {
   return (int)((size_t)s * kTsChunkBytes + fixed);
 }
 
-cudaError_t launch_trsv32(const float* Lt, const float* Linv, double* b, double* xb, int* front, int T, int Mt,
-                          int grid, DevStatus* st, long long timeout_ns, int withhold, long long* trace,
-                          int4* trace_items, cudaStream_t stream) {
+cudaError_t launch_chain_mats(const float* Lt, const float* Linv, float* M, float* P, int T, int Mt, cudaStream_t stream) {
+  if (Mt < 2) return cudaSuccess;
+  const dim3 grid((unsigned)Mt, 2);
+  if (T == 128)
+    chain_mats_kernel<128><<<grid, 256, 0, stream>>>(Lt, Linv, M, P, Mt);
+  else if (T == 256)
+    chain_mats_kernel<256><<<grid, 256, 0, stream>>>(Lt, Linv, M, P, Mt);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsv32(const float* Lt, const float* Linv, const float* M, const float* P, double* b, double* xb,
+                          int* front, int T, int Mt, int grid, DevStatus* st, long long timeout_ns, int withhold,
+                          long long* trace, int4* trace_items, cudaStream_t stream) {
   int S = 0;
   const int smem = trsv32_smem_bytes(T, Mt, grid, &S);
   if (smem < 0) return cudaErrorInvalidValue;
   TsArgs a;
   a.Lt = Lt;
   a.Linv = Linv;
+  a.M = M;
+  a.P = P;
   a.b = b;
   a.xb = xb;
   a.front = front;
