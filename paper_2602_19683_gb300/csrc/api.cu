@@ -708,10 +708,10 @@ gp_status fx_quantize(gp_ctx* c, const double* A, long long na, const double* B,
   GP_TRY(grow(fx, sizeof(gpk::FxScale)));
   GP_TRY(grow(qa, (size_t)std::max(na, 1LL) * D * sizeof(long long)));
   if (qb) GP_TRY(grow(*qb, (size_t)std::max(nb, 1LL) * D * sizeof(long long)));
-  GP_CUDA(gpk::launch_fx_prepare(A, na, B, B ? nb : 0, D, l, (gpk::FxScale*)fx.p, c->stream));
+  GP_CUDA(gpk::launch_fx_prepare(A, na, B, B ? nb : 0, D, l, (gpk::FxScale*)fx.p, c->sms, c->stream));
   GP_CUDA(gpk::launch_fx_quantize(A, na * D, (const gpk::FxScale*)fx.p, (long long*)qa.p, c->sms, c->stream));
   if (qb) GP_CUDA(gpk::launch_fx_quantize(B, nb * D, (const gpk::FxScale*)fx.p, (long long*)qb->p, c->sms, c->stream));
-  count_launch(c, qb ? 3 : 2);
+  count_launch(c, qb ? 4 : 3);
   return GP_OK;
 }
 

@@ -23,8 +23,11 @@ struct DevStatus {
 // Fixed-point coordinates of the covariance assembly (se_kernel.cuh): the quantisation shared by the
 // point sets of one launch family (device resident, written by fx_prepare_kernel).
 struct FxScale {
-  int32_t F;       // q = round(x 2^F)
-  int32_t usable;  // 1: every quantised coordinate |q| < 2^58 and max |x| <= 64 l (the error bound holds)
+  int32_t F;                // q = round(x 2^F)
+  int32_t usable;           // 1: every quantised coordinate |q| < 2^58 and max |x| <= 64 l (the error bound holds)
+  unsigned long long smax;  // during the preparation: bit pattern of max |x| (orders like the value)
+  int32_t nonfinite;        // during the preparation: 1 if some coordinate is NaN or infinite
+  int32_t pad;
 };
 
 #ifdef __CUDACC__

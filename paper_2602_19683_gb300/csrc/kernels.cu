@@ -105,17 +105,16 @@ __device__ __forceinline__ FxScale fx_decide(double S, int nonfinite, int D, dou
   return r;
 }
 
-// Quantisation of one launch family: S = max |coordinate| over A (na x D) and B (nb x D); F = 57 -
-// floor(log2 S), so that |q| < 2^58; usable when S <= 64 l, 2F <= 1022, D <= 256 and every coordinate is
-// finite (a zero S quantises everything to 0 with F = 0). One CTA.
-__global__ void __launch_bounds__(1024) fx_prepare_kernel(const double* __restrict__ A, long long na,
-                                                          const double* __restrict__ B, long long nb, int D, double l,
-                                                          FxScale* out) {
-  __shared__ double red[32];
-  __shared__ int bad[32];
+// Quantisation of one launch family: S = max |coordinate| over A (na x D) and B (nb x D), reduced by
+// many CTAs into out->smax / out->nonfinite (zeroed beforehand), then fx_decide_kernel sets F and
+// usable (fx_decide).
+__global__ void __launch_bounds__(kThreads) fx_reduce_kernel(const double* __restrict__ A, long long na,
+                                                             const double* __restrict__ B, long long nb, int D,
+                                                             FxScale* out) {
   double mx = 0.0;
   int nonfinite = 0;
-  for (long long e = threadIdx.x; e < (na + nb) * D; e += blockDim.x) {
+  const long long total = (na + nb) * D;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const double x = e < na * D ? A[e] : B[e - na * D];
     if (!(fabs(x) <= 1.7976931348623157e308)) nonfinite = 1;
     else mx = fmax(mx, fabs(x));
@@ -126,19 +125,15 @@ __global__ void __launch_bounds__(1024) fx_prepare_kernel(const double* __restri
     nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
   }
   if (threadIdx.x % 32 == 0) {
-    red[threadIdx.x / 32] = mx;
-    bad[threadIdx.x / 32] = nonfinite;
+    if (mx > 0.0) atomicMax(&out->smax, (unsigned long long)__double_as_longlong(mx));
+    if (nonfinite) atomicOr(&out->nonfinite, 1);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double S = 0.0;
-    int nf = 0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-      S = fmax(S, red[w]);
-      nf |= bad[w];
-    }
-    *out = fx_decide(S, nf, D, l);
-  }
+}
+
+__global__ void fx_decide_kernel(int D, double l, FxScale* out) {
+  const FxScale r = fx_decide(__longlong_as_double((long long)out->smax), out->nonfinite, D, l);
+  out->F = r.F;
+  out->usable = r.usable;
 }
 
 // Q[e] = round(X[e] 2^F) (nothing when the scale is not usable).
@@ -1454,8 +1449,13 @@ cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, c
 }
 
 cudaError_t launch_fx_prepare(const double* A, long long na, const double* B, long long nb, int D, double l, FxScale* out,
-                              cudaStream_t st) {
-  fx_prepare_kernel<<<1, 1024, 0, st>>>(A, na, B, nb, D, l, out);
+                              int sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(FxScale), st);
+  if (e != cudaSuccess) return e;
+  const long long want = ((na + nb) * D + kThreads - 1) / kThreads;
+  const long long grid = want < 1 ? 1 : (want < (long long)sms * 4 ? want : (long long)sms * 4);
+  fx_reduce_kernel<<<(unsigned)grid, kThreads, 0, st>>>(A, na, B, nb, D, out);
+  fx_decide_kernel<<<1, 1, 0, st>>>(D, l, out);
   return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ struct DagArgs {
 // the FP64 distance). With a usable scale the squared distances are exact integer sums (se_kernel.cuh).
 cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, cudaStream_t st);
 cudaError_t launch_fx_prepare(const double* A, long long na, const double* B, long long nb, int D, double l, FxScale* out,
-                              cudaStream_t st);
+                              int sms, cudaStream_t st);
 cudaError_t launch_fx_quantize(const double* X, long long cnt, const FxScale* fx, long long* Q, int sms, cudaStream_t st);
 cudaError_t launch_assemble_tiles(const double* X, long long n, int D, double l, double v, double s2, double* Kt, int T,
                                   int Mt, cudaStream_t st, const long long* Q = nullptr, const FxScale* fx = nullptr);
