@@ -358,6 +358,14 @@ gp_status gp_debug_tile_product(gp_ctx* ctx, int32_t precision, const double* A,
  * giving +0 and NaN staying NaN. Asynchronous. */
 gp_status gp_debug_exp_neg(gp_ctx* ctx, const double* x, int64_t n, double* out);
 
+/* TEST HOOK (host only, no GPU needed): the work items, in order, of CTA `cta` of the FP32 correction
+ * solve's persistent kernel run with `ctas` CTAs on Mt tile rows, as {kind, I, J} int32 triples in out
+ * (host, 3 x cap). Kinds: 0 forward tile (I, J), 1 forward chain step of block I (J = I - 1), 2 forward
+ * y product of block I, 3 the first forward block (0), 4-7 the same for the backward sweep (the chain
+ * step of block J carries I = J + 1). Returns the number of items (out may be null), -1 on invalid
+ * arguments. */
+int64_t gp_debug_solve_items(int32_t Mt, int32_t ctas, int32_t cta, int32_t* out, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

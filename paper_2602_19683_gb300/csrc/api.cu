@@ -1080,6 +1080,10 @@ gp_status gp_solve(gp_ctx* c, gp_factor* f, const double* b, double* x) {
   return GP_OK;
 }
 
+int64_t gp_debug_solve_items(int32_t Mt, int32_t ctas, int32_t cta, int32_t* out, int64_t cap) {
+  return gpk::trsv32_items(Mt, ctas, cta, out, cap);
+}
+
 gp_status gp_debug_exp_neg(gp_ctx* c, const double* x, int64_t n, double* out) {
   if (!c || n < 0 || (n > 0 && (!x || !out))) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));

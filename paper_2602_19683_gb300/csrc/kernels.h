@@ -155,6 +155,10 @@ cudaError_t launch_logdet(const double* Kt, int T, long long n, double* out, cud
 // slot counter is st->next_task (zero on entry). trsv32_smem_bytes returns the dynamic shared memory of a
 // launch (and its stages), or -1 when the solve does not fit this kernel (T, or too many tile rows per CTA).
 int trsv32_smem_bytes(int T, int Mt, int grid, int* stages);
+// The solve kernel's item sequence of CTA c out of G (capped at Mt), computed on the host by the same
+// iterator the kernel runs: {kind, I, J} triples (kinds 0-7: forward tile, chain step, y product, first
+// block; backward the same); returns the count (out may be null), -1 on invalid arguments.
+long long trsv32_items(int Mt, int G, int c, int* out, long long cap);
 cudaError_t launch_trsv32(const float* Lt, const float* Linv, const float* M, const float* P, double* b, double* xb,
                           int* front, int T, int Mt, int grid, DevStatus* st, long long timeout_ns, int withhold,
                           long long* trace, int4* trace_items, cudaStream_t stream);

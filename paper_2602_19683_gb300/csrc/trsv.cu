@@ -57,12 +57,12 @@ struct TsIter {
   int pend = -1;  // y block to emit next (-1: none)
 };
 
-__device__ __forceinline__ bool ts_own(int r, int c, int G, int Mt) { return r >= c && r < Mt && (r - c) % G == 0; }
+__host__ __device__ __forceinline__ bool ts_own(int r, int c, int G, int Mt) { return r >= c && r < Mt && (r - c) % G == 0; }
 // first owned row index k with c + k G >= J + 2; last owned block index with c + k G <= I - 2 (-1: none)
-__device__ __forceinline__ int ts_kfirst(int J, int c, int G) { return J + 2 <= c ? 0 : (J + 2 - c + G - 1) / G; }
-__device__ __forceinline__ int ts_klast(int I, int c, int G) { return I - 2 < c ? -1 : (I - 2 - c) / G; }
+__host__ __device__ __forceinline__ int ts_kfirst(int J, int c, int G) { return J + 2 <= c ? 0 : (J + 2 - c + G - 1) / G; }
+__host__ __device__ __forceinline__ int ts_klast(int I, int c, int G) { return I - 2 < c ? -1 : (I - 2 - c) / G; }
 
-__device__ bool ts_next(TsIter& s, int c, int G, int Mt, TsItem& it) {
+__host__ __device__ bool ts_next(TsIter& s, int c, int G, int Mt, TsItem& it) {
   const int last = c + ((Mt - 1 - c) / G) * G;  // the CTA's last row
   for (;;) {
     if (s.pend >= 0) {
@@ -516,6 +516,23 @@ __global__ void __launch_bounds__(256) chain_mats_kernel(const float* __restrict
 }
 
 }  // namespace
+
+long long trsv32_items(int Mt, int G, int c, int* out, long long cap) {
+  if (Mt < 1 || G < 1 || c < 0 || c >= (G < Mt ? G : Mt)) return -1;
+  G = G < Mt ? G : Mt;
+  TsIter s;
+  TsItem it{0, 0, 0};
+  long long n = 0;
+  while (ts_next(s, c, G, Mt, it)) {
+    if (out && n < cap) {
+      out[3 * n] = it.kind;
+      out[3 * n + 1] = it.I;
+      out[3 * n + 2] = it.J;
+    }
+    ++n;
+  }
+  return n;
+}
 
 int trsv32_smem_bytes(int T, int Mt, int grid, int* stages) {
   if ((T != 128 && T != 256) || grid < 1 || Mt < 1) return -1;
