@@ -366,6 +366,12 @@ gp_status gp_debug_exp_neg(gp_ctx* ctx, const double* x, int64_t n, double* out)
  * arguments. */
 int64_t gp_debug_solve_items(int32_t Mt, int32_t ctas, int32_t cta, int32_t* out, int64_t cap);
 
+/* TEST HOOK (host only): the covariance assembly's squared distance from fixed-point coordinates,
+ * sum_d (qa[d] - qb[d])^2 2^-twoF rounded once to FP64 by the same integer routines the kernels run.
+ * qa, qb: host arrays of D values with |q| < 2^58; 1 <= D <= 256, twoF <= 1022 (normal or zero
+ * results). Writes *out; GP_ERR_INVALID_ARG outside those ranges. */
+gp_status gp_debug_fx_sqdist(const int64_t* qa, const int64_t* qb, int32_t D, int32_t twoF, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ SIGNATURES = {
     "gp_solve": ([_P, _P, _P, _P], _I32),
     "gp_debug_exp_neg": ([_P, _P, _I64, _P], _I32),
     "gp_debug_solve_items": ([_I32, _I32, _I32, _P, _I64], _I64),
+    "gp_debug_fx_sqdist": ([_P, _P, _I32, _I32, ctypes.POINTER(_D)], _I32),
     "gp_nlml_grad": ([_P, _P, _P, _I64, _I32, gp_hyper, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I32),
     "gp_batch_create": ([_P, _I32, ctypes.POINTER(gp_batch_desc), ctypes.POINTER(_P)], _I32),
     "gp_batch_run": ([_P, _P], _I32),

@@ -1080,6 +1080,15 @@ gp_status gp_solve(gp_ctx* c, gp_factor* f, const double* b, double* x) {
   return GP_OK;
 }
 
+gp_status gp_debug_fx_sqdist(const int64_t* qa, const int64_t* qb, int32_t D, int32_t twoF, double* out) {
+  if (!qa || !qb || !out || D < 1 || D > 256 || twoF > 1022 || twoF < -896) return GP_ERR_INVALID_ARG;
+  const long long lim = 1LL << 58;
+  for (int d = 0; d < D; ++d)
+    if (qa[d] <= -lim || qa[d] >= lim || qb[d] <= -lim || qb[d] >= lim) return GP_ERR_INVALID_ARG;
+  *out = gpk::fx_sqdist_host((const long long*)qa, (const long long*)qb, D, twoF);
+  return GP_OK;
+}
+
 int64_t gp_debug_solve_items(int32_t Mt, int32_t ctas, int32_t cta, int32_t* out, int64_t cap) {
   return gpk::trsv32_items(Mt, ctas, cta, out, cap);
 }

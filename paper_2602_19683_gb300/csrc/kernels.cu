@@ -1441,6 +1441,12 @@ __global__ void exp_neg_kernel(const double* __restrict__ x, long long n, double
     out[i] = exp_neg(x[i]);
 }
 
+double fx_sqdist_host(const long long* qa, const long long* qb, int D, int twoF) {
+  U128 acc{0ull, 0ull};
+  for (int d = 0; d < D; ++d) fx_add_sq(acc, qa[d], qb[d]);
+  return fx_to_double(acc, twoF);
+}
+
 cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const long long want = (n + kThreads - 1) / kThreads;

@@ -127,6 +127,9 @@ struct DagArgs {
 // scale fx (launch_fx_prepare over every point set of the call, then launch_fx_quantize per set; null:
 // the FP64 distance). With a usable scale the squared distances are exact integer sums (se_kernel.cuh).
 cudaError_t launch_exp_neg(const double* x, long long n, double* out, int sms, cudaStream_t st);
+// The assembly's fixed-point squared distance sum_d (qa_d - qb_d)^2 2^-twoF, run on the host by the same
+// integer routines (se_kernel.cuh).
+double fx_sqdist_host(const long long* qa, const long long* qb, int D, int twoF);
 cudaError_t launch_fx_prepare(const double* A, long long na, const double* B, long long nb, int D, double l, FxScale* out,
                               int sms, cudaStream_t st);
 cudaError_t launch_fx_quantize(const double* X, long long cnt, const FxScale* fx, long long* Q, int sms, cudaStream_t st);

@@ -16,6 +16,8 @@
 //    operations. About ten FP64 operations; results within one ulp of exp (checked against CUDA's exp in
 //    tests/test_gpu_se_kernel.py).
 #pragma once
+#include <string.h>
+
 #include "common.cuh"
 #include "exp_table.cuh"
 
@@ -47,20 +49,37 @@ struct U128 {
   unsigned long long lo, hi;
 };
 
+// High 64 bits of u * u and leading zeros of a nonzero word, on the device and on the host (the host
+// build serves the exactness test of these routines).
+__host__ __device__ __forceinline__ unsigned long long fx_mulhi(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(u, u);
+#else
+  return (unsigned long long)(((unsigned __int128)u * u) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ int fx_clz(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return __builtin_clzll(x);
+#endif
+}
+
 // s += (qa - qb)^2 exactly (|qa|, |qb| < 2^58, so the square is below 2^118 and D <= 256 terms fit).
-__device__ __forceinline__ void fx_add_sq(U128& s, long long qa, long long qb) {
+__host__ __device__ __forceinline__ void fx_add_sq(U128& s, long long qa, long long qb) {
   const long long t = qa - qb;
   const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
-  const unsigned long long lo = u * u, hi = __umul64hi(u, u);
+  const unsigned long long lo = u * u, hi = fx_mulhi(u);
   s.lo += lo;
   s.hi += hi + (s.lo < lo ? 1ull : 0ull);
 }
 
 // s 2^(-twoF) rounded to nearest-even FP64, with integer operations (the result is assumed normal or
 // zero: twoF <= 1022 and s < 2^128).
-__device__ __forceinline__ double fx_to_double(U128 s, int twoF) {
+__host__ __device__ __forceinline__ double fx_to_double(U128 s, int twoF) {
   if ((s.hi | s.lo) == 0ull) return 0.0;
-  const int lz = s.hi ? __clzll(s.hi) : 64 + __clzll(s.lo);
+  const int lz = s.hi ? fx_clz(s.hi) : 64 + fx_clz(s.lo);
   unsigned long long h, l;  // s << lz: the leading one at bit 127
   if (lz == 0) {
     h = s.hi;
@@ -80,7 +99,14 @@ __device__ __forceinline__ double fx_to_double(U128 s, int twoF) {
     mant >>= 1;
     ++e;
   }
-  return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  const unsigned long long bits = ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double r;
+  memcpy(&r, &bits, sizeof(r));
+  return r;
+#endif
 }
 
 }  // namespace gpk
