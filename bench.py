@@ -30,10 +30,15 @@ sys.path.insert(0, ROOT)
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~2 GHz on 152 SMs)
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one FP64 Cholesky launch of the task-DAG
-# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.072 GB read + 2.594 GB written.
+# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.070 GB read + 2.613 GB written.
 # Traffic follows the number of tile updates,
 # (Mt^3 - Mt)/6, so a launch with Mt tile rows of edge 256 moves this times updates(Mt)/updates(32).
-FP64_CHOL_TRAFFIC_MT32_T256 = 2.072146688e9 + 2.593921536e9
+FP64_CHOL_TRAFFIC_MT32_T256 = 2.069696512e9 + 2.612768512e9
+
+
+def tile_updates(mt: int) -> int:
+    """Trailing tile updates (SYRK + GEMM) of a tiled Cholesky with mt tile rows."""
+    return (mt ** 3 - mt) // 6
 
 
 _TF32_MEASURED = {}
@@ -86,9 +91,10 @@ def tf32_peak_tflops():
     return bf16 * 1.1 / 2.25, f"{src} BF16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
 
 
-# DRAM bytes (read + written) of one mixed-precision Cholesky launch at n = 32768, tile 128, from an
-# ncu capture of the whole launch (dram__bytes_read.sum + dram__bytes_write.sum, one pass).
-MIXED_CHOL_TRAFFIC_N32768_T128 = 630.63e9 + 74.45e9
+# DRAM bytes (read + written) of one 3xTF32 Cholesky launch captured with ncu at n = 16384, tile 128
+# (128 tile rows; dram__bytes_read.sum + dram__bytes_write.sum): 17.735 GB read + 9.862 GB written.
+# Like the FP64 launch's, the traffic is scaled to other sizes by the number of tile updates.
+MIXED_CHOL_TRAFFIC_MT128_T128 = 17.734678016e9 + 9.862176000e9
 
 
 def hbm_peak_gbs():
@@ -125,7 +131,8 @@ def mixed_cholesky_roofline(n: int, tile: int, chol_s: float, prec: str = "fp32"
     nprod, kind, label = FORM_PRODUCTS[prec]
     peak, peak_src = tf32_peak_tflops() if kind == "tf32" else bf16_peak_tflops()
     executed = nprod * (n ** 3 / 3) / chol_s / 1e12
-    traffic = MIXED_CHOL_TRAFFIC_N32768_T128 if (n, tile, prec) == (32768, 128, "fp32") else None
+    traffic = (MIXED_CHOL_TRAFFIC_MT128_T128 * tile_updates(-(-n // tile)) / tile_updates(128)
+               if (tile, prec) == (128, "fp32") else None)
     r = {"kernel": f"dag_kernel mixed (tiled Cholesky, {label} on tcgen05)", "bound": "tensor",
          "achieved": executed, "peak": peak, "unit": "TFLOP/s", "frac": executed / peak,
          "peak_source": peak_src, "algorithmic_tflops": (n ** 3 / 3) / chol_s / 1e12, "traffic": traffic}
@@ -133,16 +140,15 @@ def mixed_cholesky_roofline(n: int, tile: int, chol_s: float, prec: str = "fp32"
         hbm, src = hbm_peak_gbs()
         r["traffic_gbs"] = traffic / chol_s / 1e9
         r["traffic_frac_of_hbm"] = traffic / chol_s / 1e9 / hbm
-        r["traffic_note"] = (f"bytes per launch, ncu capture of the n=32768 launch; rate vs the {src} HBM copy "
-                             f"peak {hbm:.0f} GB/s: the updates stream their packed operands from HBM")
+        r["traffic_note"] = (f"bytes per launch, ncu capture at n=16384 scaled by the tile-update count; rate vs "
+                             f"the {src} HBM copy peak {hbm:.0f} GB/s")
     return r
 
 
 def fp64_cholesky_traffic(n: int, tile: int):
     if tile != 256:
         return None
-    mt = (n + tile - 1) // tile
-    return FP64_CHOL_TRAFFIC_MT32_T256 * (mt ** 3 - mt) / (32 ** 3 - 32)
+    return FP64_CHOL_TRAFFIC_MT32_T256 * tile_updates(-(-n // tile)) / tile_updates(32)
 
 
 def algorithmic_flops(n: int, m: int) -> float:
@@ -195,6 +201,8 @@ def parse():
                    help="FP64 tile-algorithm variant of the Cholesky graph (cfg.tile_variant)")
     p.add_argument("--e2e-steps", type=int, default=3, help="timed steps of the end-to-end pass (at most --steps)")
     p.add_argument("--no-vendor", action="store_true", help="skip the cuSOLVER/cuBLAS baseline leg")
+    p.add_argument("--forms", default="", help="comma-separated further precision forms timed on the same workload "
+                   "beside the FP64 run, each with its errors against it (bf16x6, bf16x3, tf32, bf16)")
     p.add_argument("--locality-order", default="default", choices=["default", "on", "off"],
                    help="tensor-core forms: start grouped updates that share a packed operand back to back "
                         "(cfg.locality_order; the library's default is on)")
@@ -202,7 +210,11 @@ def parse():
     p.add_argument("--cpu-m", type=int, default=1024)
     p.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference-arm step")
     p.add_argument("--ref-m", type=int, default=512)
-    return p.parse_args()
+    args = p.parse_args()
+    bad = [f for f in args.forms.split(",") if f and f not in ("bf16x6", "bf16x3", "tf32", "bf16")]
+    if bad:
+        p.error(f"--forms: unknown form(s) {bad}")
+    return args
 
 
 def world():
@@ -350,6 +362,8 @@ def form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, m
     cov_x = torch.empty_like(cov64)
     iters = [0]
     ph_ev = []
+    # the single-product forms factor K + tau I: they give the mean only (no covariance, no log det K)
+    shifted = prec in ("tf32", "bf16")
 
     def step_x(record=False):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
@@ -364,7 +378,8 @@ def form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, m
         _, iters[0] = api.gp_predict_mean(cx, fx[0], yd, Xsd, out=mean_x, want_iters=True)
         if record:
             evs[3].record(stream)
-        api.gp_predict_full_cov(cx, fx[0], Xsd, out=cov_x)
+        if not shifted:
+            api.gp_predict_full_cov(cx, fx[0], Xsd, out=cov_x)
         if record:
             evs[4].record(stream)
             ph_ev.append(evs)
@@ -383,7 +398,7 @@ def form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, m
     api.gp_sync(cx)
     msx = m0.elapsed_time(m1) / args.steps
     phase = [sum(e[k].elapsed_time(e[k + 1]) for e in ph_ev) / len(ph_ev) / 1e3 for k in range(4)]
-    logdet_x = api.gp_logdet(cx, fx[0])
+    logdet_x = None if shifted else api.gp_logdet(cx, fx[0])
 
     def relerr(a, b):
         return float((a - b).abs().max() / b.abs().max())
@@ -392,14 +407,23 @@ def form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, m
                     "FP64 iterative refinement of the mean",
             "fp64_ozaki": "FP64-accurate products from seven 8-bit digits per value on the BF16 tensor cores "
                           "(28 digit products, integer recombination), FP64 POTRF and diagonal-tile inverses, "
-                          "no refinement"}[prec]
+                          "no refinement",
+            "bf16x6": "three BF16 slices per value, six products per update on tcgen05, FP64 POTRF, "
+                      "FP64 iterative refinement of the mean",
+            "bf16x3": "two BF16 slices per value, three products per update on tcgen05, FP64 POTRF, "
+                      "FP64 iterative refinement of the mean",
+            "tf32": "one TF32 product per update on K + shift I, FP64 POTRF, GMRES refinement of the mean in FP64",
+            "bf16": "one BF16 product per update on K + shift I, FP64 POTRF, GMRES refinement of the mean in FP64"}[prec]
+    stats = api.gp_factor_stats(cx, fx[0])
     out = {"precision": desc, "tile": tile,
            "roofline": mixed_cholesky_roofline(n, tile, phase[1], prec),
            "s_per_solve": msx / 1e3, "tflops": algorithmic_flops(n, m) / (msx / 1e3) / 1e12,
            "speedup_vs_fp64": ms64 / msx, "ir_iterations": iters[0],
            "phases_s": {"assemble": phase[0], "cholesky": phase[1], "mean": phase[2], "full_cov": phase[3]},
-           "mean_err_vs_fp64": relerr(mean_x, mean64), "cov_err_vs_fp64": relerr(cov_x, cov64),
-           "logdet_err_vs_fp64": abs(logdet_x - logdet64) / abs(logdet64)}
+           "mean_err_vs_fp64": relerr(mean_x, mean64),
+           "cov_err_vs_fp64": None if shifted else relerr(cov_x, cov64),
+           "logdet_err_vs_fp64": None if shifted else abs(logdet_x - logdet64) / abs(logdet64),
+           "backward_error": stats["eta"], "shift": stats["shift"]}
     fx[0].free()
     cx.close()
     return out
@@ -514,7 +538,8 @@ def run_ours(args):
         if args.precision == "fp64":
             mean64, cov64 = mean.clone(), cov.clone()
             logdet64 = api.gp_logdet(ctx, fac[0])
-            for prec in ([] if args.no_mixed else ["fp32"]) + ([] if args.no_emulated else ["fp64_ozaki"]):
+            extra = [f for f in args.forms.split(",") if f]
+            for prec in ([] if args.no_mixed else ["fp32"]) + ([] if args.no_emulated else ["fp64_ozaki"]) + extra:
                 legs[prec] = form_leg(api, torch, args, local, stream, dev, Xd, yd, Xsd, h, prec, n, m, ms,
                                       mean64, cov64, logdet64, barrier)
         mixed = legs.get("fp32")
@@ -550,6 +575,8 @@ def run_ours(args):
         line["mixed"] = mixed
     if "fp64_ozaki" in legs:
         line["fp64_emulated"] = legs["fp64_ozaki"]
+    if any(p not in ("fp32", "fp64_ozaki") for p in legs):
+        line["forms"] = {p: v for p, v in legs.items() if p not in ("fp32", "fp64_ozaki")}
     if args.trace and rank == 0:
         line["trace"] = traced_cholesky(api, local, Xd, h, args)
     if e2e:

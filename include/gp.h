@@ -117,10 +117,13 @@ typedef struct {
                              group back to back when their longest-path rank is within 10 % of the best
                              ready task's (they then read the shared operand from L2): 0 or 1 = on (the
                              default), -1 = off (longest-path order only)                              */
-  double shift;           /* GP_TF32 / GP_BF16 only: the factorised matrix is K + shift I (the stored FP64 K and
-                             every result keep K itself): > 0 fixed; 0 = automatic, u sqrt(n) max K_ii
-                             (u = 2^-11 / 2^-8) times 8 after each non-positive pivot, at most five
-                             tries (gp_cholesky then waits for the stream); < 0 = no shift             */
+  double shift;           /* GP_TF32 / GP_BF16 only: the factorised matrix is K + shift I (the stored FP64 K
+                             keeps K itself, and the GMRES-refined mean solves with K): > 0 fixed; 0 =
+                             automatic, u sqrt(n) max K_ii (u = 2^-11 / 2^-8) times 8 after each
+                             non-positive pivot, at most five tries (gp_cholesky then waits for the
+                             stream); < 0 = no shift. A factor that carries a shift serves the mean
+                             only: gp_predict_full_cov, gp_predict_var and gp_logdet return
+                             GP_ERR_INVALID_ARG for it, and gp_nlml_grad needs shift < 0          */
   int32_t tile_variant;    /* GP_FP64 Cholesky graph (Sec. 3.2 names the three tile-algorithm variants):
                              0 = right-looking (each column's trailing updates as separate tasks, longest-
                              path order; the default), 1 = left-looking, 2 = top-looking (all updates of a
@@ -160,21 +163,25 @@ gp_status gp_cholesky(gp_ctx* ctx, gp_factor* K);
 gp_status gp_predict_mean(gp_ctx* ctx, gp_factor* L, const double* y, const double* Xs, int64_t m,
                           double* mean_out, int32_t* ir_iters_out);
 
-/* Eq. (3): cov (m x m, both triangles written) = K_{Xs,Xs} - V^T V with L V = K_{X,Xs}. */
+/* Eq. (3): cov (m x m, both triangles written) = K_{Xs,Xs} - V^T V with L V = K_{X,Xs}.
+ * GP_ERR_INVALID_ARG for a factor of K + shift I (single-product forms with a shift). */
 gp_status gp_predict_full_cov(gp_ctx* ctx, gp_factor* L, const double* Xs, int64_t m, double* cov_out);
 
 /* Predictive variances only, the diagonal of Eq. (3) (the paper notes that the diagonal of the
  * posterior covariance holds the predictive variances, Sec. 3.1): var[j] = k(xs_j, xs_j) - ||V_:,j||^2
- * with L V = K_{X,Xs}, without forming V^T V. var_out: device, m. */
+ * with L V = K_{X,Xs}, without forming V^T V. var_out: device, m. GP_ERR_INVALID_ARG for a factor of
+ * K + shift I. */
 gp_status gp_predict_var(gp_ctx* ctx, gp_factor* L, const double* Xs, int64_t m, double* var_out);
 
-/* log det K = 2 sum log L_ii of the factor (host output; waits for the stream). */
+/* log det K = 2 sum log L_ii of the factor (host output; waits for the stream). GP_ERR_INVALID_ARG for
+ * a factor of K + shift I. */
 gp_status gp_logdet(gp_ctx* ctx, gp_factor* L, double* out);
 
 /* Negative log marginal likelihood and its gradient w.r.t. (l, v, s2) at h, for device X (n x D) and
  * y (n): assembles K, factors it, solves for alpha, then runs the blocked Cholesky adjoint to obtain
  * Kbar = 1/2 (K^{-1} - alpha alpha^T) tile by tile and contracts it with dK/dtheta recomputed from X
- * (dK is never stored). Host outputs; waits for the stream. */
+ * (dK is never stored). Host outputs; waits for the stream. GP_TF32 / GP_BF16 need cfg.shift < 0 (an
+ * unshifted factor of K), else GP_ERR_INVALID_ARG. */
 gp_status gp_nlml_grad(gp_ctx* ctx, const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
                        double* nlml_out, double grad_out[3]);
 

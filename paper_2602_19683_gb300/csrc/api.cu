@@ -822,6 +822,7 @@ gp_status gp_cholesky(gp_ctx* c, gp_factor* f) {
   a.Linv = (double*)f->Linv.p;
   if (packed_operands(c, f)) a.Pk = (uint8_t*)f->Pk.p;
   if (packed_operands(c, f) && f->T == 128) a.PLinv = (uint8_t*)f->PLinv.p;
+  f->shift = 0.0;
   if (!single_product(f->precision)) {
     GP_TRY(run_dag(c, a, tb, mixed));
     GP_TRY(make_f32_copy(c, f));
@@ -951,6 +952,7 @@ gp_status gp_predict_mean(gp_ctx* c, gp_factor* f, const double* y, const double
 
 gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, double* cov_out) {
   if (!c || !f || m < 0 || (m > 0 && (!Xs || !cov_out)) || !f->factored) return GP_ERR_INVALID_ARG;
+  if (f->shift != 0) return GP_ERR_INVALID_ARG;  // a factor of K + tau I gives no Eq. 3 covariance of K
   if (m == 0) return GP_OK;
   if (m > 8 * 65535LL || f->Mt * (long long)f->T > 8 * 65535LL) return GP_ERR_INVALID_ARG;  // dense-assembly grid
   GP_CUDA(cudaSetDevice(c->device));
@@ -1001,6 +1003,7 @@ gp_status gp_predict_full_cov(gp_ctx* c, gp_factor* f, const double* Xs, int64_t
 
 gp_status gp_predict_var(gp_ctx* c, gp_factor* f, const double* Xs, int64_t m, double* var_out) {
   if (!c || !f || m < 0 || (m > 0 && (!Xs || !var_out)) || !f->factored) return GP_ERR_INVALID_ARG;
+  if (f->shift != 0) return GP_ERR_INVALID_ARG;  // shifted factor (see gp_predict_full_cov)
   if (m == 0) return GP_OK;
   if (m > 8 * 65535LL || f->Mt * (long long)f->T > 8 * 65535LL) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
@@ -1102,7 +1105,7 @@ gp_status gp_debug_exp_neg(gp_ctx* c, const double* x, int64_t n, double* out) {
 }
 
 gp_status gp_logdet(gp_ctx* c, gp_factor* f, double* out) {
-  if (!c || !f || !out || !f->factored) return GP_ERR_INVALID_ARG;
+  if (!c || !f || !out || !f->factored || f->shift != 0) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   GP_CUDA(gpk::launch_logdet((const double*)f->Kt.p, f->T, f->n, c->d_scalar, c->stream));
   count_launch(c);
@@ -1114,6 +1117,9 @@ gp_status gp_logdet(gp_ctx* c, gp_factor* f, double* out) {
 gp_status gp_nlml_grad(gp_ctx* c, const double* X, const double* y, int64_t n, int32_t D, gp_hyper h,
                        double* nlml_out, double grad_out[3]) {
   if (!c || !X || !y || !nlml_out || !grad_out || n < 1 || D < 1 || !valid_hyper(h)) return GP_ERR_INVALID_ARG;
+  // log det K and the adjoint need a factor of K itself: the single-product forms factor K + tau I
+  // unless cfg.shift < 0
+  if (single_product(c->cfg.precision) && c->cfg.shift >= 0) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   // forward: K, L, alpha (refined in mixed mode)
   GP_TRY(gp_assemble(c, X, n, D, h, &c->grad_factor));

@@ -101,6 +101,32 @@ def test_single_product_forms_shift_and_gmres_reach_the_mean_bar(api, form, n, m
           f"mean {em:.2e}")
     assert stats["shift"] > 0
     assert em <= 1e-10
+    # the factor is of K + tau I: Eq. 3's covariance, the variances and log det K are refused, not
+    # silently formed from the shifted matrix; likewise the NLML gradient under an automatic shift
+    for call in (lambda: api.gp_predict_full_cov(ctx, f, Xsd), lambda: api.gp_predict_var(ctx, f, Xsd),
+                 lambda: api.gp_logdet(ctx, f), lambda: api.gp_nlml_grad(ctx, Xd, yd, api.Hyper(*H0))):
+        with pytest.raises(api.GPError):
+            call()
+    f.free()
+
+
+def test_unshifted_tf32_factor_gives_covariance(api):
+    """GP_TF32 with cfg.shift < 0 factors K itself (positive definite at n = 1024): the covariance and
+    log-determinant are then formed, at the single product's accuracy."""
+    n, m = 1024, 128
+    X, y, Xs, _ = nfir.make_dataset(n, m, 8, 4)
+    ref = oracle.gp_predict(X, y, Xs, H0, tile=256)
+    ctx = api.Context(0, precision="tf32", shift=-1.0, timeout_s=20)
+    Xd, yd, Xsd = to_dev(X, y, Xs)
+    f = api.gp_assemble(ctx, Xd, api.Hyper(*H0))
+    api.gp_cholesky(ctx, f)
+    assert api.gp_factor_stats(ctx, f)["shift"] == 0
+    cov = api.gp_predict_full_cov(ctx, f, Xsd).cpu().numpy()
+    logdet = api.gp_logdet(ctx, f)
+    api.gp_sync(ctx)
+    ec, el = rel(cov, ref["cov"]), abs(logdet - ref["logdet"]) / abs(ref["logdet"])
+    print(f"tf32 unshifted n={n}: cov {ec:.2e} logdet {el:.2e}")
+    assert ec <= 5e-2 and el <= 1e-2
     f.free()
 
 
