@@ -30,15 +30,11 @@ sys.path.insert(0, ROOT)
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 pipe (measured: 1.22 TFLOP/s FFMA at ~2 GHz on 152 SMs)
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one FP64 Cholesky launch of the task-DAG
-# kernel, captured with ncu at n = 8192, T = 256 (32 tile rows): 2.070 GB read + 2.613 GB written.
-# Traffic follows the number of tile updates,
-# (Mt^3 - Mt)/6, so a launch with Mt tile rows of edge 256 moves this times updates(Mt)/updates(32).
-FP64_CHOL_TRAFFIC_MT32_T256 = 2.069696512e9 + 2.612768512e9
-
-
-def tile_updates(mt: int) -> int:
-    """Trailing tile updates (SYRK + GEMM) of a tiled Cholesky with mt tile rows."""
-    return (mt ** 3 - mt) // 6
+# kernel at n = 32768, T = 256, captured with ncu (the three metrics in one pass, the first Cholesky
+# launch of the run): 417.33 GB read + 189.03 GB written. Not scaled to other sizes: at T = 256 the
+# captures give 4.68 GB at n = 8192 and 73.0 GB at n = 16384, growing about twice as fast as the tile
+# updates ((Mt^3 - Mt)/6), as L2 serves a smaller share of the operand reads of larger panels.
+FP64_CHOL_TRAFFIC_N32768_T256 = 417.33e9 + 189.03e9
 
 
 _TF32_MEASURED = {}
@@ -91,10 +87,12 @@ def tf32_peak_tflops():
     return bf16 * 1.1 / 2.25, f"{src} BF16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
 
 
-# DRAM bytes (read + written) of one 3xTF32 Cholesky launch captured with ncu at n = 16384, tile 128
-# (128 tile rows; dram__bytes_read.sum + dram__bytes_write.sum): 17.735 GB read + 9.862 GB written.
-# Like the FP64 launch's, the traffic is scaled to other sizes by the number of tile updates.
-MIXED_CHOL_TRAFFIC_MT128_T128 = 17.734678016e9 + 9.862176000e9
+# DRAM bytes (read + written) of one 3xTF32 Cholesky launch at n = 32768, tile 128, captured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the first Cholesky launch of the run):
+# 265.891 GB read + 70.305 GB written. Not scaled to other sizes: the same capture at n = 16384 gives
+# 27.6 GB, and 8x that (the ratio of tile updates) falls 34 % short of the n = 32768 figure, because
+# the share of operand reads served by L2 falls as the panels grow.
+MIXED_CHOL_TRAFFIC_N32768_T128 = 265.891120640e9 + 70.305402624e9
 
 
 def hbm_peak_gbs():
@@ -131,8 +129,7 @@ def mixed_cholesky_roofline(n: int, tile: int, chol_s: float, prec: str = "fp32"
     nprod, kind, label = FORM_PRODUCTS[prec]
     peak, peak_src = tf32_peak_tflops() if kind == "tf32" else bf16_peak_tflops()
     executed = nprod * (n ** 3 / 3) / chol_s / 1e12
-    traffic = (MIXED_CHOL_TRAFFIC_MT128_T128 * tile_updates(-(-n // tile)) / tile_updates(128)
-               if (tile, prec) == (128, "fp32") else None)
+    traffic = MIXED_CHOL_TRAFFIC_N32768_T128 if (n, tile, prec) == (32768, 128, "fp32") else None
     r = {"kernel": f"dag_kernel mixed (tiled Cholesky, {label} on tcgen05)", "bound": "tensor",
          "achieved": executed, "peak": peak, "unit": "TFLOP/s", "frac": executed / peak,
          "peak_source": peak_src, "algorithmic_tflops": (n ** 3 / 3) / chol_s / 1e12, "traffic": traffic}
@@ -140,15 +137,13 @@ def mixed_cholesky_roofline(n: int, tile: int, chol_s: float, prec: str = "fp32"
         hbm, src = hbm_peak_gbs()
         r["traffic_gbs"] = traffic / chol_s / 1e9
         r["traffic_frac_of_hbm"] = traffic / chol_s / 1e9 / hbm
-        r["traffic_note"] = (f"bytes per launch, ncu capture at n=16384 scaled by the tile-update count; rate vs "
-                             f"the {src} HBM copy peak {hbm:.0f} GB/s")
+        r["traffic_note"] = (f"bytes per launch, one-pass ncu capture of the n=32768 launch; rate vs the {src} "
+                             f"HBM copy peak {hbm:.0f} GB/s")
     return r
 
 
 def fp64_cholesky_traffic(n: int, tile: int):
-    if tile != 256:
-        return None
-    return FP64_CHOL_TRAFFIC_MT32_T256 * tile_updates(-(-n // tile)) / tile_updates(32)
+    return FP64_CHOL_TRAFFIC_N32768_T256 if (n, tile) == (32768, 256) else None
 
 
 def algorithmic_flops(n: int, m: int) -> float:
@@ -567,7 +562,7 @@ def run_ours(args):
                           "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                           "peak_source": "FP64 FFMA pipe: 2 FMA/clk/SM x 152 SMs x max SM clock (derived)",
                           "traffic": fp64_cholesky_traffic(n, ctx_tile(n, args.tile)),
-                          "traffic_note": "bytes per launch, ncu capture at n=8192 scaled by the tile-update count"}
+                          "traffic_note": "bytes per launch, one-pass ncu capture of the n=32768 launch"}
                          if args.precision == "fp64" else
                          mixed_cholesky_roofline(n, ctx_tile(n, args.tile, True), chol_ms / 1e3, args.precision)),
             "gpu_launches": launches, "clocks": clocks}
