@@ -57,8 +57,9 @@ enum {
 
 /* Precision of the trailing SYRK/GEMM updates, of the panel TRSMs after the first block column and of
  * the covariance products (the diagonal POTRFs and every residual stay FP64). The reduced forms keep
- * an FP64 copy of K and refine K^{-1} y in FP64 (classic iterative refinement); their covariance and
- * log-determinant are not refined. The tensor-core forms other than GP_FP32 need tile edge 128 (the
+ * an FP64 copy of K and refine K^{-1} y in FP64 (classic iterative refinement; GMRES for GP_TF32 and
+ * GP_BF16); their covariance and log-determinant are not refined, and the shifted factors of GP_TF32 and
+ * GP_BF16 give the mean only. The tensor-core forms other than GP_FP32 need tile edge 128 (the
  * automatic choice; cfg.tile 0 or 128) and cfg.tensor_cores = 0. */
 enum {
   GP_FP64 = 0,       /* everything FP64 on the FP64 pipe                                            */
