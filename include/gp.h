@@ -156,11 +156,13 @@ gp_status gp_assemble(gp_ctx* ctx, const double* X, int64_t n, int32_t D, gp_hyp
 gp_status gp_cholesky(gp_ctx* ctx, gp_factor* K);
 
 /* Eq. (2): mean[0..m) = K_{Xs,X} K^{-1} y, using the factor L from gp_cholesky. y and Xs are device
- * arrays (n and m x D). With GP_FP32 precision the solve is refined in FP64 against the stored FP64
- * K; *ir_iters_out (host, may be NULL) receives the iteration count, which makes this call wait for
- * the stream. With GP_FP32 the call waits for the stream at every refinement step; it stops refining
- * at the first device error (left in the status word for gp_sync) and returns GP_ERR_NONFINITE for a
- * non-finite residual without one. alpha = K^{-1} y stays in the factor for gp_nlml. */
+ * arrays (n and m x D). With the reduced forms the solve is refined in FP64 against the stored FP64
+ * K (classic refinement for GP_FP32, GP_BF16X6, GP_BF16X3; GMRES for GP_TF32, GP_BF16); *ir_iters_out
+ * (host, may be NULL) receives the refinement steps (GMRES: preconditioned matrix-vector products),
+ * which makes this call wait for the stream. The refined forms wait for the stream at every step (the
+ * host reads the backward error); they stop refining at the first device error (left in the status
+ * word for gp_sync) and return GP_ERR_NONFINITE for a non-finite residual without one. GP_FP64 and
+ * GP_FP64_OZAKI do not refine. alpha = K^{-1} y stays in the factor for gp_nlml_grad and gp_alpha. */
 gp_status gp_predict_mean(gp_ctx* ctx, gp_factor* L, const double* y, const double* Xs, int64_t m,
                           double* mean_out, int32_t* ir_iters_out);
 
